@@ -1,0 +1,515 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Every test here checks the oracle against something other than itself: values
+the paper prints (tests/golden/paper_constants.json), closed-form flow
+solutions, conservation laws, algebraic identities of the model, the paper's
+own statements (MRT with equal rates is SRT; near-zero error on straight walls
+at tau* and at Lambda = 3/8; error falls with grid refinement), and brute force
+on tiny inputs. A plausible slip in the oracle (a dropped forcing term, a wrong
+sign, a transposed index, a wrong mirror direction) fails at least one of them.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1812_05401_gb300 import inputs as I
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
+TAU_STAR = 0.5 + math.sqrt(6.0) / 4.0
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+# -----------------------------------------------------------------------------
+# Model constants against the printed values
+# -----------------------------------------------------------------------------
+
+def test_velocity_set_matches_printed_formula():
+    assert O.velocity_set().tolist() == GOLDEN["velocity_set"]["value"]
+
+
+def test_weights_match_printed_values_and_isotropy():
+    w = O.weights()
+    printed = [float(Fraction(s)) for s in GOLDEN["weights"]["value"]]
+    assert np.array_equal(w, np.array(printed))
+    xi = O.velocity_set().astype(float)
+    # Lattice isotropy that fixes c_s^2 = 1/3 (Section 2.1.1).
+    assert abs(w.sum() - 1.0) < 1e-15
+    np.testing.assert_allclose(np.einsum("a,ai,aj->ij", w, xi, xi), np.eye(2) / 3.0, atol=1e-15)
+    assert abs(np.einsum("a,ai->i", w, xi)).max() < 1e-16
+
+
+def test_moment_matrix_matches_printed_and_is_orthogonal():
+    M = O.moment_matrix()
+    assert np.array_equal(M, np.array(GOLDEN["moment_matrix"]["value"], dtype=float))
+    # The Lallemand-Luo basis is orthogonal; a mistyped entry breaks this.
+    np.testing.assert_array_equal(M @ M.T, np.diag([9.0, 36, 36, 6, 12, 6, 12, 4, 4]))
+    Minv = O.moment_matrix_inverse()
+    np.testing.assert_allclose(Minv @ M, np.eye(9), atol=1e-15)
+    # Row k of M is the moment of xi-polynomials: rho, j_x, j_y, p_xx, p_xy rows.
+    xi = O.velocity_set()
+    np.testing.assert_array_equal(M[3], xi[:, 0])
+    np.testing.assert_array_equal(M[5], xi[:, 1])
+    np.testing.assert_array_equal(M[7], xi[:, 0] ** 2 - xi[:, 1] ** 2)
+    np.testing.assert_array_equal(M[8], xi[:, 0] * xi[:, 1])
+
+
+# -----------------------------------------------------------------------------
+# Equilibrium and forcing: exact moment identities
+# -----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(5))
+def test_equilibrium_moments_closed_form(seed):
+    r = _rng(seed)
+    rho, ux, uy = 1.0 + 0.1 * r.standard_normal(), 0.1 * r.standard_normal(), 0.1 * r.standard_normal()
+    feq = O.equilibrium(rho, ux, uy)
+    xi = O.velocity_set().astype(float)
+    u = np.array([ux, uy])
+    assert abs(feq.sum() - rho) < 1e-15
+    np.testing.assert_allclose(xi.T @ feq, rho * u, atol=1e-16)
+    # Second-order Hermite equilibrium: sum xi xi f_eq = rho c_s^2 I + rho u u.
+    np.testing.assert_allclose(np.einsum("a,ai,aj->ij", feq, xi, xi),
+                               rho / 3.0 * np.eye(2) + rho * np.outer(u, u), atol=1e-15)
+    # The two printed equilibria agree: M f_eq = m_eq (Sections 2.1.1, 2.1.2).
+    np.testing.assert_allclose(O.moment_matrix() @ feq, O.mrt_equilibrium_moments(rho, ux, uy),
+                               atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_guo_forcing_moments(seed):
+    r = _rng(100 + seed)
+    tau = 0.55 + r.random()
+    ux, uy, fx, fy = 0.1 * r.standard_normal(4)
+    F = O.guo_force_srt(tau, ux, uy, fx, fy)
+    xi = O.velocity_set().astype(float)
+    pre = 1.0 - 1.0 / (2.0 * tau)
+    f = np.array([fx, fy])
+    u = np.array([ux, uy])
+    # Guo et al.'s design conditions: zeroth, first and second moments.
+    assert abs(F.sum()) < 1e-16
+    np.testing.assert_allclose(xi.T @ F, pre * f, atol=1e-16)
+    np.testing.assert_allclose(np.einsum("a,ai,aj->ij", F, xi, xi),
+                               pre * (np.outer(u, f) + np.outer(f, u)), atol=1e-16)
+    # Its moments in the MRT basis: (0, 6u.f, -6u.f, f_x, -f_x, f_y, -f_y,
+    # 2(u f_x - v f_y), u f_y + v f_x), no prefactor for Eq. Guo2.
+    MF = O.moment_matrix() @ O.guo_force_mrt(ux, uy, fx, fy)
+    uf = ux * fx + uy * fy
+    np.testing.assert_allclose(
+        MF, [0, 6 * uf, -6 * uf, fx, -fx, fy, -fy, 2 * (ux * fx - uy * fy), ux * fy + uy * fx],
+        atol=1e-15)
+
+
+# -----------------------------------------------------------------------------
+# Penalization: the implicit velocity and the force
+# -----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(6))
+def test_implicit_velocity_solves_its_definition(seed):
+    r = _rng(200 + seed)
+    cfg = O.Config(nx=1, ny=1, tau=0.8, g=tuple(1e-5 * r.standard_normal(2)))
+    f = I.random_populations(1, 1, seed + 7, 0.05)[:, 0, 0]
+    usx, usy = 0.03 * r.standard_normal(2)
+    xi = O.velocity_set().astype(float)
+    for chi in (0, 1):
+        rho, ux, uy, fpx, fpy = O.node_macros(cfg, f, chi, usx, usy)
+        j = xi.T @ f
+        ftot = np.array([fpx, fpy]) + rho * np.array(cfg.g)
+        # Eq. velocity: rho u = sum xi f + f_tot / 2.
+        np.testing.assert_allclose(rho * np.array([ux, uy]), j + 0.5 * ftot, rtol=0, atol=1e-16)
+        # Eq. 261: f_pen = -rho (chi/eta)(u - u_s); compare in the form that
+        # does not amplify rounding: u - u_s = -f_pen eta / (rho chi).
+        if chi:
+            np.testing.assert_allclose(np.array([ux - usx, uy - usy]),
+                                       -np.array([fpx, fpy]) * cfg.eta / rho, rtol=1e-9, atol=1e-17)
+            # |u - u_s| is 1/(1 + chi/(2 eta)) of the unpenalized slip j/rho - u_s.
+            slip0 = np.hypot(*(j / rho + 0.5 * np.array(cfg.g) - np.array([usx, usy])))
+            assert np.hypot(ux - usx, uy - usy) <= slip0 / (1.0 + 0.5 / cfg.eta) * (1 + 1e-9)
+        else:
+            assert fpx == 0.0 and fpy == 0.0
+        # Literal Eq. 276 + Eq. 261 agree with the rearranged force to the
+        # literal form's own rounding (chi/eta times the rounding of u).
+        lit = O.node_macros(cfg, f, chi, usx, usy, literal=True)
+        np.testing.assert_allclose(lit[1:3], (ux, uy), rtol=1e-14, atol=1e-17)
+        np.testing.assert_allclose(lit[3:5], (fpx, fpy), rtol=1e-6, atol=1e-9)
+
+
+def test_single_node_collision_exact_rational_brute_force():
+    """One SRT node collision recomputed in exact rational arithmetic from the
+    moment identities (not from the oracle's formulas): post-collision mass is
+    rho and momentum is j + f_tot."""
+    cfg = O.Config(nx=1, ny=1, tau=0.8, collision=O.SRT)
+    f = I.random_populations(1, 1, 31, 0.05)[:, 0, 0]
+    xi = O.velocity_set()
+    for chi, us in ((0, (0.0, 0.0)), (1, (0.01, -0.02))):
+        fo, (px, py) = O.collide_node(cfg, f, chi, *us)
+        rho = sum(Fraction(v) for v in f)
+        jx = sum(Fraction(int(xi[a, 0])) * Fraction(f[a]) for a in range(9))
+        jy = sum(Fraction(int(xi[a, 1])) * Fraction(f[a]) for a in range(9))
+        # exact kappa-form force from the exact j (Eq. 261 with Eq. 276)
+        ce = Fraction(chi) / Fraction(cfg.eta)
+        kappa = ce / (1 + ce / 2)
+        fx = -kappa * (jx - rho * Fraction(us[0]))
+        fy = -kappa * (jy - rho * Fraction(us[1]))
+        assert abs(float(sum(Fraction(v) for v in fo) - rho)) < 1e-15
+        assert abs(float(sum(int(xi[a, 0]) * Fraction(fo[a]) for a in range(9)) - (jx + fx))) < 1e-15
+        assert abs(float(sum(int(xi[a, 1]) * Fraction(fo[a]) for a in range(9)) - (jy + fy))) < 1e-15
+        assert abs(px - float(fx)) < 1e-14 and abs(py - float(fy)) < 1e-14
+
+
+@pytest.mark.parametrize("coll", [O.SRT, O.MRT])
+@pytest.mark.parametrize("seed", range(4))
+def test_collision_conserves_mass_and_adds_force(coll, seed):
+    r = _rng(300 + seed)
+    cfg = O.Config(nx=1, ny=1, collision=coll, tau=0.52 + r.random(), lam=3 / 16,
+                   g=tuple(1e-5 * r.standard_normal(2)))
+    f = I.random_populations(1, 1, 40 + seed, 0.05)[:, 0, 0]
+    xi = O.velocity_set().astype(float)
+    for chi in (0, 1):
+        fo, (px, py) = O.collide_node(cfg, f, chi, 0.01, -0.005)
+        rho = f.sum()
+        assert abs(fo.sum() - rho) < 1e-15
+        np.testing.assert_allclose(xi.T @ fo, xi.T @ f + np.array([px, py]) + rho * np.array(cfg.g),
+                                   atol=2e-16)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_mrt_with_equal_rates_is_srt_single_node(seed):
+    """Section 2.1.2: with all relaxation rates 1/tau, MRT with Lu's forcing
+    reduces to SRT with Guo's forcing."""
+    r = _rng(400 + seed)
+    tau = 0.55 + 2 * r.random()
+    f = I.random_populations(1, 1, 60 + seed, 0.05)[:, 0, 0]
+    srt = O.Config(nx=1, ny=1, collision=O.SRT, tau=tau, g=(1e-5, -2e-5))
+    mrt = O.Config(nx=1, ny=1, collision=O.MRT, tau=tau, g=(1e-5, -2e-5), rates=(1 / tau,) * 9)
+    for chi in (0, 1):
+        a, _ = O.collide_node(srt, f, chi, 0.02, 0.01)
+        b, _ = O.collide_node(mrt, f, chi, 0.02, 0.01)
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-15)
+        # The conserved moments' rates (s_0, s_3, s_5) do not matter: the
+        # printed S with zeros there gives the same result.
+        rates = [0, 1 / tau, 1 / tau, 0, 1 / tau, 0, 1 / tau, 1 / tau, 1 / tau]
+        c, _ = O.collide_node(O.Config(nx=1, ny=1, collision=O.MRT, tau=tau, g=(1e-5, -2e-5),
+                                       rates=tuple(rates)), f, chi, 0.02, 0.01)
+        np.testing.assert_allclose(a, c, rtol=0, atol=1e-15)
+
+
+def test_mrt_with_equal_rates_is_srt_on_a_grid():
+    n = 24
+    base = dict(nx=n, ny=n, tau=0.9, bodies=[O.Body(11.5, 11.5, 5.0, omega=0.002)])
+    srt = O.Config(collision=O.SRT, **base)
+    mrt = O.Config(collision=O.MRT, rates=(1 / 0.9,) * 9, **base)
+    u0 = I.velocity_field(n, n, (0.01, 0.0), 1e-3, seed=3)
+    fa = O.init_equilibrium(srt, 1.0, u0)
+    fb = fa.copy()
+    O.run(srt, fa, 300)
+    O.run(mrt, fb, 300)
+    np.testing.assert_allclose(fa, fb, rtol=0, atol=1e-14)
+
+
+# -----------------------------------------------------------------------------
+# Grid invariants
+# -----------------------------------------------------------------------------
+
+def _couette_cfg(n, coll=O.SRT, tau=0.8, r1=None, r2=None, ud=0.01):
+    c = (n - 1) / 2.0
+    r1 = r1 or 0.1875 * n
+    r2 = r2 or 0.4375 * n
+    return O.Config(nx=n, ny=n, collision=coll, tau=tau, lam=3 / 16,
+                    bodies=[O.Body(c, c, r1, omega=ud / r1), O.Body(c, c, r2, outside=True)])
+
+
+@pytest.mark.parametrize("coll", [O.SRT, O.MRT])
+def test_mass_conserved_with_periodic_boundaries(coll):
+    cfg = _couette_cfg(32, coll)
+    f = O.init_equilibrium(cfg, 1.0, I.velocity_field(32, 32, (0.0, 0.0), 1e-3, seed=5))
+    m0 = f.sum()
+    _, _, mass = O.run(cfg, f, 2000)
+    # round-off only: about 1e-16 per node update, accumulated over the run
+    assert abs(mass - m0).max() / m0 < 1e-12
+    assert abs(f.sum() - m0) / m0 < 1e-12
+    # a mass leak of one part in 1e9 per step would show
+    assert abs(mass[-1] - mass[0]) / m0 < 1e-12
+
+
+@pytest.mark.parametrize("coll", [O.SRT, O.MRT])
+def test_global_momentum_balance(coll):
+    """With periodic boundaries, the total momentum changes in a step by exactly
+    the sum of the body forces: P(n+1) - P(n) = -F_body(n) + sum rho g."""
+    g = (2e-6, -1e-6)
+    cfg = _couette_cfg(24, coll)
+    cfg.g = g
+    f = O.init_equilibrium(cfg, 1.0, I.velocity_field(24, 24, (0.0, 0.0), 1e-3, seed=9))
+    xi = O.velocity_set().astype(float)
+
+    def momentum(ff):
+        return np.einsum("ai,ayx->i", xi, ff)
+
+    for _ in range(5):
+        p0 = momentum(f)
+        fx, fy, mass = O.run(cfg, f, 1)
+        p1 = momentum(f)
+        # tolerance: summation round-off over 9 n^2 terms of size ~0.1
+        np.testing.assert_allclose(p1 - p0, [-fx[0] + g[0] * mass[0], -fy[0] + g[1] * mass[0]],
+                                   rtol=0, atol=2e-13)
+    assert abs(fx[0]) > 1e-6  # the rotating cylinder is pushing on the fluid
+
+
+def test_uniform_body_force_accelerates_exactly():
+    """No solids, uniform force g, periodic box: the velocity that step n+1
+    computes is (n + 1/2) g / rho exactly (half-force velocity, Eq. velocity)."""
+    g = (3e-6, 1e-6)
+    cfg = O.Config(nx=8, ny=6, collision=O.MRT, tau=0.7, g=g)
+    f = O.init_equilibrium(cfg)
+    n = 40
+    O.run(cfg, f, n)
+    rho, ux, uy = O.moments(cfg, f, n)
+    np.testing.assert_allclose(rho, 1.0, atol=1e-14)
+    # round-off of O(1e-17) per step; a missing half-force term would be 1.5e-6
+    np.testing.assert_allclose(ux, (n + 0.5) * g[0], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(uy, (n + 0.5) * g[1], rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("coll", [O.SRT, O.MRT])
+@pytest.mark.parametrize("tau", [0.6, 0.9, 1.4])
+def test_shear_wave_decay_gives_viscosity(coll, tau):
+    """Section 2.1.1: nu = c_s^2 (tau - 1/2). A sinusoidal shear wave in a
+    periodic box decays as exp(-nu k^2 t)."""
+    n, amp = 64, 1e-4
+    k = 2 * np.pi / n
+    steps = int(0.5 / ((tau - 0.5) / 3.0 * k * k))  # decay to exp(-1/2)
+    cfg = O.Config(nx=2, ny=n, collision=coll, tau=tau, lam=3 / 16)
+    y = np.arange(n)
+    u = np.zeros((2, n, 2))
+    u[0] = amp * np.sin(2 * np.pi * y / n)[:, None]
+    f = O.init_equilibrium(cfg, 1.0, u)
+    O.run(cfg, f, steps)
+    _, ux, _ = O.moments(cfg, f, steps)
+    a = 2.0 / n * (ux[:, 0] * np.sin(2 * np.pi * y / n)).sum()
+    nu = -math.log(a / amp) / (k * k * steps)
+    # the lattice adds O(k^2) corrections (~1% at 64 nodes per wavelength);
+    # using tau instead of tau - 1/2, or a wrong c_s^2, is off by >= 20%
+    assert abs(nu / ((tau - 0.5) / 3.0) - 1.0) < 0.02
+
+
+# -----------------------------------------------------------------------------
+# Closed-form flows and the paper's printed claims
+# -----------------------------------------------------------------------------
+
+def _plates(H, e, tau, coll, lam, ud=0.0, g=0.0, steps=None):
+    """Plates of thickness e around a gap of H rows, periodic in x and y. The
+    solid rows are y <= e and y >= e + H, so the walls sit on the outermost
+    solid nodes y = e and y = e + H (the reading that reproduces the paper's
+    near-zero error at tau*; Section 3.1)."""
+    ny, nx = H + 2 * e, 2
+    y = np.arange(ny)
+    lower, upper = y <= e, y >= e + H
+    chi = np.zeros((ny, nx), np.uint8)
+    chi[lower | upper, :] = 1
+    us = np.zeros((2, ny, nx))
+    us[0][lower, :] = -ud
+    us[0][upper, :] = ud
+    cfg = O.Config(nx=nx, ny=ny, collision=coll, tau=tau, lam=lam, chi=chi, us=us, g=(g, 0.0))
+    f = O.init_equilibrium(cfg)
+    nu = (tau - 0.5) / 3.0
+    steps = steps or int(8 * H * H / nu)
+    O.run(cfg, f, steps)
+    _, ux, _ = O.moments(cfg, f, steps)
+    return y, ux[:, 0], chi[:, 0] == 0, nu
+
+
+def _l2(u, ua, fluid):
+    """Relative L2 error over the fluid nodes, Eq. err."""
+    return math.sqrt(((u - ua)[fluid] ** 2).sum() / (ua[fluid] ** 2).sum())
+
+
+def test_symmetric_shear_near_zero_error_at_optimal_tau():
+    """Section 3.1 (Fig. 3a): the SRT error is very close to zero at
+    tau* = 1/2 + sqrt(6)/4 and clearly larger elsewhere (Eq. analy)."""
+    H, e, ud = 20, 6, 0.01
+    errs = {}
+    for tau in (0.7, TAU_STAR, 2.0):
+        y, u, fl, _ = _plates(H, e, tau, O.SRT, 3 / 16, ud=ud)
+        errs[tau] = _l2(u, 2 * ud / H * (y - e) - ud, fl)
+    assert errs[TAU_STAR] < 1e-6
+    assert errs[0.7] > 100 * errs[TAU_STAR] and errs[2.0] > 100 * errs[TAU_STAR]
+
+
+@pytest.mark.parametrize("tau", [0.7, 1.3])
+def test_symmetric_shear_mrt_lambda_three_eighths(tau):
+    """Section 3.1 (Fig. 3b, Fig. 4): MRT with Lambda = 3/8 is very close to
+    exact for any tau; the default Lambda = 3/16 is not."""
+    H, e, ud = 20, 6, 0.01
+    y, u, fl, _ = _plates(H, e, tau, O.MRT, 3 / 8, ud=ud)
+    assert _l2(u, 2 * ud / H * (y - e) - ud, fl) < 1e-6
+    y, u, fl, _ = _plates(H, e, tau, O.MRT, 3 / 16, ud=ud)
+    assert _l2(u, 2 * ud / H * (y - e) - ud, fl) > 1e-3
+
+
+@pytest.mark.parametrize("coll,tau,lam,bound", [
+    (O.SRT, TAU_STAR, 3 / 16, 1e-6), (O.MRT, 0.7, 3 / 8, 1e-6), (O.SRT, 0.8, 3 / 16, 0.2)])
+def test_poiseuille_between_penalized_plates(coll, tau, lam, bound):
+    """Plane Poiseuille flow driven by a uniform body force g between plates at
+    rest: u(y) = g (y - y0)(y1 - y) / (2 nu), the Navier-Stokes solution of the
+    momentum equation with a uniform force (Section 2.1)."""
+    H, e, g = 20, 4, 1e-6
+    y, u, fl, nu = _plates(H, e, tau, coll, lam, g=g)
+    ua = g / (2 * nu) * (y - e) * (e + H - y)
+    err = _l2(u, ua, fl)
+    assert err < bound
+    if bound > 1e-3:
+        assert err > 1e-3  # away from tau* the penalized wall slips
+
+
+def _circular_couette_error(n, steps, coll=O.SRT, tau=0.8):
+    r1, r2, ud = 0.1875 * n, 0.4375 * n, 0.01
+    cfg = _couette_cfg(n, coll, tau, r1, r2, ud)
+    f = O.init_equilibrium(cfg)
+    O.run(cfg, f, steps)
+    _, ux, uy = O.moments(cfg, f, steps)
+    chi, _ = O.mask(cfg, steps)
+    c = (n - 1) / 2.0
+    yy, xx = np.mgrid[0:n, 0:n]
+    dx, dy = xx - c, yy - c
+    r = np.hypot(dx, dy)
+    ut = -ud * r1 / (r2 ** 2 - r1 ** 2) * r + ud * r1 * r2 ** 2 / ((r2 ** 2 - r1 ** 2) * r)
+    fl = chi == 0
+    return _l2(uy, ut * dx / r, fl), (ux, uy)
+
+
+def test_circular_couette_staircase_error_falls_with_grid():
+    """Section 3.2 (Eq. Sltan, Fig. 11, Table 1 / Fig. 17): with a staircase
+    curved wall the error is nonzero but decreases as the grid is refined."""
+    e32, _ = _circular_couette_error(32, 4000)
+    e64, _ = _circular_couette_error(64, 14000)
+    assert 1e-3 < e64 < e32 < 0.1
+
+
+def test_circular_couette_rotation_symmetry():
+    """The mask is symmetric under a 90-degree rotation about the box centre,
+    so the velocity field must be too: u(R x) = R u(x)."""
+    _, (ux, uy) = _circular_couette_error(24, 600)
+    # rotation R by +90 degrees about the centre: p = (x, y) -> (n-1-y, x) and
+    # (u, v) -> (-v, u). At q = R p the field must equal R u(p), with
+    # p = R^-1 q = (y_q, n-1-x_q).
+    n = ux.shape[0]
+    yy, xx = np.mgrid[0:n, 0:n]
+    ux_rot = -uy[n - 1 - xx, yy]
+    uy_rot = ux[n - 1 - xx, yy]
+    np.testing.assert_allclose(ux, ux_rot, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(uy, uy_rot, rtol=0, atol=1e-15)
+
+
+# -----------------------------------------------------------------------------
+# Channel boundary conditions
+# -----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("coll", [O.SRT, O.MRT])
+def test_uniform_flow_is_a_fixed_point_of_the_channel(coll):
+    """Uniform inlet, zero-gradient outlet and free-slip walls leave the uniform
+    equilibrium flow f_eq(1, (U, 0)) unchanged (any wrong mirror or remap of a
+    population breaks this, since f_5 != f_6 when U != 0)."""
+    U = 0.05
+    cfg = O.Config(nx=12, ny=7, collision=coll, tau=0.6, lam=3 / 16, bc_x=O.BC_INLET_OUTLET,
+                   bc_y=O.BC_FREE_SLIP, u_in=(U, 0.0))
+    u0 = I.velocity_field(12, 7, (U, 0.0))
+    f = O.init_equilibrium(cfg, 1.0, u0)
+    f0 = f.copy()
+    O.run(cfg, f, 50)
+    # round-off only; a wrong remap would change populations by ~1e-3
+    np.testing.assert_allclose(f, f0, rtol=0, atol=2e-15)
+
+
+@pytest.mark.parametrize("coll", [O.SRT, O.MRT])
+def test_channel_mirror_symmetry(coll):
+    """A cylinder on the centre line of a free-slip channel with a symmetric
+    start stays mirror symmetric about the centre line: u(x, y) = u(x, ny-1-y),
+    v(x, y) = -v(x, ny-1-y)."""
+    nx, ny = 40, 17
+    cfg = O.Config(nx=nx, ny=ny, collision=coll, tau=0.56, lam=3 / 16, bc_x=O.BC_INLET_OUTLET,
+                   bc_y=O.BC_FREE_SLIP, u_in=(0.05, 0.0),
+                   bodies=[O.Body(10.0, (ny - 1) / 2.0, 3.0)])
+    f = O.init_equilibrium(cfg, 1.0, I.velocity_field(nx, ny, (0.05, 0.0)))
+    fx, fy, _ = O.run(cfg, f, 200)
+    _, ux, uy = O.moments(cfg, f, 200)
+    np.testing.assert_allclose(ux, ux[::-1], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(uy, -uy[::-1], rtol=0, atol=1e-15)
+    assert abs(fy).max() < 1e-14 and fx[-1] > 0  # drag downstream, no lift
+
+
+def test_outlet_copies_last_column():
+    """The zero-gradient outlet: populations entering the last column from the
+    ghost column are those that left the last column (the pull from x = nx
+    reads x = nx - 1)."""
+    nx, ny = 6, 5
+    cfg = O.Config(nx=nx, ny=ny, collision=O.SRT, tau=1.0, bc_x=O.BC_INLET_OUTLET,
+                   bc_y=O.BC_PERIODIC, u_in=(0.02, 0.0))
+    f = I.random_populations(nx, ny, 77, 0.05)
+    rho, ux, uy = O.moments(cfg, f, 0)
+    xi = O.velocity_set()
+    # recompute the pulled density at the last column from the rule directly
+    for yq in range(ny):
+        s = 0.0
+        for a in range(9):
+            xs, ys = nx - 1 - xi[a, 0], (yq - xi[a, 1]) % ny
+            xs = min(xs, nx - 1)
+            s += f[a, ys, xs]
+        assert abs(s - rho[yq, nx - 1]) < 1e-15
+
+
+# -----------------------------------------------------------------------------
+# Geometry
+# -----------------------------------------------------------------------------
+
+def test_mask_brute_force_exact_integers():
+    """Staircase masks against exact integer arithmetic: a centre on the
+    half-integer grid and an integer radius make (x-cx)^2 + (y-cy)^2 <= R^2
+    exact when every term is multiplied by 4."""
+    nx, ny = 23, 19
+    cx, cy, R = 10.5, 9.0, 6.0
+    cfg = O.Config(nx=nx, ny=ny, bodies=[O.Body(cx, cy, R, omega=0.003),
+                                         O.Body(11.0, 9.0, 9.0, outside=True)])
+    chi, us = O.mask(cfg, 0)
+    for y in range(ny):
+        for x in range(nx):
+            d4 = (2 * x - 21) ** 2 + (2 * y - 18) ** 2
+            inside = d4 <= 4 * 36
+            outside = (2 * x - 22) ** 2 + (2 * y - 18) ** 2 >= 4 * 81
+            assert chi[y, x] == int(inside or outside)
+            if inside:
+                assert us[0, y, x] == pytest.approx(-0.003 * (y - cy), abs=1e-18)
+                assert us[1, y, x] == pytest.approx(0.003 * (x - cx), abs=1e-18)
+            elif outside:
+                assert us[0, y, x] == 0.0 and us[1, y, x] == 0.0
+
+
+def test_moving_body_velocity_is_centre_derivative():
+    T, A = 400.0, 5.0
+    cfg = O.Config(nx=40, ny=40, bodies=[O.Body(20.0, 20.0, 6.0, amp_y=A, period=T)])
+    for t in (0, 37, 100, 251):
+        chi, us = O.mask(cfg, t)
+        yc = 20.0 + A * math.sin(2 * math.pi * t / T)
+        vy = A * 2 * math.pi / T * math.cos(2 * math.pi * t / T)
+        yy, xx = np.mgrid[0:40, 0:40]
+        expect = ((xx - 20.0) ** 2 + (yy - yc) ** 2 <= 36.0)
+        assert np.array_equal(chi.astype(bool), expect)
+        np.testing.assert_allclose(us[1][expect], vy, rtol=1e-15)
+        # central difference of the centre position
+        h = 1e-3
+        dc = A * (math.sin(2 * math.pi * (t + h) / T) - math.sin(2 * math.pi * (t - h) / T)) / (2 * h)
+        assert abs(dc - vy) < 1e-8
+
+
+def test_splitmix64_published_vectors():
+    """SplitMix64 from seed 1234567: the first outputs of the published
+    generator (state += golden gamma, then the two multiply-xorshift rounds)."""
+    # Known answer: seed 0 gives 0xE220A8397B1DCDAF as its first output.
+    assert int(I.splitmix64(0, 1)[0]) == 0xE220A8397B1DCDAF
+    a = I.uniform01(5, 1000)
+    assert a.min() >= 0.0 and a.max() < 1.0 and abs(a.mean() - 0.5) < 0.03
