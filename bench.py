@@ -1,0 +1,404 @@
+"""Benchmark of the VP-LBM hot path on GB300.
+
+Workload (default): the moving-cylinder channel, 16384 x 4096 D2Q9 MRT with
+FP32 populations (67.1M nodes): a cylinder of D = 256 translating as
+y(t) = y0 + 0.5 D sin(2 pi t / 20000), inlet u = 0.05, Re = 2000, free-slip
+walls, zero-gradient outlet. One step = the mask/solid-velocity update over
+the swept region plus the fused pull-penalize-collide-reduce kernel over every
+node, i.e. every row of the hot path. The two population buffers (4.8 GB) are
+far larger than L2, so no flush is needed between steps.
+
+Output: one JSON line (rank 0). `value` is MLUPS (million node updates per
+second) over all ranks; `e2e` repeats the measurement through the public API
+with a host read of each step's force record; `roofline` relates the fused
+kernel's algorithmic bytes (73 B per node update: 9 x 4 B read, 9 x 4 B
+written, 1 B mask) to its CUDA-event duration; `cpu_baseline` times the FP64
+oracle on a bounded sample of the same workload. `--impl reference` times only
+the oracle (the reference arm).
+
+Multi-GPU: the grid is not split (no halo exchange is built); every rank runs
+its own replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALGO_BYTES = {"f32": 73.0, "f16": 37.0, "bf16": 37.0, "f64": 145.0}  # per node update, u8 mask
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["paper_1812_05401_gb300/csrc/vplbm_device.cuh", "paper_1812_05401_gb300/csrc/vplbm_params.h",
+                  "paper_1812_05401_gb300/csrc/vplbm_kernels_impl.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        for k in ("hbm_gbs", "hbm_GBs", "copy_gbs"):
+            if k in d and d[k]:
+                return float(d[k]), "measured"
+        if "hbm" in d and isinstance(d["hbm"], dict):
+            for k in ("gbs", "GB/s", "value"):
+                if k in d["hbm"]:
+                    return float(d["hbm"][k]), "measured"
+    except Exception:
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def traffic_per_launch(workload: str, storage: str):
+    """DRAM bytes per fused launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "fused_step_traffic.json")
+    try:
+        d = json.load(open(p))
+        e = d.get(f"{workload}:{storage}")
+        if e and e.get("kernel_hash") == kernel_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload(name: str, storage: str):
+    from paper_1812_05401_gb300 import inputs as I
+    if name == "moving-cylinder":
+        return I.c5_moving_cylinder(storage)
+    if name == "cylinder-re1000":
+        return I.c3_cylinder_re1000(storage)
+    if name == "cylinder-re100":
+        return I.c2_cylinder_re100()
+    raise ValueError(name)
+
+
+# -----------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the workload
+# -----------------------------------------------------------------------------
+
+def oracle_sample(w, budget_s: float = 12.0, max_steps: int = 50):
+    """Runs the FP64 oracle on a window of the workload's grid: rows around the
+    body (at most 1024) and the first half of the columns (at most 8192), same
+    physics, as many steps as fit in budget_s. Returns (MLUPS, description,
+    threads)."""
+    import oracle as O
+    tau = O.tau_from_reynolds(w.u_ref, w.l_ref, w.re) if w.re else w.tau
+    ny = min(w.ny, 1024)
+    nx = min(w.nx, 8192)
+    y_off = max(0, int(w.bodies[0].cy) - ny // 2) if w.bodies else 0
+    bodies = [O.Body(b.cx, b.cy - y_off, b.radius, b.amp_x, b.amp_y, b.period, b.omega, b.outside)
+              for b in w.bodies]
+    chan = w.bc == "channel"
+    cfg = O.Config(nx=nx, ny=ny, collision=O.MRT if w.collision == "mrt" else O.SRT, tau=tau,
+                   lam=w.lam, bc_x=O.BC_INLET_OUTLET if chan else O.BC_PERIODIC,
+                   bc_y=O.BC_FREE_SLIP if chan else O.BC_PERIODIC,
+                   u_in=(w.u_ref, 0.0) if chan else (0.0, 0.0), bodies=bodies)
+    import numpy as np
+    u0 = np.zeros((2, ny, nx))
+    if chan:
+        u0[0] = w.u_ref
+    f = O.init_equilibrium(cfg, 1.0, u0)
+    O.run(cfg, f, 1)  # warm-up (page-in)
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps:
+        O.run(cfg, f, 1, t0=steps + 1)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    mlups = nx * ny * steps / dt / 1e6
+    desc = (f"FP64 oracle, {nx}x{ny} window of the {w.nx}x{w.ny} grid (rows around the body), "
+            f"{steps} steps, {dt:.1f} s")
+    return mlups, desc, O.num_threads()
+
+
+# -----------------------------------------------------------------------------
+# GPU arm
+# -----------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1812_05401_gb300 import vplbm as V
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = make_workload(args.workload, args.storage)
+    nodes = w.nx * w.ny
+    s = V.Solver.from_workload(w, stream=stream, ring_len=max(4096, args.steps + 16))
+    try:
+        # warm-up
+        s.step(args.warmup)
+        s.synchronize()
+        s.forces()
+
+        # ---- device-resident timed region ------------------------------------
+        V.vplbm_enable_timing(s.h, True)
+        V.vplbm_fused_timing(s.h)  # reset
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        l0 = s.launches
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+        s.step(args.steps)
+        with torch.cuda.stream(stream):
+            e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        launches = s.launches - l0
+        ms = e0.elapsed_time(e1)
+        clk = clocks.stop()
+        s.synchronize()  # raises if the run diverged
+        fused_ms, fused_n = V.vplbm_fused_timing(s.h)
+        V.vplbm_enable_timing(s.h, False)
+        ms = max_over_ranks(ms)
+        value = world * nodes * args.steps / (ms / 1e3) / 1e6
+
+        # ---- end to end through the public API: each step's force record is
+        # read back to the host (synchronizing), the body state goes in as the
+        # launch parameters of the step.
+        s.forces()
+        e_steps = max(3, args.steps // 2)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            s.step(1)
+            fx, fy, ms_ = s.forces(cap=1)
+        torch.cuda.synchronize()
+        barrier()
+        e_s = max_over_ranks(time.perf_counter() - t0)
+        e2e = world * nodes * e_steps / e_s / 1e6
+    finally:
+        s.close()
+
+    # ---- same workload, FP16-offset storage (FP32 vs FP16-store comparison)
+    extra = {}
+    if args.compare_f16 and args.storage == "f32":
+        w16 = make_workload(args.workload, "f16")
+        s16 = V.Solver.from_workload(w16, stream=stream, ring_len=4096)
+        try:
+            s16.step(args.warmup)
+            s16.synchronize()
+            V.vplbm_enable_timing(s16.h, True)
+            V.vplbm_fused_timing(s16.h)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                a0.record(stream)
+            s16.step(args.steps)
+            with torch.cuda.stream(stream):
+                a1.record(stream)
+            torch.cuda.synchronize()
+            s16.synchronize()
+            ms16 = max_over_ranks(a0.elapsed_time(a1))
+            k16, n16 = V.vplbm_fused_timing(s16.h)
+        finally:
+            s16.close()
+        peak, src = hbm_peak()
+        kms = k16 / max(n16, 1)
+        ach = ALGO_BYTES["f16"] * nodes / (kms / 1e3) / 1e9
+        extra["f16_offset_store"] = {"value": round(world * nodes * args.steps / (ms16 / 1e3) / 1e6, 1),
+                                     "unit": "MLUPS", "fused_kernel_ms": round(kms, 4),
+                                     "achieved_gbs": round(ach, 1), "frac": round(ach / peak, 4),
+                                     "algo_bytes_per_node": ALGO_BYTES["f16"]}
+
+    peak, peak_src = hbm_peak()
+    kms = fused_ms / max(fused_n, 1)
+    achieved = ALGO_BYTES[args.storage] * nodes / (kms / 1e3) / 1e9
+    traffic = traffic_per_launch(args.workload, args.storage)
+    result = {
+        "metric": "VP-LBM MLUPS (node updates per second / 1e6)",
+        "value": round(value, 1),
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.storage != "f64" else "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name + f" MRT {args.storage.upper()}" + (" (populations as FP16 offsets)" if args.storage == "f16" else ""),
+                   "nx": w.nx, "ny": w.ny, "nodes": nodes, "storage": args.storage,
+                   "collision": w.collision, "re": w.re, "u_in": w.u_ref,
+                   "step": "mask update of the moving body + fused pull/penalize/collide/reduce kernel",
+                   "l2": "inputs larger than L2 (two population buffers of %.2f GB)" % (
+                       2 * 9 * nodes * {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}[args.storage] / 1e9),
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": round(e2e, 1), "unit": "MLUPS", "h2d_bytes_per_step": 704,
+                "d2h_bytes_per_step": 24,
+                "note": "public API per step: vplbm_step(1) then vplbm_forces (synchronizing read of F_x, F_y, mass)"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_source": f"{peak_src} copy bandwidth",
+                     "kernel": "fused_step_kernel<F32,MRT>" if args.storage == "f32" else f"fused_step_kernel<{args.storage},MRT>",
+                     "kernel_ms": round(kms, 4), "algo_bytes_per_node": ALGO_BYTES[args.storage],
+                     "algo_bytes_per_launch": ALGO_BYTES[args.storage] * nodes},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    result.update(extra)
+    if rank == 0 and not args.no_cpu_baseline:
+        mlups, desc, cores = oracle_sample(w, args.cpu_budget)
+        result["cpu_baseline"] = {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores,
+                                  "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = make_workload(args.workload, args.storage)
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(w, budget_s=2.0, max_steps=1)
+    desc, cores = "", 1
+    for _ in range(args.steps):
+        v, desc, cores = oracle_sample(w, budget_s=args.cpu_budget / max(args.steps, 1), max_steps=20)
+        vals.append(v)
+    value = statistics.median(vals)
+    out = {"impl": "reference", "metric": "VP-LBM MLUPS (node updates per second / 1e6)",
+           "value": round(value, 3), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name + f" MRT {args.storage.upper()}", "nx": w.nx, "ny": w.ny},
+           "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                            "sample": desc},
+           "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="moving-cylinder",
+                    choices=["moving-cylinder", "cylinder-re1000", "cylinder-re100"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f64"])
+    ap.add_argument("--no-compare-f16", dest="compare_f16", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        from paper_1812_05401_gb300 import build as B
+        if not B.up_to_date():
+            B.build()
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

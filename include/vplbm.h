@@ -1,0 +1,203 @@
+/*
+ * vplbm — C ABI of the GB300 (sm_103a) volume-penalization lattice Boltzmann
+ * solver (Benamour, Liberge, Beghein, arXiv 1812.05401).
+ *
+ * One solver holds one D2Q9 grid on one GPU. Each time step is one fused CUDA
+ * kernel that, for every node (fluid and solid alike, Section 2.2), pulls the
+ * nine populations, forms the density (Eq. density) and the implicit penalized
+ * velocity (Eq. vitesse_fluide_penalisation_1), evaluates the penalization
+ * force f = -rho (chi/eta)(u - u_s) (Eq. 261), collides with SRT + Guo
+ * forcing (Eqs. LatticeBoltz, Guo1) or MRT + Lu forcing (Eqs. equa_lbl_mrt,
+ * Guo2), writes the post-collision populations, and reduces in FP64 the force
+ * on the solids and the total mass. Moving rigid bodies get their staircase
+ * mask and solid velocity rewritten by a second kernel before each step.
+ *
+ * Conventions shared by every entry point:
+ *  - Node (i, j) sits at (x, y) = (i, j); lattice spacing and time step are 1.
+ *  - Host arrays are row-major doubles: fields [ny][nx], vectors [2][ny][nx]
+ *    (component, then row, then column), populations [9][ny][nx] with the
+ *    velocity order of Eq. vecteurs_D2Q9: 0 rest, 1..4 = E, N, W, S,
+ *    5..8 = NE, NW, SW, SE.
+ *  - The solver owns its device memory; the caller owns every pointer it
+ *    passes and every output buffer. Nothing is retained after a call returns.
+ *  - Calls are asynchronous on the solver's stream unless stated; a call that
+ *    returns data to the host synchronizes that stream.
+ *  - No C++ exception crosses the ABI. A failing call returns a status and
+ *    leaves a message for vplbm_last_error. VPLBM_ERR_CUDA is sticky: the
+ *    handle then only accepts vplbm_destroy.
+ *  - A handle is used by one host thread at a time.
+ *  - Before any call, an earlier call's kernels on the same stream have been
+ *    ordered: no extra synchronization is needed between calls.
+ */
+#ifndef VPLBM_H
+#define VPLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VPLBM_OK = 0,
+  VPLBM_ERR_INVALID = 1,  /* bad argument or configuration */
+  VPLBM_ERR_NOMEM = 2,    /* device allocation failed or budget exceeded */
+  VPLBM_ERR_CUDA = 3,     /* CUDA runtime error (sticky) */
+  VPLBM_ERR_DIVERGED = 4, /* a step produced rho <= 0 or a non-finite velocity */
+  VPLBM_ERR_TIMEOUT = 5,  /* a bounded device-side wait gave up */
+  VPLBM_ERR_STATE = 6     /* call not valid in the handle's current state */
+} vplbm_status;
+
+/* Collision operator. */
+enum { VPLBM_SRT = 0, /* BGK, Eq. LatticeBoltz with Guo forcing, Eq. Guo1 */
+       VPLBM_MRT = 1  /* Eq. equa_lbl_mrt with Lu forcing, Eq. Guo2 */ };
+
+/* Population storage. Arithmetic is FP64 for VPLBM_F64 and FP32 otherwise.
+ * The *_OFFSET forms store f_alpha - w_alpha in 16 bits (round to nearest
+ * even). */
+enum { VPLBM_F64 = 0, VPLBM_F32 = 1, VPLBM_F16_OFFSET = 2, VPLBM_BF16_OFFSET = 3 };
+
+/* Boundary conditions, applied inside the pull (streaming) of each step.
+ * x: PERIODIC, or INLET_OUTLET: a ghost column x = -1 held at f_eq(1, u_in)
+ *    (uniform velocity inlet) and a ghost column x = nx that repeats column
+ *    nx - 1 (zero-gradient outlet).
+ * y: PERIODIC, or FREE_SLIP: specular reflection off walls half-way beyond
+ *    rows 0 and ny - 1 (the symmetry planes of Section 3.3). */
+enum { VPLBM_BC_PERIODIC = 0, VPLBM_BC_INLET_OUTLET = 1, VPLBM_BC_FREE_SLIP = 2 };
+
+/* Largest number of rigid bodies a solver tracks. */
+#define VPLBM_MAX_BODIES 8
+
+/* Rigid circular body (staircase mask: a node is solid when its position lies
+ * in the closed disc, Section 3.2). Centre at step t:
+ *   (cx, cy) + (amp_x, amp_y) sin(2 pi t / period)   (period <= 0: fixed).
+ * Solid velocity u_s = d centre/dt + omega e_z x (x - centre).
+ * outside = 1 makes the solid the region r >= radius (an enclosing wall). */
+typedef struct {
+  double cx, cy, radius;
+  double amp_x, amp_y, period;
+  double omega;
+  int32_t outside;
+  int32_t reserved;
+} vplbm_body;
+
+typedef struct {
+  int32_t nx, ny;          /* nodes, each >= 1 */
+  int32_t collision;       /* VPLBM_SRT | VPLBM_MRT */
+  int32_t storage;         /* VPLBM_F64 | VPLBM_F32 | VPLBM_F16_OFFSET | VPLBM_BF16_OFFSET */
+  int32_t bc_x, bc_y;      /* see the boundary enum above */
+  int32_t use_rates;       /* MRT: 1 takes the nine rates from rates[] */
+  int32_t reduce_mass;     /* 1: record the total density of every step */
+  double tau;              /* relaxation time > 1/2; nu = (tau - 1/2)/3; MRT s_n = 1/tau */
+  double lambda;           /* MRT: s_q from Lambda = (1/s_n - 1/2)(1/s_q - 1/2) */
+  double eta;              /* penalization parameter, > 0 (paper: 1e-7) */
+  double u_in[2];          /* inlet velocity (bc_x = INLET_OUTLET) */
+  double rho0;             /* initial density */
+  double u0[2];            /* initial uniform velocity */
+  double body_force[2];    /* uniform force per unit mass g (f_tot = f_pen + rho g) */
+  double rates[9];         /* explicit MRT S diagonal when use_rates = 1 */
+  int32_t force_ring_len;  /* steps of (F_x, F_y, mass) kept on the device; >= 1 */
+  int32_t reserved;
+  void* stream;            /* cudaStream_t to run on, or NULL for a private stream */
+} vplbm_config;
+
+typedef struct vplbm_solver vplbm_solver;
+
+/* Fills cfg with defaults: SRT, FP32, periodic, tau 0.8, Lambda 3/16,
+ * eta 1e-7, rho0 1, mass reduction on, ring of 4096 steps. nx = ny = 0. */
+void vplbm_config_init(vplbm_config* cfg);
+
+/* Relaxation time for a reference speed u_ref, length l_ref and Reynolds
+ * number re: nu = u_ref l_ref / re, tau = 3 nu + 1/2 (Section 2.1.1). */
+double vplbm_tau_from_reynolds(double u_ref, double l_ref, double re);
+
+/* Device bytes a solver with this configuration allocates (admission). */
+size_t vplbm_footprint_bytes(const vplbm_config* cfg);
+
+/* Allocates the solver and sets the store to f*(0) = f_eq(rho0, u0) with an
+ * all-fluid mask. INVALID for nx or ny < 1, tau <= 1/2, eta <= 0, unknown
+ * enums; NOMEM if the device allocation fails. *out is NULL on failure. */
+vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out);
+
+/* Restarts from f*(0) = f_eq(rho0, u(x)) with u a host [2][ny][nx] array
+ * (NULL: the uniform u0). Resets the step counter and the force record. */
+vplbm_status vplbm_set_initial_velocity(vplbm_solver* s, const double* u);
+
+/* Static mask and solid velocity (Section 2.2, Eq. 261): chi [ny][nx] bytes,
+ * nonzero = solid; us [2][ny][nx] doubles or NULL (u_s = 0). on_device = 1:
+ * both are device pointers. Replaces any earlier static mask; bodies set with
+ * vplbm_set_bodies stay, and a static solid node takes precedence. */
+vplbm_status vplbm_set_mask_and_solid_velocity(vplbm_solver* s, const uint8_t* chi,
+                                               const double* us, int32_t on_device);
+
+/* Rigid bodies (host array of n <= VPLBM_MAX_BODIES; n = 0 removes them).
+ * The mask is rebuilt now and, when a body moves, over the region it sweeps
+ * before every step. Where bodies overlap the lower index wins. */
+vplbm_status vplbm_set_bodies(vplbm_solver* s, const vplbm_body* bodies, int32_t n);
+
+/* Advances n >= 0 time steps (asynchronous). Step t maps f*(t) to f*(t+1)
+ * with the mask and solid velocity of time t. */
+vplbm_status vplbm_step(vplbm_solver* s, int64_t n);
+
+/* Waits for the solver's stream and reports VPLBM_ERR_DIVERGED if any step
+ * since the last check produced rho <= 0 or a non-finite velocity. */
+vplbm_status vplbm_synchronize(vplbm_solver* s);
+
+/* Steps taken since creation or the last restart. */
+int64_t vplbm_step_count(const vplbm_solver* s);
+
+/* Density and implicit velocity that the next step computes (pulled
+ * populations of step t = vplbm_step_count). Outputs [ny][nx] doubles, host
+ * (on_device = 0, synchronizes) or device (on_device = 1) pointers. */
+vplbm_status vplbm_moments(vplbm_solver* s, double* rho, double* ux, double* uy,
+                           int32_t on_device);
+
+/* Post-collision store f*(t) as doubles [9][ny][nx] (host or device). */
+vplbm_status vplbm_populations(vplbm_solver* s, double* f, int32_t on_device);
+
+/* Replaces the store with f [9][ny][nx] (rounded to the storage type), keeping
+ * the step counter: loads a checkpoint or a test state. */
+vplbm_status vplbm_set_populations(vplbm_solver* s, const double* f, int32_t on_device);
+
+/* Mask the next step uses: [ny][nx] bytes, 0 fluid, nonzero solid (host). */
+vplbm_status vplbm_mask(vplbm_solver* s, uint8_t* chi);
+
+/* Per-step record since the previous call (synchronizes): F_x, F_y, the force
+ * the fluid exerts on all solid nodes (minus the sum of Eq. 261 over them,
+ * reduced in FP64), and the total density (0 if reduce_mass = 0). Returns up
+ * to cap entries, oldest first, in *count; if more than force_ring_len steps
+ * went unread the oldest were overwritten. Any pointer may be NULL. */
+vplbm_status vplbm_forces(vplbm_solver* s, double* fx, double* fy, double* mass,
+                          int64_t cap, int64_t* count);
+
+/* Advances n solvers by steps[i] steps each, batching them into grouped
+ * launches (one launch per time step per storage/collision class covering
+ * every solver still running). All solvers must share one stream. Results
+ * are bitwise identical to vplbm_step on each solver alone. */
+vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n,
+                              const int64_t* steps);
+
+/* Kernel launches this solver issued on its hot path (fused steps and mask
+ * updates) since creation. */
+int64_t vplbm_launch_count(const vplbm_solver* s);
+
+/* Timing of the fused step kernel: enable = 1 brackets each fused launch with
+ * CUDA events on the solver's stream. vplbm_fused_timing synchronizes and
+ * returns the summed device time (ms) and the number of timed launches since
+ * the last read. */
+vplbm_status vplbm_enable_timing(vplbm_solver* s, int32_t enable);
+vplbm_status vplbm_fused_timing(vplbm_solver* s, double* total_ms, int64_t* launches);
+
+/* Message for the last failing call on this handle (never NULL). */
+const char* vplbm_last_error(const vplbm_solver* s);
+const char* vplbm_status_string(vplbm_status st);
+
+/* Frees everything the solver owns. NULL is a no-op. Does not destroy a
+ * caller-supplied stream. */
+void vplbm_destroy(vplbm_solver* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VPLBM_H */

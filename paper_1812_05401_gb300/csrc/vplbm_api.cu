@@ -1,0 +1,961 @@
+// Host runtime of the VP-LBM solver: the C ABI of include/vplbm.h.
+//
+// A solver owns two population buffers (A/B ping-pong, [9][ny][pitch] in the
+// storage type, rows padded to 128 bytes), the mask ([ny][pitch] bytes), an
+// optional static solid-velocity field, the reduction scratch of the fused
+// step and a ring of per-step (F_x, F_y, sum rho) records. Each time step is
+// one launch of the fused kernel, preceded, when a body moves, by one launch
+// of the mask update over the region the bodies sweep.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "vplbm.h"
+#include "vplbm_launch.h"
+#include "vplbm_params.h"
+
+using namespace vplbm;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct BodyGeom {
+  double cx, cy, r2;
+  int outside;
+};
+struct BodyGeomSet {
+  BodyGeom b[kMaxBodies];
+  int n;
+};
+
+// Staircase mask of the rigid bodies over the box [x0, x0+w) x [y0, y0+h):
+// a node takes the index (1-based) of the first body containing it, 0 if none;
+// static solid nodes (255) are left alone. The in-disc test is evaluated with
+// explicitly rounded FP64 operations (no contraction), so that the integer
+// outcome is reproducible.
+__global__ void mask_update_kernel(uint8_t* mask, int pitch, int x0, int y0, int w, int h,
+                                   const __grid_constant__ BodyGeomSet g) {
+  const int x = x0 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = y0 + blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= x0 + w || y >= y0 + h) return;
+  const long long i = (long long)y * pitch + x;
+  const uint8_t m = mask[i];
+  if (m == kStaticSolid) return;
+  uint8_t v = 0;
+  for (int b = 0; b < g.n; ++b) {
+    const double dx = __dsub_rn(double(x), g.b[b].cx);
+    const double dy = __dsub_rn(double(y), g.b[b].cy);
+    const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    const bool in = g.b[b].outside ? (r2 >= g.b[b].r2) : (r2 <= g.b[b].r2);
+    if (in) {
+      v = uint8_t(b + 1);
+      break;
+    }
+  }
+  if (v != m) mask[i] = v;
+}
+
+// Static mask import: chi != 0 -> 255; a node that was statically solid and is
+// no longer becomes fluid (body nodes are then rebuilt by mask_update_kernel).
+__global__ void mask_import_kernel(uint8_t* mask, int pitch, int nx, int ny, const uint8_t* chi) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= nx || y >= ny) return;
+  const long long i = (long long)y * pitch + x;
+  const uint8_t c = chi[(long long)y * nx + x];
+  const uint8_t m = mask[i];
+  mask[i] = c ? kStaticSolid : (m == kStaticSolid ? uint8_t(0) : m);
+}
+
+__global__ void mask_export_kernel(const uint8_t* mask, int pitch, int nx, int ny, uint8_t* chi) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= nx || y >= ny) return;
+  chi[(long long)y * nx + x] = mask[(long long)y * pitch + x] ? 1 : 0;
+}
+
+// Static solid velocity [2][ny][nx] doubles -> {float2|double2}[ny][pitch].
+template <class T2>
+__global__ void us_import_kernel(T2* us, int pitch, int nx, int ny, const double* src) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= nx || y >= ny) return;
+  const long long o = (long long)y * nx + x;
+  const long long nn = (long long)nx * ny;
+  T2 v;
+  v.x = src[o];
+  v.y = src[nn + o];
+  us[(long long)y * pitch + x] = v;
+}
+
+dim3 grid2d(int w, int h, dim3 blk) {
+  return dim3((w + blk.x - 1) / blk.x, (h + blk.y - 1) / blk.y);
+}
+
+size_t element_size(int storage) {
+  switch (storage) {
+    case kF64: return 8;
+    case kF32: return 4;
+    default: return 2;
+  }
+}
+
+int row_pitch(int nx, int storage) {
+  const int per128 = int(128 / element_size(storage));
+  return ((nx + per128 - 1) / per128) * per128;
+}
+
+}  // namespace
+
+struct vplbm_solver {
+  vplbm_config cfg{};
+  int pitch = 0;
+  long long plane = 0;
+  size_t esize = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+
+  void* f[2] = {nullptr, nullptr};
+  int cur = 0;  // buffer holding f*(t)
+  uint8_t* mask = nullptr;
+  void* us = nullptr;
+  double* partials = nullptr;
+  double* group_partials = nullptr;
+  unsigned* counters = nullptr;
+  double* ring = nullptr;
+  int* flag = nullptr;
+
+  int tiles_x = 0, tiles_y = 0, n_tiles = 0, n_groups = 0;
+  StepParams base{};  // constants; src/dst/t/bodies filled per step
+
+  int64_t t = 0;
+  int64_t ring_read = 0;  // first step not yet returned by vplbm_forces
+  std::vector<vplbm_body> bodies;
+  bool moving = false;
+  int64_t mask_t = -1;  // time the moving bodies' mask reflects (-1: none)
+
+  int64_t launches = 0;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+  double timed_ms = 0.0;
+  int64_t timed_count = 0;
+
+  std::string err;
+  bool sticky = false;
+};
+
+namespace {
+
+vplbm_status fail(vplbm_solver* s, vplbm_status st, const std::string& msg) {
+  if (s) {
+    s->err = msg;
+    if (st == VPLBM_ERR_CUDA) s->sticky = true;
+  }
+  return st;
+}
+
+vplbm_status cuda_fail(vplbm_solver* s, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();  // not sticky in the runtime
+    return fail(s, VPLBM_ERR_NOMEM, m);
+  }
+  return fail(s, VPLBM_ERR_CUDA, m);
+}
+
+#define VP_CUDA(s, call)                                  \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail((s), e_, #call); \
+  } while (0)
+
+void body_state(const vplbm_body& b, int64_t t, BodyState* st) {
+  // centre(t) = c + amp sin(2 pi t / period), velocity = its time derivative
+  if (b.period > 0.0) {
+    const double ph = 2.0 * kPi * (double)t / b.period;
+    const double sn = std::sin(ph), co = std::cos(ph);
+    const double rate = 2.0 * kPi / b.period;
+    st->cx = b.cx + b.amp_x * sn;
+    st->cy = b.cy + b.amp_y * sn;
+    st->vx = b.amp_x * rate * co;
+    st->vy = b.amp_y * rate * co;
+  } else {
+    st->cx = b.cx;
+    st->cy = b.cy;
+    st->vx = 0.0;
+    st->vy = 0.0;
+  }
+  st->omega = b.omega;
+}
+
+struct Box {
+  int x0, y0, x1, y1;  // inclusive
+  bool empty() const { return x1 < x0 || y1 < y0; }
+};
+
+Box body_box(const vplbm_solver* s, const vplbm_body& b, int64_t t) {
+  if (b.outside) return Box{0, 0, s->cfg.nx - 1, s->cfg.ny - 1};
+  BodyState st;
+  body_state(b, t, &st);
+  Box r;
+  r.x0 = std::max(0, int(std::floor(st.cx - b.radius)) - 1);
+  r.x1 = std::min(s->cfg.nx - 1, int(std::ceil(st.cx + b.radius)) + 1);
+  r.y0 = std::max(0, int(std::floor(st.cy - b.radius)) - 1);
+  r.y1 = std::min(s->cfg.ny - 1, int(std::ceil(st.cy + b.radius)) + 1);
+  return r;
+}
+
+Box unite(Box a, Box b) {
+  if (a.empty()) return b;
+  if (b.empty()) return a;
+  return Box{std::min(a.x0, b.x0), std::min(a.y0, b.y0), std::max(a.x1, b.x1), std::max(a.y1, b.y1)};
+}
+
+vplbm_status launch_mask_update(vplbm_solver* s, Box box, int64_t t) {
+  if (box.empty()) return VPLBM_OK;
+  BodyGeomSet g{};
+  g.n = int(s->bodies.size());
+  for (int b = 0; b < g.n; ++b) {
+    BodyState st;
+    body_state(s->bodies[b], t, &st);
+    g.b[b].cx = st.cx;
+    g.b[b].cy = st.cy;
+    g.b[b].r2 = s->bodies[b].radius * s->bodies[b].radius;
+    g.b[b].outside = s->bodies[b].outside;
+  }
+  const dim3 blk(64, 4);
+  const int w = box.x1 - box.x0 + 1, h = box.y1 - box.y0 + 1;
+  mask_update_kernel<<<grid2d(w, h, blk), blk, 0, s->stream>>>(s->mask, s->pitch, box.x0, box.y0, w,
+                                                               h, g);
+  VP_CUDA(s, cudaGetLastError());
+  s->launches++;
+  return VPLBM_OK;
+}
+
+// Brings the mask of the moving bodies to time t (only the swept region).
+vplbm_status ensure_mask(vplbm_solver* s, int64_t t) {
+  if (!s->moving || s->mask_t == t) return VPLBM_OK;
+  Box box{0, 0, -1, -1};
+  for (const auto& b : s->bodies) {
+    if (b.period <= 0.0) continue;
+    box = unite(box, body_box(s, b, t));
+    if (s->mask_t >= 0) box = unite(box, body_box(s, b, s->mask_t));
+  }
+  if (s->mask_t < 0) box = Box{0, 0, s->cfg.nx - 1, s->cfg.ny - 1};
+  vplbm_status st = launch_mask_update(s, box, t);
+  if (st != VPLBM_OK) return st;
+  s->mask_t = t;
+  return VPLBM_OK;
+}
+
+void fill_bodies(const vplbm_solver* s, int64_t t, StepParams* p) {
+  p->n_bodies = int(s->bodies.size());
+  for (int b = 0; b < p->n_bodies; ++b) {
+    BodyState st;
+    body_state(s->bodies[b], t, &st);
+    const double v[5] = {st.cx, st.cy, st.vx, st.vy, st.omega};
+    for (int k = 0; k < 5; ++k) {
+      p->cd.body[b][k] = v[k];
+      p->cf.body[b][k] = float(v[k]);
+    }
+  }
+}
+
+// Float copies of the FP64 constants.
+void round_consts(StepParams* p) {
+  Consts<double>& d = p->cd;
+  Consts<float>& f = p->cf;
+  f.omega = float(d.omega);
+  f.srt_pre = float(d.srt_pre);
+  f.s_e = float(d.s_e);
+  f.s_eps = float(d.s_eps);
+  f.s_qx = float(d.s_qx);
+  f.s_qy = float(d.s_qy);
+  f.s_pxx = float(d.s_pxx);
+  f.s_pxy = float(d.s_pxy);
+  f.a_s = float(d.a_s);
+  f.kappa_s = float(d.kappa_s);
+  f.gx = float(d.gx);
+  f.gy = float(d.gy);
+  for (int a = 0; a < 9; ++a) f.heq_in[a] = float(d.heq_in[a]);
+}
+
+StepParams step_params(const vplbm_solver* s, int64_t t, int parity) {
+  StepParams p = s->base;
+  const int c = s->cur ^ parity;
+  p.src = s->f[c];
+  p.dst = s->f[c ^ 1];
+  p.t = t;
+  fill_bodies(s, t, &p);
+  return p;
+}
+
+cudaError_t launch_fused(const vplbm_solver* s, const StepParams& p) {
+  const int coll = s->cfg.collision;
+  switch (s->cfg.storage) {
+    case kF64: return launch_fused_f64(coll, p, s->stream);
+    case kF32: return launch_fused_f32(coll, p, s->stream);
+    case kF16: return launch_fused_f16(coll, p, s->stream);
+    default: return launch_fused_bf16(coll, p, s->stream);
+  }
+}
+
+cudaError_t launch_group(int storage, int coll, const StepParams* dp, const GroupTile* dt, int nb,
+                         long long k, cudaStream_t st) {
+  switch (storage) {
+    case kF64: return launch_group_f64(coll, dp, dt, nb, k, st);
+    case kF32: return launch_group_f32(coll, dp, dt, nb, k, st);
+    case kF16: return launch_group_f16(coll, dp, dt, nb, k, st);
+    default: return launch_group_bf16(coll, dp, dt, nb, k, st);
+  }
+}
+
+cudaError_t launch_moments(const vplbm_solver* s, const StepParams& p, double* r, double* ux, double* uy) {
+  switch (s->cfg.storage) {
+    case kF64: return launch_moments_f64(p, r, ux, uy, s->stream);
+    case kF32: return launch_moments_f32(p, r, ux, uy, s->stream);
+    case kF16: return launch_moments_f16(p, r, ux, uy, s->stream);
+    default: return launch_moments_bf16(p, r, ux, uy, s->stream);
+  }
+}
+
+cudaError_t launch_init(const vplbm_solver* s, const StepParams& p, void* dst, const double* u) {
+  const double r0 = s->cfg.rho0, ux = s->cfg.u0[0], uy = s->cfg.u0[1];
+  switch (s->cfg.storage) {
+    case kF64: return launch_init_f64(p, dst, u, r0, ux, uy, s->stream);
+    case kF32: return launch_init_f32(p, dst, u, r0, ux, uy, s->stream);
+    case kF16: return launch_init_f16(p, dst, u, r0, ux, uy, s->stream);
+    default: return launch_init_bf16(p, dst, u, r0, ux, uy, s->stream);
+  }
+}
+
+cudaError_t launch_export(const vplbm_solver* s, const StepParams& p, const void* src, double* f) {
+  switch (s->cfg.storage) {
+    case kF64: return launch_export_f64(p, src, f, s->stream);
+    case kF32: return launch_export_f32(p, src, f, s->stream);
+    case kF16: return launch_export_f16(p, src, f, s->stream);
+    default: return launch_export_bf16(p, src, f, s->stream);
+  }
+}
+
+cudaError_t launch_import(const vplbm_solver* s, const StepParams& p, void* dst, const double* f) {
+  switch (s->cfg.storage) {
+    case kF64: return launch_import_f64(p, dst, f, s->stream);
+    case kF32: return launch_import_f32(p, dst, f, s->stream);
+    case kF16: return launch_import_f16(p, dst, f, s->stream);
+    default: return launch_import_bf16(p, dst, f, s->stream);
+  }
+}
+
+vplbm_status validate(const vplbm_config* c, std::string* why) {
+  if (!c) return *why = "config is NULL", VPLBM_ERR_INVALID;
+  if (c->nx < 1 || c->ny < 1) return *why = "nx and ny must be >= 1", VPLBM_ERR_INVALID;
+  if ((long long)c->nx * c->ny > (1ll << 34)) return *why = "grid too large", VPLBM_ERR_INVALID;
+  if (c->collision != VPLBM_SRT && c->collision != VPLBM_MRT)
+    return *why = "unknown collision", VPLBM_ERR_INVALID;
+  if (c->storage < VPLBM_F64 || c->storage > VPLBM_BF16_OFFSET)
+    return *why = "unknown storage", VPLBM_ERR_INVALID;
+  if (c->bc_x != VPLBM_BC_PERIODIC && c->bc_x != VPLBM_BC_INLET_OUTLET)
+    return *why = "bc_x must be PERIODIC or INLET_OUTLET", VPLBM_ERR_INVALID;
+  if (c->bc_y != VPLBM_BC_PERIODIC && c->bc_y != VPLBM_BC_FREE_SLIP)
+    return *why = "bc_y must be PERIODIC or FREE_SLIP", VPLBM_ERR_INVALID;
+  if (!(c->tau > 0.5) || !std::isfinite(c->tau)) return *why = "tau must be > 1/2", VPLBM_ERR_INVALID;
+  if (!(c->eta > 0.0)) return *why = "eta must be > 0", VPLBM_ERR_INVALID;
+  if (c->collision == VPLBM_MRT && !c->use_rates && !(c->lambda > 0.0))
+    return *why = "lambda must be > 0", VPLBM_ERR_INVALID;
+  if (!(c->rho0 > 0.0)) return *why = "rho0 must be > 0", VPLBM_ERR_INVALID;
+  if (c->force_ring_len < 1) return *why = "force_ring_len must be >= 1", VPLBM_ERR_INVALID;
+  return VPLBM_OK;
+}
+
+void tiles_of(const vplbm_config* c, int* tx, int* ty, int* nt, int* ng) {
+  *tx = (c->nx + kTileX - 1) / kTileX;
+  *ty = (c->ny + kTileY - 1) / kTileY;
+  *nt = *tx * *ty;
+  *ng = (*nt + kGroup - 1) / kGroup;
+}
+
+// Equilibrium offset f_eq(rho, u) - w in FP64 (host; inlet ghost column).
+void heq_host(double rho, double ux, double uy, double out[9]) {
+  static const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  static const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  static const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                              1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+  const double uu = ux * ux + uy * uy;
+  for (int a = 0; a < 9; ++a) {
+    const double xu = ex[a] * ux + ey[a] * uy;
+    out[a] = w[a] * ((rho - 1.0) + rho * (3.0 * xu + 4.5 * xu * xu - 1.5 * uu));
+  }
+}
+
+vplbm_status check_usable(vplbm_solver* s) {
+  if (!s) return VPLBM_ERR_INVALID;
+  if (s->sticky) return VPLBM_ERR_CUDA;
+  return VPLBM_OK;
+}
+
+vplbm_status drain_timing(vplbm_solver* s) {
+  for (auto& pr : s->ev_pending) {
+    float ms = 0.f;
+    VP_CUDA(s, cudaEventSynchronize(pr.second));
+    VP_CUDA(s, cudaEventElapsedTime(&ms, pr.first, pr.second));
+    s->timed_ms += ms;
+    s->timed_count++;
+    s->ev_pool.push_back(pr.first);
+    s->ev_pool.push_back(pr.second);
+  }
+  s->ev_pending.clear();
+  return VPLBM_OK;
+}
+
+vplbm_status get_event(vplbm_solver* s, cudaEvent_t* e) {
+  if (!s->ev_pool.empty()) {
+    *e = s->ev_pool.back();
+    s->ev_pool.pop_back();
+    return VPLBM_OK;
+  }
+  VP_CUDA(s, cudaEventCreate(e));
+  return VPLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void vplbm_config_init(vplbm_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->collision = VPLBM_SRT;
+  c->storage = VPLBM_F32;
+  c->bc_x = VPLBM_BC_PERIODIC;
+  c->bc_y = VPLBM_BC_PERIODIC;
+  c->reduce_mass = 1;
+  c->tau = 0.8;
+  c->lambda = 3.0 / 16.0;
+  c->eta = 1e-7;
+  c->rho0 = 1.0;
+  c->force_ring_len = 4096;
+}
+
+double vplbm_tau_from_reynolds(double u_ref, double l_ref, double re) {
+  const double nu = u_ref * l_ref / re;  // kinematic viscosity
+  return 3.0 * nu + 0.5;                 // nu = c_s^2 (tau - 1/2), c_s^2 = 1/3
+}
+
+size_t vplbm_footprint_bytes(const vplbm_config* c) {
+  std::string why;
+  if (validate(c, &why) != VPLBM_OK) return 0;
+  int tx, ty, nt, ng;
+  tiles_of(c, &tx, &ty, &nt, &ng);
+  const size_t pitch = size_t(row_pitch(c->nx, c->storage));
+  const size_t plane = pitch * size_t(c->ny);
+  size_t b = 2 * 9 * plane * element_size(c->storage);  // A/B populations
+  b += plane;                                            // mask
+  b += 3 * sizeof(double) * (size_t(nt) + size_t(ng));   // reduction partials
+  b += sizeof(unsigned) * (size_t(ng) + 1);
+  b += 3 * sizeof(double) * size_t(c->force_ring_len);
+  return b;
+}
+
+vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
+  if (!out) return VPLBM_ERR_INVALID;
+  *out = nullptr;
+  std::string why;
+  vplbm_status v = validate(cfg, &why);
+  if (v != VPLBM_OK) {
+    std::fprintf(stderr, "vplbm_create: %s\n", why.c_str());
+    return v;
+  }
+  vplbm_solver* s = new (std::nothrow) vplbm_solver();
+  if (!s) return VPLBM_ERR_NOMEM;
+  s->cfg = *cfg;
+  s->esize = element_size(cfg->storage);
+  s->pitch = row_pitch(cfg->nx, cfg->storage);
+  s->plane = (long long)s->pitch * cfg->ny;
+  tiles_of(cfg, &s->tiles_x, &s->tiles_y, &s->n_tiles, &s->n_groups);
+
+  auto bail = [&](vplbm_status st) {
+    std::fprintf(stderr, "vplbm_create: %s\n", s->err.c_str());
+    vplbm_destroy(s);
+    return st;
+  };
+  vplbm_status st = VPLBM_OK;
+  if (cfg->stream) {
+    s->stream = static_cast<cudaStream_t>(cfg->stream);
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(s, e, "cudaStreamCreate"));
+    s->own_stream = true;
+  }
+  const size_t pop = size_t(9) * size_t(s->plane) * s->esize;
+  cudaError_t e = cudaSuccess;
+  if ((e = cudaMalloc(&s->f[0], pop)) != cudaSuccess ||
+      (e = cudaMalloc(&s->f[1], pop)) != cudaSuccess ||
+      (e = cudaMalloc(reinterpret_cast<void**>(&s->mask), size_t(s->plane))) != cudaSuccess ||
+      (e = cudaMalloc(reinterpret_cast<void**>(&s->partials), 3 * sizeof(double) * s->n_tiles)) != cudaSuccess ||
+      (e = cudaMalloc(reinterpret_cast<void**>(&s->group_partials), 3 * sizeof(double) * s->n_groups)) != cudaSuccess ||
+      (e = cudaMalloc(reinterpret_cast<void**>(&s->counters), sizeof(unsigned) * (s->n_groups + 1))) != cudaSuccess ||
+      (e = cudaMalloc(reinterpret_cast<void**>(&s->ring), 3 * sizeof(double) * cfg->force_ring_len)) != cudaSuccess ||
+      (e = cudaMalloc(reinterpret_cast<void**>(&s->flag), sizeof(int))) != cudaSuccess) {
+    return bail(cuda_fail(s, e, "cudaMalloc"));
+  }
+  if ((e = cudaMemsetAsync(s->mask, 0, size_t(s->plane), s->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(s->counters, 0, sizeof(unsigned) * (s->n_groups + 1), s->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(s->ring, 0, 3 * sizeof(double) * cfg->force_ring_len, s->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(s->f[0], 0, pop, s->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(s->f[1], 0, pop, s->stream)) != cudaSuccess) {
+    return bail(cuda_fail(s, e, "cudaMemsetAsync"));
+  }
+
+  StepParams& p = s->base;
+  std::memset(&p, 0, sizeof(p));
+  p.mask = s->mask;
+  p.us = nullptr;
+  p.nx = cfg->nx;
+  p.ny = cfg->ny;
+  p.pitch = s->pitch;
+  p.plane = s->plane;
+  p.bc_x = cfg->bc_x;
+  p.bc_y = cfg->bc_y;
+  p.tiles_x = s->tiles_x;
+  p.n_tiles = s->n_tiles;
+  Consts<double>& cd = p.cd;
+  cd.omega = 1.0 / cfg->tau;
+  cd.srt_pre = 1.0 - 1.0 / (2.0 * cfg->tau);
+  if (cfg->use_rates) {
+    cd.s_e = cfg->rates[1];
+    cd.s_eps = cfg->rates[2];
+    cd.s_qx = cfg->rates[4];
+    cd.s_qy = cfg->rates[6];
+    cd.s_pxx = cfg->rates[7];
+    cd.s_pxy = cfg->rates[8];
+  } else {
+    // S = diag(0, s_n, s_n, 0, s_q, 0, s_q, s_n, s_n), s_n = 1/tau,
+    // Lambda = (1/s_n - 1/2)(1/s_q - 1/2)
+    const double sn = 1.0 / cfg->tau;
+    const double sq = 1.0 / (0.5 + cfg->lambda / (1.0 / sn - 0.5));
+    cd.s_e = sn;
+    cd.s_eps = sn;
+    cd.s_qx = sq;
+    cd.s_qy = sq;
+    cd.s_pxx = sn;
+    cd.s_pxy = sn;
+  }
+  cd.a_s = 0.5 / cfg->eta;
+  cd.kappa_s = (1.0 / cfg->eta) / (1.0 + 0.5 / cfg->eta);
+  cd.gx = cfg->body_force[0];
+  cd.gy = cfg->body_force[1];
+  heq_host(1.0, cfg->u_in[0], cfg->u_in[1], cd.heq_in);
+  round_consts(&p);
+  p.partials = s->partials;
+  p.group_partials = s->group_partials;
+  p.counters = s->counters;
+  p.ring = s->ring;
+  p.flag = s->flag;
+  p.ring_len = cfg->force_ring_len;
+  p.reduce_mass = cfg->reduce_mass ? 1 : 0;
+
+  if ((st = vplbm_set_initial_velocity(s, nullptr)) != VPLBM_OK) return bail(st);
+  *out = s;
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_set_initial_velocity(vplbm_solver* s, const double* u) {
+  vplbm_status st = check_usable(s);
+  if (st != VPLBM_OK) return st;
+  double* du = nullptr;
+  const size_t n = size_t(s->cfg.nx) * size_t(s->cfg.ny);
+  if (u) {
+    VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&du), 2 * n * sizeof(double), s->stream));
+    VP_CUDA(s, cudaMemcpyAsync(du, u, 2 * n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  }
+  s->cur = 0;
+  VP_CUDA(s, launch_init(s, s->base, s->f[0], du));
+  if (du) VP_CUDA(s, cudaFreeAsync(du, s->stream));
+  s->t = 0;
+  s->ring_read = 0;
+  VP_CUDA(s, cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream));
+  VP_CUDA(s, cudaMemsetAsync(s->ring, 0, 3 * sizeof(double) * s->cfg.force_ring_len, s->stream));
+  if (s->moving) s->mask_t = -1;
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_set_mask_and_solid_velocity(vplbm_solver* s, const uint8_t* chi, const double* us,
+                                               int32_t on_device) {
+  vplbm_status st = check_usable(s);
+  if (st != VPLBM_OK) return st;
+  if (!chi) return fail(s, VPLBM_ERR_INVALID, "chi is NULL");
+  const int nx = s->cfg.nx, ny = s->cfg.ny;
+  const size_t n = size_t(nx) * ny;
+  const uint8_t* dchi = chi;
+  const double* dus = us;
+  uint8_t* tchi = nullptr;
+  double* tus = nullptr;
+  if (!on_device) {
+    VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&tchi), n, s->stream));
+    VP_CUDA(s, cudaMemcpyAsync(tchi, chi, n, cudaMemcpyHostToDevice, s->stream));
+    dchi = tchi;
+    if (us) {
+      VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&tus), 2 * n * sizeof(double), s->stream));
+      VP_CUDA(s, cudaMemcpyAsync(tus, us, 2 * n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+      dus = tus;
+    }
+  }
+  const dim3 blk(64, 4);
+  mask_import_kernel<<<grid2d(nx, ny, blk), blk, 0, s->stream>>>(s->mask, s->pitch, nx, ny, dchi);
+  VP_CUDA(s, cudaGetLastError());
+  if (dus) {
+    const size_t vs = s->cfg.storage == kF64 ? sizeof(double2) : sizeof(float2);
+    if (!s->us) VP_CUDA(s, cudaMalloc(&s->us, vs * size_t(s->plane)));
+    if (s->cfg.storage == kF64)
+      us_import_kernel<double2><<<grid2d(nx, ny, blk), blk, 0, s->stream>>>(
+          static_cast<double2*>(s->us), s->pitch, nx, ny, dus);
+    else
+      us_import_kernel<float2><<<grid2d(nx, ny, blk), blk, 0, s->stream>>>(
+          static_cast<float2*>(s->us), s->pitch, nx, ny, dus);
+    VP_CUDA(s, cudaGetLastError());
+    s->base.us = s->us;
+  } else {
+    s->base.us = nullptr;
+  }
+  if (tchi) VP_CUDA(s, cudaFreeAsync(tchi, s->stream));
+  if (tus) VP_CUDA(s, cudaFreeAsync(tus, s->stream));
+  // Rebuild the bodies where the static layer changed.
+  if (!s->bodies.empty()) {
+    st = launch_mask_update(s, Box{0, 0, nx - 1, ny - 1}, s->t);
+    if (st != VPLBM_OK) return st;
+    s->mask_t = s->moving ? s->t : -1;
+  }
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_set_bodies(vplbm_solver* s, const vplbm_body* bodies, int32_t n) {
+  vplbm_status st = check_usable(s);
+  if (st != VPLBM_OK) return st;
+  if (n < 0 || n > kMaxBodies || (n > 0 && !bodies))
+    return fail(s, VPLBM_ERR_INVALID, "need 0 <= n <= VPLBM_MAX_BODIES bodies");
+  for (int i = 0; i < n; ++i)
+    if (!(bodies[i].radius >= 0.0) || !std::isfinite(bodies[i].cx) || !std::isfinite(bodies[i].cy))
+      return fail(s, VPLBM_ERR_INVALID, "body radius must be >= 0 and centre finite");
+  s->bodies.assign(bodies, bodies + n);
+  s->moving = false;
+  for (const auto& b : s->bodies)
+    if (b.period > 0.0 && (b.amp_x != 0.0 || b.amp_y != 0.0)) s->moving = true;
+  // Full rebuild at the current time (also clears removed bodies).
+  st = launch_mask_update(s, Box{0, 0, s->cfg.nx - 1, s->cfg.ny - 1}, s->t);
+  if (st != VPLBM_OK) return st;
+  s->mask_t = s->moving ? s->t : -1;
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_step(vplbm_solver* s, int64_t n) {
+  vplbm_status st = check_usable(s);
+  if (st != VPLBM_OK) return st;
+  if (n < 0) return fail(s, VPLBM_ERR_INVALID, "n must be >= 0");
+  for (int64_t k = 0; k < n; ++k) {
+    if ((st = ensure_mask(s, s->t)) != VPLBM_OK) return st;
+    const StepParams p = step_params(s, s->t, 0);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (s->timing) {
+      if ((st = get_event(s, &e0)) != VPLBM_OK) return st;
+      if ((st = get_event(s, &e1)) != VPLBM_OK) return st;
+      VP_CUDA(s, cudaEventRecord(e0, s->stream));
+    }
+    VP_CUDA(s, launch_fused(s, p));
+    if (s->timing) {
+      VP_CUDA(s, cudaEventRecord(e1, s->stream));
+      s->ev_pending.emplace_back(e0, e1);
+    }
+    s->launches++;
+    s->cur ^= 1;
+    s->t++;
+  }
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_synchronize(vplbm_solver* s) {
+  vplbm_status st = check_usable(s);
+  if (st != VPLBM_OK) return st;
+  int flag = 0;
+  VP_CUDA(s, cudaMemcpyAsync(&flag, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  VP_CUDA(s, cudaStreamSynchronize(s->stream));
+  if (flag) {
+    VP_CUDA(s, cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream));
+    return fail(s, VPLBM_ERR_DIVERGED, "a step produced rho <= 0 or a non-finite velocity");
+  }
+  return VPLBM_OK;
+}
+
+int64_t vplbm_step_count(const vplbm_solver* s) { return s ? s->t : -1; }
+
+vplbm_status vplbm_moments(vplbm_solver* s, double* rho, double* ux, double* uy, int32_t on_device) {
+  vplbm_status st = check_usable(s);
+  if (st != VPLBM_OK) return st;
+  if (!rho || !ux || !uy) return fail(s, VPLBM_ERR_INVALID, "output pointer is NULL");
+  if ((st = ensure_mask(s, s->t)) != VPLBM_OK) return st;
+  const size_t n = size_t(s->cfg.nx) * s->cfg.ny;
+  StepParams p = step_params(s, s->t, 0);
+  if (on_device) {
+    VP_CUDA(s, launch_moments(s, p, rho, ux, uy));
+    return VPLBM_OK;
+  }
+  double* d = nullptr;
+  VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&d), 3 * n * sizeof(double), s->stream));
+  VP_CUDA(s, launch_moments(s, p, d, d + n, d + 2 * n));
+  VP_CUDA(s, cudaMemcpyAsync(rho, d, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  VP_CUDA(s, cudaMemcpyAsync(ux, d + n, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  VP_CUDA(s, cudaMemcpyAsync(uy, d + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  VP_CUDA(s, cudaFreeAsync(d, s->stream));
+  VP_CUDA(s, cudaStreamSynchronize(s->stream));
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_populations(vplbm_solver* s, double* f, int32_t on_device) {
+  vplbm_status st = check_usable(s);
+  if (st != VPLBM_OK) return st;
+  if (!f) return fail(s, VPLBM_ERR_INVALID, "output pointer is NULL");
+  const size_t n = size_t(s->cfg.nx) * s->cfg.ny;
+  if (on_device) {
+    VP_CUDA(s, launch_export(s, s->base, s->f[s->cur], f));
+    return VPLBM_OK;
+  }
+  double* d = nullptr;
+  VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&d), 9 * n * sizeof(double), s->stream));
+  VP_CUDA(s, launch_export(s, s->base, s->f[s->cur], d));
+  VP_CUDA(s, cudaMemcpyAsync(f, d, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  VP_CUDA(s, cudaFreeAsync(d, s->stream));
+  VP_CUDA(s, cudaStreamSynchronize(s->stream));
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_set_populations(vplbm_solver* s, const double* f, int32_t on_device) {
+  vplbm_status st = check_usable(s);
+  if (st != VPLBM_OK) return st;
+  if (!f) return fail(s, VPLBM_ERR_INVALID, "input pointer is NULL");
+  const size_t n = size_t(s->cfg.nx) * s->cfg.ny;
+  if (on_device) {
+    VP_CUDA(s, launch_import(s, s->base, s->f[s->cur], f));
+    return VPLBM_OK;
+  }
+  double* d = nullptr;
+  VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&d), 9 * n * sizeof(double), s->stream));
+  VP_CUDA(s, cudaMemcpyAsync(d, f, 9 * n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  VP_CUDA(s, launch_import(s, s->base, s->f[s->cur], d));
+  VP_CUDA(s, cudaFreeAsync(d, s->stream));
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_mask(vplbm_solver* s, uint8_t* chi) {
+  vplbm_status st = check_usable(s);
+  if (st != VPLBM_OK) return st;
+  if (!chi) return fail(s, VPLBM_ERR_INVALID, "output pointer is NULL");
+  if ((st = ensure_mask(s, s->t)) != VPLBM_OK) return st;
+  const int nx = s->cfg.nx, ny = s->cfg.ny;
+  const size_t n = size_t(nx) * ny;
+  uint8_t* d = nullptr;
+  VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&d), n, s->stream));
+  const dim3 blk(64, 4);
+  mask_export_kernel<<<grid2d(nx, ny, blk), blk, 0, s->stream>>>(s->mask, s->pitch, nx, ny, d);
+  VP_CUDA(s, cudaGetLastError());
+  VP_CUDA(s, cudaMemcpyAsync(chi, d, n, cudaMemcpyDeviceToHost, s->stream));
+  VP_CUDA(s, cudaFreeAsync(d, s->stream));
+  VP_CUDA(s, cudaStreamSynchronize(s->stream));
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_forces(vplbm_solver* s, double* fx, double* fy, double* mass, int64_t cap,
+                          int64_t* count) {
+  vplbm_status st = check_usable(s);
+  if (st != VPLBM_OK) return st;
+  if (count) *count = 0;
+  if (cap < 0) return fail(s, VPLBM_ERR_INVALID, "cap must be >= 0");
+  const int64_t L = s->cfg.force_ring_len;
+  const int64_t k = std::min(std::min(s->t - s->ring_read, L), cap);
+  std::vector<double> host(3 * size_t(std::max<int64_t>(k, 1)));
+  // records of steps t-k .. t-1, at ring slots (step % L): at most two runs
+  int64_t done = 0;
+  while (done < k) {
+    const int64_t step = s->t - k + done;
+    const int64_t slot = step % L;
+    const int64_t run = std::min(k - done, L - slot);
+    VP_CUDA(s, cudaMemcpyAsync(host.data() + 3 * done, s->ring + 3 * slot, 3 * sizeof(double) * run,
+                               cudaMemcpyDeviceToHost, s->stream));
+    done += run;
+  }
+  VP_CUDA(s, cudaStreamSynchronize(s->stream));
+  for (int64_t i = 0; i < k; ++i) {
+    if (fx) fx[i] = host[3 * i + 0];
+    if (fy) fy[i] = host[3 * i + 1];
+    if (mass) mass[i] = host[3 * i + 2];
+  }
+  if (count) *count = k;
+  s->ring_read = s->t;
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int64_t* steps) {
+  if (n < 0 || (n > 0 && (!solvers || !steps))) return VPLBM_ERR_INVALID;
+  if (n == 0) return VPLBM_OK;
+  cudaStream_t stream = solvers[0]->stream;
+  int64_t max_steps = 0;
+  for (int i = 0; i < n; ++i) {
+    vplbm_solver* s = solvers[i];
+    vplbm_status st = check_usable(s);
+    if (st != VPLBM_OK) return st;
+    if (s->stream != stream) return fail(s, VPLBM_ERR_INVALID, "group solvers must share a stream");
+    if (steps[i] < 0) return fail(s, VPLBM_ERR_INVALID, "steps must be >= 0");
+    for (int j = 0; j < i; ++j)
+      if (solvers[j] == s) return fail(s, VPLBM_ERR_INVALID, "a solver appears twice in the group");
+    max_steps = std::max(max_steps, steps[i]);
+  }
+  vplbm_solver* s0 = solvers[0];
+  // Solvers with moving bodies need a mask update between steps: step them
+  // alone, interleaved with the grouped launches of the others.
+  struct Member {
+    int idx;
+    int64_t steps;
+  };
+  std::vector<Member> classes[4][2];
+  std::vector<int> moving;
+  for (int i = 0; i < n; ++i) {
+    if (solvers[i]->moving) {
+      moving.push_back(i);
+      continue;
+    }
+    classes[solvers[i]->cfg.storage][solvers[i]->cfg.collision].push_back({i, steps[i]});
+  }
+  struct Plan {
+    int storage, coll;
+    StepParams* d_params;
+    GroupTile* d_table;
+    std::vector<int64_t> prefix_steps;  // steps of the j-th member (descending)
+    std::vector<int> prefix_tiles;      // tiles of members 0..j
+  };
+  std::vector<Plan> plans;
+  for (int sg = 0; sg < 4; ++sg) {
+    for (int c = 0; c < 2; ++c) {
+      auto& mem = classes[sg][c];
+      if (mem.empty()) continue;
+      std::stable_sort(mem.begin(), mem.end(),
+                       [](const Member& a, const Member& b) { return a.steps > b.steps; });
+      std::vector<StepParams> hp;
+      std::vector<GroupTile> ht;
+      Plan pl;
+      pl.storage = sg;
+      pl.coll = c;
+      for (size_t j = 0; j < mem.size(); ++j) {
+        vplbm_solver* s = solvers[mem[j].idx];
+        hp.push_back(step_params(s, s->t, 0));
+        hp.push_back(step_params(s, s->t, 1));
+        for (int tile = 0; tile < s->n_tiles; ++tile) ht.push_back(GroupTile{int(j), tile});
+        pl.prefix_steps.push_back(mem[j].steps);
+        pl.prefix_tiles.push_back(int(ht.size()));
+      }
+      VP_CUDA(s0, cudaMallocAsync(reinterpret_cast<void**>(&pl.d_params), hp.size() * sizeof(StepParams), stream));
+      VP_CUDA(s0, cudaMallocAsync(reinterpret_cast<void**>(&pl.d_table), ht.size() * sizeof(GroupTile), stream));
+      VP_CUDA(s0, cudaMemcpyAsync(pl.d_params, hp.data(), hp.size() * sizeof(StepParams),
+                                  cudaMemcpyHostToDevice, stream));
+      VP_CUDA(s0, cudaMemcpyAsync(pl.d_table, ht.data(), ht.size() * sizeof(GroupTile),
+                                  cudaMemcpyHostToDevice, stream));
+      plans.push_back(std::move(pl));
+    }
+  }
+  for (int64_t k = 0; k < max_steps; ++k) {
+    for (auto& pl : plans) {
+      // members are sorted by steps, so the ones still running are a prefix
+      int active = 0;
+      while (active < int(pl.prefix_steps.size()) && pl.prefix_steps[active] > k) ++active;
+      if (active == 0) continue;
+      const int nb = pl.prefix_tiles[active - 1];
+      VP_CUDA(s0, launch_group(pl.storage, pl.coll, pl.d_params, pl.d_table, nb, k, stream));
+    }
+    for (int i : moving) {
+      if (steps[i] > k) {
+        vplbm_status st = vplbm_step(solvers[i], 1);
+        if (st != VPLBM_OK) return st;
+      }
+    }
+  }
+  for (auto& pl : plans) {
+    VP_CUDA(s0, cudaFreeAsync(pl.d_params, stream));
+    VP_CUDA(s0, cudaFreeAsync(pl.d_table, stream));
+  }
+  for (int i = 0; i < n; ++i) {
+    vplbm_solver* s = solvers[i];
+    if (s->moving) continue;
+    s->launches += steps[i];  // one grouped launch per step covers this solver
+    s->cur ^= int(steps[i] & 1);
+    s->t += steps[i];
+  }
+  return VPLBM_OK;
+}
+
+int64_t vplbm_launch_count(const vplbm_solver* s) { return s ? s->launches : -1; }
+
+vplbm_status vplbm_enable_timing(vplbm_solver* s, int32_t enable) {
+  vplbm_status st = check_usable(s);
+  if (st != VPLBM_OK) return st;
+  s->timing = enable != 0;
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_fused_timing(vplbm_solver* s, double* total_ms, int64_t* launches) {
+  vplbm_status st = check_usable(s);
+  if (st != VPLBM_OK) return st;
+  if ((st = drain_timing(s)) != VPLBM_OK) return st;
+  if (total_ms) *total_ms = s->timed_ms;
+  if (launches) *launches = s->timed_count;
+  s->timed_ms = 0.0;
+  s->timed_count = 0;
+  return VPLBM_OK;
+}
+
+const char* vplbm_last_error(const vplbm_solver* s) {
+  if (!s) return "no solver";
+  return s->err.c_str();
+}
+
+const char* vplbm_status_string(vplbm_status st) {
+  switch (st) {
+    case VPLBM_OK: return "ok";
+    case VPLBM_ERR_INVALID: return "invalid argument";
+    case VPLBM_ERR_NOMEM: return "out of device memory";
+    case VPLBM_ERR_CUDA: return "CUDA error";
+    case VPLBM_ERR_DIVERGED: return "diverged";
+    case VPLBM_ERR_TIMEOUT: return "timeout";
+    case VPLBM_ERR_STATE: return "invalid state";
+  }
+  return "unknown status";
+}
+
+void vplbm_destroy(vplbm_solver* s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  for (auto& pr : s->ev_pending) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  for (auto e : s->ev_pool) cudaEventDestroy(e);
+  cudaFree(s->f[0]);
+  cudaFree(s->f[1]);
+  cudaFree(s->mask);
+  cudaFree(s->us);
+  cudaFree(s->partials);
+  cudaFree(s->group_partials);
+  cudaFree(s->counters);
+  cudaFree(s->ring);
+  cudaFree(s->flag);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,592 @@
+// Device side of the VP-LBM solver: storage traits, the fused
+// stream-penalize-collide-reduce step, the mask update for moving bodies, and
+// the initialisation / read-back kernels. Included by one translation unit per
+// storage type (kernels_<storage>.cu).
+//
+// Arithmetic form. The kernel works on offsets h_alpha = f_alpha - w_alpha
+// (w: the D2Q9 weights). Equilibrium, forcing and both collision operators are
+// affine in f with the rest state w as a fixed point, so colliding h is the
+// same operation, and it keeps the small deviations from the rest state out of
+// the rounding of numbers near w. For FP32 storage h is formed exactly
+// (Sterbenz) when f lies within a factor two of w.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vplbm_params.h"
+
+namespace vplbm {
+
+// D2Q9 velocity set in the order of Eq. vecteurs_D2Q9.
+__device__ __host__ constexpr int cx(int a) {
+  return a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0);
+}
+__device__ __host__ constexpr int cy(int a) {
+  return a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0);
+}
+// Direction with the same x and opposite y velocity (free-slip reflection).
+__device__ __host__ constexpr int mirror_y(int a) {
+  return a == 2 ? 4 : a == 4 ? 2 : a == 5 ? 8 : a == 8 ? 5 : a == 6 ? 7 : a == 7 ? 6 : a;
+}
+// Weights, Eq. anex_eq19.
+template <class T>
+__device__ __forceinline__ constexpr T wgt(int a) {
+  return a == 0 ? T(4.0 / 9.0) : (a <= 4 ? T(1.0 / 9.0) : T(1.0 / 36.0));
+}
+
+// ---------------------------------------------------------------------------
+// Storage traits: E is the element in HBM, T the arithmetic type.
+// ---------------------------------------------------------------------------
+template <int S> struct Store;
+template <> struct Store<kF64> {
+  using E = double;
+  using T = double;
+  static __device__ __forceinline__ T load(const E* p, int a) { return __ldg(p) - wgt<T>(a); }
+  static __device__ __forceinline__ void store(E* p, T h, int a) { *p = h + wgt<T>(a); }
+  static __device__ __forceinline__ double to_f64(const E* p, int) { return *p; }
+  static __device__ __forceinline__ void from_f64(E* p, double f, int) { *p = f; }
+};
+template <> struct Store<kF32> {
+  using E = float;
+  using T = float;
+  static __device__ __forceinline__ T load(const E* p, int a) { return __ldg(p) - wgt<T>(a); }
+  static __device__ __forceinline__ void store(E* p, T h, int a) { *p = h + wgt<T>(a); }
+  static __device__ __forceinline__ double to_f64(const E* p, int) { return double(*p); }
+  static __device__ __forceinline__ void from_f64(E* p, double f, int) { *p = float(f); }
+};
+template <> struct Store<kF16> {
+  using E = __half;
+  using T = float;
+  static __device__ __forceinline__ T load(const E* p, int) { return __half2float(__ldg(p)); }
+  static __device__ __forceinline__ void store(E* p, T h, int) { *p = __float2half_rn(h); }
+  static __device__ __forceinline__ double to_f64(const E* p, int a) {
+    return wgt<double>(a) + double(__half2float(*p));
+  }
+  static __device__ __forceinline__ void from_f64(E* p, double f, int a) {
+    *p = __double2half(f - wgt<double>(a));
+  }
+};
+template <> struct Store<kBF16> {
+  using E = __nv_bfloat16;
+  using T = float;
+  static __device__ __forceinline__ T load(const E* p, int) { return __bfloat162float(__ldg(p)); }
+  static __device__ __forceinline__ void store(E* p, T h, int) { *p = __float2bfloat16_rn(h); }
+  static __device__ __forceinline__ double to_f64(const E* p, int a) {
+    return wgt<double>(a) + double(__bfloat162float(*p));
+  }
+  static __device__ __forceinline__ void from_f64(E* p, double f, int a) {
+    *p = __double2bfloat16(f - wgt<double>(a));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Pull with boundary conditions (streaming, left-hand side of Eq. LatticeBoltz)
+// ---------------------------------------------------------------------------
+template <class S, int A>
+__device__ __forceinline__ typename S::T pull_bc(const StepParams& p, const typename S::E* src,
+                                                 int x, int y) {
+  using T = typename S::T;
+  int as = A;
+  int xs = x - cx(A);
+  int ys = y - cy(A);
+  if (ys < 0 || ys >= p.ny) {
+    if (p.bc_y == kBcPeriodic) {
+      ys = ys < 0 ? ys + p.ny : ys - p.ny;
+    } else {  // free slip: the mirror of the population that left this row
+      as = mirror_y(A);
+      ys = y;
+    }
+  }
+  if (xs < 0 || xs >= p.nx) {
+    if (p.bc_x == kBcPeriodic) {
+      xs = xs < 0 ? xs + p.nx : xs - p.nx;
+    } else if (xs < 0) {  // inlet ghost column at f_eq(1, u_in)
+      const Consts<T>& c = consts<T>(p);
+      return as == A ? c.heq_in[A] : c.heq_in[mirror_y(A)];
+    } else {  // zero-gradient outlet ghost column
+      xs = p.nx - 1;
+    }
+  }
+  return S::load(src + (long long)as * p.plane + (long long)ys * p.pitch + xs, A);
+}
+
+template <class S, int A>
+__device__ __forceinline__ typename S::T pull_interior(const StepParams& p,
+                                                       const typename S::E* src, long long i) {
+  return S::load(src + (long long)A * p.plane + i - cx(A) - (long long)cy(A) * p.pitch, A);
+}
+
+template <class S>
+__device__ __forceinline__ void pull_node(const StepParams& p, const typename S::E* src,
+                                          bool interior, int x, int y, typename S::T h[9]) {
+  if (interior) {
+    const long long i = (long long)y * p.pitch + x;
+    h[0] = pull_interior<S, 0>(p, src, i);
+    h[1] = pull_interior<S, 1>(p, src, i);
+    h[2] = pull_interior<S, 2>(p, src, i);
+    h[3] = pull_interior<S, 3>(p, src, i);
+    h[4] = pull_interior<S, 4>(p, src, i);
+    h[5] = pull_interior<S, 5>(p, src, i);
+    h[6] = pull_interior<S, 6>(p, src, i);
+    h[7] = pull_interior<S, 7>(p, src, i);
+    h[8] = pull_interior<S, 8>(p, src, i);
+  } else {
+    h[0] = pull_bc<S, 0>(p, src, x, y);
+    h[1] = pull_bc<S, 1>(p, src, x, y);
+    h[2] = pull_bc<S, 2>(p, src, x, y);
+    h[3] = pull_bc<S, 3>(p, src, x, y);
+    h[4] = pull_bc<S, 4>(p, src, x, y);
+    h[5] = pull_bc<S, 5>(p, src, x, y);
+    h[6] = pull_bc<S, 6>(p, src, x, y);
+    h[7] = pull_bc<S, 7>(p, src, x, y);
+    h[8] = pull_bc<S, 8>(p, src, x, y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Density, implicit velocity and penalization force of one node
+// (Eqs. density, velocity, 261 and 276).
+//   d = j + rho g / 2 - rho u_s,  u = u_s + d / (rho (1 + a)),
+//   f_pen = -kappa d,  a = chi/(2 eta),  kappa = (chi/eta)/(1 + a).
+// This is Eq. 276 rewritten so that neither u - u_s nor a rho u_s appear:
+// the 1/eta factor never multiplies a rounding error.
+// ---------------------------------------------------------------------------
+template <class T>
+struct Macro {
+  T drho, rho, ux, uy, fpx, fpy, Fx, Fy;
+};
+
+template <class T>
+__device__ __forceinline__ void solid_velocity(const StepParams& p, uint8_t m, int x, int y,
+                                               T& usx, T& usy) {
+  if (m == kStaticSolid) {
+    if (p.us) {
+      const long long i = (long long)y * p.pitch + x;
+      if (sizeof(T) == 8) {
+        const double2 v = reinterpret_cast<const double2*>(p.us)[i];
+        usx = T(v.x);
+        usy = T(v.y);
+      } else {
+        const float2 v = reinterpret_cast<const float2*>(p.us)[i];
+        usx = T(v.x);
+        usy = T(v.y);
+      }
+    }
+  } else {
+    const T* b = consts<T>(p).body[m - 1];
+    const T dx = T(x) - b[0];
+    const T dy = T(y) - b[1];
+    usx = b[2] - b[4] * dy;
+    usy = b[3] + b[4] * dx;
+  }
+}
+
+template <class T>
+__device__ __forceinline__ Macro<T> macros(const StepParams& p, const T h[9], uint8_t m, int x,
+                                           int y) {
+  Macro<T> r;
+  r.drho = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
+  r.rho = T(1) + r.drho;
+  const T jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
+  const T jy = (h[2] - h[4]) + (h[5] + h[6]) - (h[7] + h[8]);
+  const Consts<T>& c = consts<T>(p);
+  T usx = T(0), usy = T(0), a = T(0), kap = T(0);
+  if (m) {
+    a = c.a_s;
+    kap = c.kappa_s;
+    solid_velocity<T>(p, m, x, y, usx, usy);
+  }
+  const T gx = c.gx, gy = c.gy;
+  const T dx = jx + T(0.5) * r.rho * gx - r.rho * usx;
+  const T dy = jy + T(0.5) * r.rho * gy - r.rho * usy;
+  const T inv = T(1) / (r.rho * (T(1) + a));
+  r.ux = usx + dx * inv;
+  r.uy = usy + dy * inv;
+  r.fpx = -kap * dx;
+  r.fpy = -kap * dy;
+  r.Fx = r.fpx + r.rho * gx;
+  r.Fy = r.fpy + r.rho * gy;
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Collision on offsets.
+// SRT (Eq. LatticeBoltz + Eq. Guo1):
+//   h* = h - omega (h - h_eq) + (1 - omega/2) w [3 (xi - u) + 9 (xi.u) xi] . F
+//   h_eq = w [drho + rho (3 xi.u + 4.5 (xi.u)^2 - 1.5 u.u)]
+// ---------------------------------------------------------------------------
+template <class T, int A>
+__device__ __forceinline__ T srt_one(T h, T omega, T pre, T common, T rho, T ux, T uy, T Fx,
+                                     T Fy, T uF) {
+  const T xu = T(cx(A)) * ux + T(cy(A)) * uy;
+  const T xF = T(cx(A)) * Fx + T(cy(A)) * Fy;
+  const T heq = wgt<T>(A) * (common + rho * xu * (T(3) + T(4.5) * xu));
+  const T Fa = pre * wgt<T>(A) * (T(3) * (xF - uF) + T(9) * xu * xF);
+  return h - omega * (h - heq) + Fa;
+}
+
+template <class T>
+__device__ __forceinline__ void collide_srt(const StepParams& p, T h[9], const Macro<T>& q) {
+  const T omega = consts<T>(p).omega, pre = consts<T>(p).srt_pre;
+  const T uu = q.ux * q.ux + q.uy * q.uy;
+  const T common = q.drho - T(1.5) * q.rho * uu;
+  const T uF = q.ux * q.Fx + q.uy * q.Fy;
+  h[0] = srt_one<T, 0>(h[0], omega, pre, common, q.rho, q.ux, q.uy, q.Fx, q.Fy, uF);
+  h[1] = srt_one<T, 1>(h[1], omega, pre, common, q.rho, q.ux, q.uy, q.Fx, q.Fy, uF);
+  h[2] = srt_one<T, 2>(h[2], omega, pre, common, q.rho, q.ux, q.uy, q.Fx, q.Fy, uF);
+  h[3] = srt_one<T, 3>(h[3], omega, pre, common, q.rho, q.ux, q.uy, q.Fx, q.Fy, uF);
+  h[4] = srt_one<T, 4>(h[4], omega, pre, common, q.rho, q.ux, q.uy, q.Fx, q.Fy, uF);
+  h[5] = srt_one<T, 5>(h[5], omega, pre, common, q.rho, q.ux, q.uy, q.Fx, q.Fy, uF);
+  h[6] = srt_one<T, 6>(h[6], omega, pre, common, q.rho, q.ux, q.uy, q.Fx, q.Fy, uF);
+  h[7] = srt_one<T, 7>(h[7], omega, pre, common, q.rho, q.ux, q.uy, q.Fx, q.Fy, uF);
+  h[8] = srt_one<T, 8>(h[8], omega, pre, common, q.rho, q.ux, q.uy, q.Fx, q.Fy, uF);
+}
+
+// MRT (Eq. equa_lbl_mrt with Lu forcing, Eq. Guo2), on the moments of h.
+// m = M h with M of Eq. eq1.7; since M w = (1, -2, 1, 0, ...), the equilibrium
+// moments of h are m_eq(rho, u) - M w. The forcing moments M F are
+// (0, 6 u.F, -6 u.F, F_x, -F_x, F_y, -F_y, 2 (u F_x - v F_y), u F_y + v F_x).
+// Rates of the conserved moments (rho, j_x, j_y) do not change the result
+// (j* = j + F for any rate, because m_eq uses the half-force velocity).
+// f* = M^-1 m* with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
+template <class T>
+__device__ __forceinline__ void collide_mrt(const StepParams& p, T h[9], const Macro<T>& q) {
+  const Consts<T>& c = consts<T>(p);
+  const T s1 = c.s_e, s2 = c.s_eps, s4 = c.s_qx, s6 = c.s_qy, s7 = c.s_pxx, s8 = c.s_pxy;
+  const T sum14 = (h[1] + h[2]) + (h[3] + h[4]);
+  const T sum58 = (h[5] + h[6]) + (h[7] + h[8]);
+  const T e = -T(4) * h[0] - sum14 + T(2) * sum58;
+  const T eps = T(4) * h[0] - T(2) * sum14 + sum58;
+  const T jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
+  const T qx = T(2) * (h[3] - h[1]) + (h[5] - h[6]) + (h[8] - h[7]);
+  const T jy = (h[2] - h[4]) + (h[5] + h[6]) - (h[7] + h[8]);
+  const T qy = T(2) * (h[4] - h[2]) + (h[5] + h[6]) - (h[7] + h[8]);
+  const T pxx = (h[1] - h[2]) + (h[3] - h[4]);
+  const T pxy = (h[5] - h[6]) + (h[7] - h[8]);
+
+  const T rho = q.rho, ux = q.ux, uy = q.uy, Fx = q.Fx, Fy = q.Fy;
+  const T uu = ux * ux + uy * uy;
+  const T uF = ux * Fx + uy * Fy;
+  const T e_eq = -T(2) * q.drho + T(3) * rho * uu;
+  const T eps_eq = q.drho - T(3) * rho * uu;
+
+  const T es = e - s1 * (e - e_eq) + (T(1) - T(0.5) * s1) * T(6) * uF;
+  const T epss = eps - s2 * (eps - eps_eq) - (T(1) - T(0.5) * s2) * T(6) * uF;
+  const T jxs = jx + Fx;
+  const T jys = jy + Fy;
+  const T qxs = qx - s4 * (qx + rho * ux) - (T(1) - T(0.5) * s4) * Fx;
+  const T qys = qy - s6 * (qy + rho * uy) - (T(1) - T(0.5) * s6) * Fy;
+  const T pxxs = pxx - s7 * (pxx - rho * (ux * ux - uy * uy)) +
+                 (T(1) - T(0.5) * s7) * T(2) * (ux * Fx - uy * Fy);
+  const T pxys = pxy - s8 * (pxy - rho * ux * uy) + (T(1) - T(0.5) * s8) * (ux * Fy + uy * Fx);
+
+  const T a0 = q.drho * T(1.0 / 9.0);
+  const T a1 = es * T(1.0 / 36.0);
+  const T a2 = epss * T(1.0 / 36.0);
+  const T a3 = jxs * T(1.0 / 6.0);
+  const T a4 = qxs * T(1.0 / 12.0);
+  const T a5 = jys * T(1.0 / 6.0);
+  const T a6 = qys * T(1.0 / 12.0);
+  const T a7 = pxxs * T(0.25);
+  const T a8 = pxys * T(0.25);
+
+  const T b14 = a0 - a1 - T(2) * a2;  // common part of directions 1..4
+  const T b58 = a0 + T(2) * a1 + a2;  // common part of directions 5..8
+  h[0] = a0 - T(4) * a1 + T(4) * a2;
+  h[1] = b14 + (a3 - T(2) * a4) + a7;
+  h[2] = b14 + (a5 - T(2) * a6) - a7;
+  h[3] = b14 - (a3 - T(2) * a4) + a7;
+  h[4] = b14 - (a5 - T(2) * a6) - a7;
+  h[5] = b58 + (a3 + a4) + (a5 + a6) + a8;
+  h[6] = b58 - (a3 + a4) + (a5 + a6) - a8;
+  h[7] = b58 - (a3 + a4) - (a5 + a6) + a8;
+  h[8] = b58 + (a3 + a4) - (a5 + a6) - a8;
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic block and grid reductions in FP64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum of v[0..2] over the block (kThreads threads), fixed order; result valid
+// in thread 0.
+__device__ __forceinline__ void block_sum3(double v[3], double (*sm)[3]) {
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0) {
+    sm[warp][0] = v[0];
+    sm[warp][1] = v[1];
+    sm[warp][2] = v[2];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int k = 0; k < 3; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) s += sm[w][k];
+      v[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// Finishes the per-step reduction once this tile's partial is written: the
+// last tile of each group of kGroup tiles sums the group in tile order, and
+// the last group to finish sums the groups in group order and writes the
+// step's record. Both levels are fixed-order, so the result does not depend
+// on which blocks ran when.
+__device__ __forceinline__ void finish_reduction(const StepParams& p, int tile, long long t,
+                                                 const double tile_sum[3], double (*sm)[3]) {
+  __shared__ int s_last;
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int group = tile / kGroup;
+  const int n_groups = (p.n_tiles + kGroup - 1) / kGroup;
+  if (tid == 0) {
+    double* dst = p.partials + 3ll * tile;
+    __stcg(dst + 0, tile_sum[0]);
+    __stcg(dst + 1, tile_sum[1]);
+    __stcg(dst + 2, tile_sum[2]);
+    __threadfence();
+    const int gsize = min(kGroup, p.n_tiles - group * kGroup);
+    const unsigned prev = atomicAdd(p.counters + group, 1u);
+    s_last = (prev == (unsigned)(gsize - 1));
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  {
+    double v[3] = {0.0, 0.0, 0.0};
+    const int t0 = group * kGroup;
+    const int gsize = min(kGroup, p.n_tiles - t0);
+    if (tid < gsize) {
+      const double* src = p.partials + 3ll * (t0 + tid);
+      v[0] = __ldcg(src + 0);
+      v[1] = __ldcg(src + 1);
+      v[2] = __ldcg(src + 2);
+    }
+    block_sum3(v, sm);
+    if (tid == 0) {
+      double* g = p.group_partials + 3ll * group;
+      __stcg(g + 0, v[0]);
+      __stcg(g + 1, v[1]);
+      __stcg(g + 2, v[2]);
+      p.counters[group] = 0u;  // ready for the next step
+      __threadfence();
+      const unsigned prev = atomicAdd(p.counters + n_groups, 1u);
+      s_last = (prev == (unsigned)(n_groups - 1));
+    }
+    __syncthreads();
+  }
+  if (!s_last) return;
+  __threadfence();
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int g = tid; g < n_groups; g += kThreads) {
+    // each thread adds its strided share in increasing group order
+    v[0] += __ldcg(p.group_partials + 3ll * g + 0);
+    v[1] += __ldcg(p.group_partials + 3ll * g + 1);
+    v[2] += __ldcg(p.group_partials + 3ll * g + 2);
+  }
+  block_sum3(v, sm);
+  if (tid == 0) {
+    double* r = p.ring + 3ll * (t % p.ring_len);
+    r[0] = v[0];
+    r[1] = v[1];
+    r[2] = p.reduce_mass ? v[2] : 0.0;
+    p.counters[n_groups] = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The fused time step of one tile (kTileX x kTileY nodes; each thread takes
+// one column of the tile and kRows rows, kBlockY rows apart).
+// ---------------------------------------------------------------------------
+template <int STORE, int COLL>
+__device__ __forceinline__ void step_tile(const StepParams& p, int tile, long long t) {
+  using S = Store<STORE>;
+  using T = typename S::T;
+  using E = typename S::E;
+  __shared__ double sm[kThreads / 32][3];
+
+  const int tx = tile % p.tiles_x;
+  const int ty = tile / p.tiles_x;
+  const int x0 = tx * kTileX, y0 = ty * kTileY;
+  const int x = x0 + threadIdx.x;
+  const bool interior = x0 >= 1 && x0 + kTileX <= p.nx - 1 && y0 >= 1 && y0 + kTileY <= p.ny - 1;
+  const E* __restrict__ src = static_cast<const E*>(p.src);
+  E* __restrict__ dst = static_cast<E*>(p.dst);
+
+  T dm = T(0);                 // sum of drho over this thread's nodes
+  double bfx = 0.0, bfy = 0.0;  // force on solid nodes (FP64 from the node up)
+  bool any_solid = false;
+
+#pragma unroll 2
+  for (int r = 0; r < kRows; ++r) {
+    const int y = y0 + threadIdx.y + r * kBlockY;
+    const bool active = x < p.nx && y < p.ny;
+    if (!active) continue;
+    T h[9];
+    pull_node<S>(p, src, interior, x, y, h);
+    const long long i = (long long)y * p.pitch + x;
+    const uint8_t m = p.mask[i];
+    const Macro<T> q = macros<T>(p, h, m, x, y);
+    if (COLL == kSrt)
+      collide_srt<T>(p, h, q);
+    else
+      collide_mrt<T>(p, h, q);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) S::store(dst + (long long)a * p.plane + i, h[a], a);
+    if (!(q.rho > T(0)) || !isfinite(q.ux) || !isfinite(q.uy)) atomicOr(p.flag, 1);
+    dm += q.drho;
+    if (m) {
+      any_solid = true;
+      bfx -= double(q.fpx);
+      bfy -= double(q.fpy);
+    }
+  }
+
+  // Per-step record: the block's force on solid nodes (FP64) and total density
+  // (the arithmetic type within the block, FP64 from the tile up). Blocks
+  // without solid nodes skip the FP64 work.
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const bool warp_solid = __any_sync(0xffffffffu, any_solid);
+  if (p.reduce_mass) dm = warp_sum(dm);
+  if (warp_solid) {
+    bfx = warp_sum(bfx);
+    bfy = warp_sum(bfy);
+  }
+  __shared__ T smass[kThreads / 32];
+  if (lane == 0) {
+    smass[warp] = dm;
+    sm[warp][0] = bfx;
+    sm[warp][1] = bfy;
+  }
+  const int block_solid = __syncthreads_or(any_solid);
+  double ts[3] = {0.0, 0.0, 0.0};
+  if (tid == 0) {
+    T msum = T(0);
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) msum += smass[w];
+    if (block_solid) {
+#pragma unroll
+      for (int w = 0; w < kThreads / 32; ++w) {
+        ts[0] += sm[w][0];
+        ts[1] += sm[w][1];
+      }
+    }
+    if (p.reduce_mass) {
+      // sum rho = active nodes + sum drho
+      const int nact = min(kTileX, p.nx - x0) * min(kTileY, p.ny - y0);
+      ts[2] = double(nact) + double(msum);
+    }
+  }
+  __syncthreads();
+  finish_reduction(p, tile, t, ts, sm);
+}
+
+template <int STORE, int COLL>
+__global__ void __launch_bounds__(kThreads, 4) fused_step_kernel(const __grid_constant__ StepParams p) {
+  step_tile<STORE, COLL>(p, blockIdx.x, p.t);
+}
+
+// Grouped launch for serving: block b runs tile table[b].tile of solver
+// table[b].solver at that solver's k-th step of the batch. Each solver has two
+// parameter sets in a device array, for even and odd k (source and destination
+// buffers swapped); params[].t is the solver's step index at k = 0.
+template <int STORE, int COLL>
+__global__ void __launch_bounds__(kThreads, 4) fused_group_kernel(const StepParams* __restrict__ params,
+                                                                  const GroupTile* __restrict__ table,
+                                                                  long long k) {
+  const GroupTile gt = table[blockIdx.x];
+  const StepParams& p = params[2 * gt.solver + int(k & 1)];
+  step_tile<STORE, COLL>(p, gt.tile, p.t + k);
+}
+
+// ---------------------------------------------------------------------------
+// Moments: the density and implicit velocity the next step computes.
+// ---------------------------------------------------------------------------
+template <int STORE>
+__global__ void moments_kernel(const __grid_constant__ StepParams p, double* rho, double* ux,
+                               double* uy) {
+  using S = Store<STORE>;
+  using T = typename S::T;
+  const int x = blockIdx.x * kBlockX + threadIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.y;
+  if (x >= p.nx || y >= p.ny) return;
+  T h[9];
+  pull_node<S>(p, static_cast<const typename S::E*>(p.src), false, x, y, h);
+  const uint8_t m = p.mask[(long long)y * p.pitch + x];
+  const Macro<T> q = macros<T>(p, h, m, x, y);
+  const long long o = (long long)y * p.nx + x;
+  rho[o] = double(q.rho);
+  ux[o] = double(q.ux);
+  uy[o] = double(q.uy);
+}
+
+// f*(t) := f_eq(rho0, u(x)), u from a device [2][ny][nx] array or uniform.
+template <int STORE>
+__global__ void init_kernel(const __grid_constant__ StepParams p, void* dst, const double* u,
+                            double rho0, double u0x, double u0y) {
+  using S = Store<STORE>;
+  using T = typename S::T;
+  const int x = blockIdx.x * kBlockX + threadIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.y;
+  if (x >= p.nx || y >= p.ny) return;
+  const long long o = (long long)y * p.nx + x;
+  const long long nn = (long long)p.nx * p.ny;
+  const T ux = T(u ? u[o] : u0x), uy = T(u ? u[nn + o] : u0y), rho = T(rho0);
+  const T drho = rho - T(1);
+  const T common = drho - T(1.5) * rho * (ux * ux + uy * uy);
+  typename S::E* d = static_cast<typename S::E*>(dst);
+  const long long i = (long long)y * p.pitch + x;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const T xu = T(cx(a)) * ux + T(cy(a)) * uy;
+    const T heq = wgt<T>(a) * (common + rho * xu * (T(3) + T(4.5) * xu));
+    S::store(d + (long long)a * p.plane + i, heq, a);
+  }
+}
+
+// Store <-> dense FP64 [9][ny][nx].
+template <int STORE>
+__global__ void export_kernel(const __grid_constant__ StepParams p, const void* srcv, double* f) {
+  using S = Store<STORE>;
+  const int x = blockIdx.x * kBlockX + threadIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.y;
+  if (x >= p.nx || y >= p.ny) return;
+  const typename S::E* src = static_cast<const typename S::E*>(srcv);
+  const long long i = (long long)y * p.pitch + x;
+  const long long o = (long long)y * p.nx + x;
+  const long long nn = (long long)p.nx * p.ny;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) f[a * nn + o] = S::to_f64(src + a * p.plane + i, a);
+}
+
+template <int STORE>
+__global__ void import_kernel(const __grid_constant__ StepParams p, void* dstv, const double* f) {
+  using S = Store<STORE>;
+  const int x = blockIdx.x * kBlockX + threadIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.y;
+  if (x >= p.nx || y >= p.ny) return;
+  typename S::E* dst = static_cast<typename S::E*>(dstv);
+  const long long i = (long long)y * p.pitch + x;
+  const long long o = (long long)y * p.nx + x;
+  const long long nn = (long long)p.nx * p.ny;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) S::from_f64(dst + a * p.plane + i, f[a * nn + o], a);
+}
+
+}  // namespace vplbm

@@ -1,0 +1,56 @@
+// Instantiates the kernels of one storage type (VPLBM_STORE, VPLBM_SUFFIX)
+// and defines its launchers.
+#include "vplbm_device.cuh"
+#include "vplbm_launch.h"
+
+#define VPLBM_CAT2(a, b) a##b
+#define VPLBM_CAT(a, b) VPLBM_CAT2(a, b)
+#define VPLBM_FN(name) VPLBM_CAT(name, VPLBM_SUFFIX)
+
+namespace vplbm {
+
+static dim3 node_grid(const StepParams& p) {
+  return dim3((p.nx + kBlockX - 1) / kBlockX, (p.ny + kBlockY - 1) / kBlockY);
+}
+
+cudaError_t VPLBM_FN(launch_fused_)(int coll, const StepParams& p, cudaStream_t st) {
+  if (coll == kSrt)
+    fused_step_kernel<VPLBM_STORE, kSrt><<<p.n_tiles, dim3(kBlockX, kBlockY), 0, st>>>(p);
+  else
+    fused_step_kernel<VPLBM_STORE, kMrt><<<p.n_tiles, dim3(kBlockX, kBlockY), 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t VPLBM_FN(launch_group_)(int coll, const StepParams* d_params, const GroupTile* d_table,
+                                    int n_blocks, long long k, cudaStream_t st) {
+  if (n_blocks <= 0) return cudaSuccess;
+  if (coll == kSrt)
+    fused_group_kernel<VPLBM_STORE, kSrt><<<n_blocks, dim3(kBlockX, kBlockY), 0, st>>>(d_params, d_table, k);
+  else
+    fused_group_kernel<VPLBM_STORE, kMrt><<<n_blocks, dim3(kBlockX, kBlockY), 0, st>>>(d_params, d_table, k);
+  return cudaGetLastError();
+}
+
+cudaError_t VPLBM_FN(launch_moments_)(const StepParams& p, double* rho, double* ux, double* uy,
+                                      cudaStream_t st) {
+  moments_kernel<VPLBM_STORE><<<node_grid(p), dim3(kBlockX, kBlockY), 0, st>>>(p, rho, ux, uy);
+  return cudaGetLastError();
+}
+
+cudaError_t VPLBM_FN(launch_init_)(const StepParams& p, void* dst, const double* u, double rho0,
+                                   double u0x, double u0y, cudaStream_t st) {
+  init_kernel<VPLBM_STORE><<<node_grid(p), dim3(kBlockX, kBlockY), 0, st>>>(p, dst, u, rho0, u0x, u0y);
+  return cudaGetLastError();
+}
+
+cudaError_t VPLBM_FN(launch_export_)(const StepParams& p, const void* src, double* f, cudaStream_t st) {
+  export_kernel<VPLBM_STORE><<<node_grid(p), dim3(kBlockX, kBlockY), 0, st>>>(p, src, f);
+  return cudaGetLastError();
+}
+
+cudaError_t VPLBM_FN(launch_import_)(const StepParams& p, void* dst, const double* f, cudaStream_t st) {
+  import_kernel<VPLBM_STORE><<<node_grid(p), dim3(kBlockX, kBlockY), 0, st>>>(p, dst, f);
+  return cudaGetLastError();
+}
+
+}  // namespace vplbm

@@ -1,0 +1,74 @@
+// Parameters shared between the host runtime and the device kernels of the
+// VP-LBM solver.
+#pragma once
+
+#include <stdint.h>
+
+namespace vplbm {
+
+enum { kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
+enum { kSrt = 0, kMrt = 1 };
+enum { kBcPeriodic = 0, kBcInletOutlet = 1, kBcFreeSlip = 2 };
+
+constexpr int kMaxBodies = 8;
+constexpr int kBlockX = 64;             // threads per block along x (one node each)
+constexpr int kBlockY = 4;              // threads per block along y
+constexpr int kRows = 8;                // rows each thread processes
+constexpr int kThreads = kBlockX * kBlockY;
+constexpr int kTileX = kBlockX;         // tile of one block: kTileX x kTileY nodes
+constexpr int kTileY = kBlockY * kRows;
+constexpr int kGroup = 256;             // tiles per first-level reduction group
+constexpr uint8_t kStaticSolid = 255;   // mask value of a node solid through the static mask
+
+// State of one rigid body at the time of a step.
+struct BodyState {
+  double cx, cy, vx, vy, omega;
+};
+
+// Collision and forcing constants in the arithmetic type of the kernel (the
+// FP32 kernels read float copies: converting FP64 parameters per thread would
+// run at the FP64 rate).
+template <class T>
+struct Consts {
+  T omega, srt_pre;                       // 1/tau and 1 - 1/(2 tau)
+  T s_e, s_eps, s_qx, s_qy, s_pxx, s_pxy;  // MRT rates
+  T a_s, kappa_s;                         // 1/(2 eta) and (1/eta)/(1 + 1/(2 eta))
+  T gx, gy;                               // body force per unit mass
+  T heq_in[9];                            // inlet ghost f_eq(1, u_in) - w
+  T body[kMaxBodies][5];                  // cx, cy, vx, vy, omega of each body
+};
+
+// Everything one fused step of one solver needs (passed by value as a
+// __grid_constant__ kernel parameter, or from a device array when grouped).
+struct StepParams {
+  const void* src;          // f*(t), storage element type, [9][ny][pitch]
+  void* dst;                // f*(t+1)
+  const uint8_t* mask;      // [ny][pitch]: 0 fluid, 1..kMaxBodies body, 255 static solid
+  const void* us;           // static solid velocity, float2/double2 [ny][pitch], or null
+  int nx, ny, pitch;
+  int bc_x, bc_y;
+  int tiles_x, n_tiles;
+  int n_bodies;
+  long long plane;          // pitch * ny
+  Consts<double> cd;        // constants for the FP64 kernels
+  Consts<float> cf;         // the same, rounded, for the FP32 kernels
+  double* partials;         // [n_tiles][3]
+  double* group_partials;   // [n_groups][3]
+  unsigned* counters;       // [n_groups + 1], zero between steps
+  double* ring;             // [ring_len][3]: F_x, F_y, sum rho per step
+  int* flag;                // set to 1 on divergence
+  long long t;              // index of this step
+  int ring_len;
+  int reduce_mass;
+};
+
+template <class T> __host__ __device__ inline const Consts<T>& consts(const StepParams& p);
+template <> __host__ __device__ inline const Consts<double>& consts<double>(const StepParams& p) { return p.cd; }
+template <> __host__ __device__ inline const Consts<float>& consts<float>(const StepParams& p) { return p.cf; }
+
+struct GroupTile {
+  int solver;
+  int tile;
+};
+
+}  // namespace vplbm

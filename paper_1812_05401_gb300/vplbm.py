@@ -1,0 +1,376 @@
+"""Thin ctypes binding of the vplbm C ABI (include/vplbm.h).
+
+Functions keep the C names and only marshal arguments; every step of the time
+step runs in the CUDA library. There is no fallback: if libvplbm.so is missing
+or cannot be loaded, loading raises.
+
+`Solver` is a small convenience wrapper over the same calls (numpy arrays in,
+numpy arrays out, torch streams accepted). `config_from_workload` turns a
+workload description (paper_1812_05401_gb300.inputs.Workload) into a
+vplbm_config plus rigid bodies.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvplbm.so")
+
+VPLBM_OK, VPLBM_ERR_INVALID, VPLBM_ERR_NOMEM, VPLBM_ERR_CUDA = 0, 1, 2, 3
+VPLBM_ERR_DIVERGED, VPLBM_ERR_TIMEOUT, VPLBM_ERR_STATE = 4, 5, 6
+VPLBM_SRT, VPLBM_MRT = 0, 1
+VPLBM_F64, VPLBM_F32, VPLBM_F16_OFFSET, VPLBM_BF16_OFFSET = 0, 1, 2, 3
+VPLBM_BC_PERIODIC, VPLBM_BC_INLET_OUTLET, VPLBM_BC_FREE_SLIP = 0, 1, 2
+VPLBM_MAX_BODIES = 8
+
+STORAGE = {"f64": VPLBM_F64, "f32": VPLBM_F32, "f16": VPLBM_F16_OFFSET, "bf16": VPLBM_BF16_OFFSET}
+COLLISION = {"srt": VPLBM_SRT, "mrt": VPLBM_MRT}
+BYTES_PER_VALUE = {VPLBM_F64: 8, VPLBM_F32: 4, VPLBM_F16_OFFSET: 2, VPLBM_BF16_OFFSET: 2}
+
+
+class vplbm_body(C.Structure):
+    _fields_ = [("cx", C.c_double), ("cy", C.c_double), ("radius", C.c_double),
+                ("amp_x", C.c_double), ("amp_y", C.c_double), ("period", C.c_double),
+                ("omega", C.c_double), ("outside", C.c_int32), ("reserved", C.c_int32)]
+
+
+class vplbm_config(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("collision", C.c_int32),
+                ("storage", C.c_int32), ("bc_x", C.c_int32), ("bc_y", C.c_int32),
+                ("use_rates", C.c_int32), ("reduce_mass", C.c_int32),
+                ("tau", C.c_double), ("lam", C.c_double), ("eta", C.c_double),
+                ("u_in", C.c_double * 2), ("rho0", C.c_double), ("u0", C.c_double * 2),
+                ("body_force", C.c_double * 2), ("rates", C.c_double * 9),
+                ("force_ring_len", C.c_int32), ("reserved", C.c_int32), ("stream", C.c_void_p)]
+
+
+class VplbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib() -> C.CDLL:
+    """Loads libvplbm.so; raises if it is not built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_1812_05401_gb300.build.build() "
+                              "(the CUDA library has no fallback)")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        dp = C.POINTER(C.c_double)
+        L.vplbm_config_init.argtypes = [C.POINTER(vplbm_config)]
+        L.vplbm_config_init.restype = None
+        L.vplbm_tau_from_reynolds.argtypes = [C.c_double] * 3
+        L.vplbm_tau_from_reynolds.restype = C.c_double
+        L.vplbm_footprint_bytes.argtypes = [C.POINTER(vplbm_config)]
+        L.vplbm_footprint_bytes.restype = C.c_size_t
+        L.vplbm_create.argtypes = [C.POINTER(vplbm_config), C.POINTER(P)]
+        L.vplbm_set_initial_velocity.argtypes = [P, dp]
+        L.vplbm_set_mask_and_solid_velocity.argtypes = [P, P, P, C.c_int32]
+        L.vplbm_set_bodies.argtypes = [P, C.POINTER(vplbm_body), C.c_int32]
+        L.vplbm_step.argtypes = [P, C.c_int64]
+        L.vplbm_synchronize.argtypes = [P]
+        L.vplbm_step_count.argtypes = [P]
+        L.vplbm_step_count.restype = C.c_int64
+        L.vplbm_moments.argtypes = [P, P, P, P, C.c_int32]
+        L.vplbm_populations.argtypes = [P, P, C.c_int32]
+        L.vplbm_set_populations.argtypes = [P, P, C.c_int32]
+        L.vplbm_mask.argtypes = [P, P]
+        L.vplbm_forces.argtypes = [P, dp, dp, dp, C.c_int64, C.POINTER(C.c_int64)]
+        L.vplbm_group_step.argtypes = [C.POINTER(P), C.c_int32, C.POINTER(C.c_int64)]
+        L.vplbm_launch_count.argtypes = [P]
+        L.vplbm_launch_count.restype = C.c_int64
+        L.vplbm_enable_timing.argtypes = [P, C.c_int32]
+        L.vplbm_fused_timing.argtypes = [P, dp, C.POINTER(C.c_int64)]
+        L.vplbm_last_error.argtypes = [P]
+        L.vplbm_last_error.restype = C.c_char_p
+        L.vplbm_status_string.argtypes = [C.c_int]
+        L.vplbm_status_string.restype = C.c_char_p
+        L.vplbm_destroy.argtypes = [P]
+        L.vplbm_destroy.restype = None
+        for name in ("vplbm_create", "vplbm_set_initial_velocity", "vplbm_set_mask_and_solid_velocity",
+                     "vplbm_set_bodies", "vplbm_step", "vplbm_synchronize", "vplbm_moments",
+                     "vplbm_populations", "vplbm_set_populations", "vplbm_mask", "vplbm_forces",
+                     "vplbm_group_step", "vplbm_enable_timing", "vplbm_fused_timing"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+        return L
+
+
+# ---------------------------------------------------------------------------
+# C-named wrappers (argument marshalling only)
+# ---------------------------------------------------------------------------
+
+def vplbm_config_init() -> vplbm_config:
+    c = vplbm_config()
+    lib().vplbm_config_init(C.byref(c))
+    return c
+
+
+def vplbm_tau_from_reynolds(u_ref: float, l_ref: float, re: float) -> float:
+    return lib().vplbm_tau_from_reynolds(u_ref, l_ref, re)
+
+
+def vplbm_footprint_bytes(cfg: vplbm_config) -> int:
+    return int(lib().vplbm_footprint_bytes(C.byref(cfg)))
+
+
+def _check(handle, st: int, what: str):
+    if st != VPLBM_OK:
+        msg = lib().vplbm_last_error(handle).decode() if handle else ""
+        raise VplbmError(st, f"{what}: {lib().vplbm_status_string(st).decode()} {msg}".strip())
+
+
+def vplbm_create(cfg: vplbm_config) -> int:
+    h = C.c_void_p()
+    _check(None, lib().vplbm_create(C.byref(cfg), C.byref(h)), "vplbm_create")
+    return h.value
+
+
+def _ptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def _dev(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def vplbm_set_initial_velocity(h, u=None):
+    dp = None
+    if u is not None:
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        dp = u.ctypes.data_as(C.POINTER(C.c_double))
+    _check(h, lib().vplbm_set_initial_velocity(h, dp), "vplbm_set_initial_velocity")
+
+
+def vplbm_set_mask_and_solid_velocity(h, chi, us=None, on_device: bool = False):
+    if on_device:
+        _check(h, lib().vplbm_set_mask_and_solid_velocity(
+            h, _dev(chi), None if us is None else _dev(us), 1), "vplbm_set_mask_and_solid_velocity")
+        return
+    chi = np.ascontiguousarray(chi, dtype=np.uint8)
+    us = None if us is None else np.ascontiguousarray(us, dtype=np.float64)
+    _check(h, lib().vplbm_set_mask_and_solid_velocity(h, _ptr(chi), _ptr(us), 0),
+           "vplbm_set_mask_and_solid_velocity")
+
+
+def vplbm_set_bodies(h, bodies):
+    arr = (vplbm_body * max(1, len(bodies)))()
+    for i, b in enumerate(bodies):
+        arr[i] = vplbm_body(b.cx, b.cy, b.radius, b.amp_x, b.amp_y, b.period, b.omega,
+                            int(b.outside), 0)
+    _check(h, lib().vplbm_set_bodies(h, arr, len(bodies)), "vplbm_set_bodies")
+
+
+def vplbm_step(h, n: int):
+    _check(h, lib().vplbm_step(h, int(n)), "vplbm_step")
+
+
+def vplbm_synchronize(h):
+    _check(h, lib().vplbm_synchronize(h), "vplbm_synchronize")
+
+
+def vplbm_step_count(h) -> int:
+    return int(lib().vplbm_step_count(h))
+
+
+def vplbm_moments(h, rho, ux, uy, on_device: bool = False):
+    if on_device:
+        _check(h, lib().vplbm_moments(h, _dev(rho), _dev(ux), _dev(uy), 1), "vplbm_moments")
+    else:
+        _check(h, lib().vplbm_moments(h, _ptr(rho), _ptr(ux), _ptr(uy), 0), "vplbm_moments")
+
+
+def vplbm_populations(h, f, on_device: bool = False):
+    _check(h, lib().vplbm_populations(h, _dev(f) if on_device else _ptr(f), int(on_device)),
+           "vplbm_populations")
+
+
+def vplbm_set_populations(h, f, on_device: bool = False):
+    if not on_device:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+    _check(h, lib().vplbm_set_populations(h, _dev(f) if on_device else _ptr(f), int(on_device)),
+           "vplbm_set_populations")
+
+
+def vplbm_mask(h, chi):
+    _check(h, lib().vplbm_mask(h, _ptr(chi)), "vplbm_mask")
+
+
+def vplbm_forces(h, cap: int):
+    fx, fy, ms = np.zeros(cap), np.zeros(cap), np.zeros(cap)
+    cnt = C.c_int64()
+    dp = C.POINTER(C.c_double)
+    _check(h, lib().vplbm_forces(h, fx.ctypes.data_as(dp), fy.ctypes.data_as(dp),
+                                 ms.ctypes.data_as(dp), cap, C.byref(cnt)), "vplbm_forces")
+    k = cnt.value
+    return fx[:k], fy[:k], ms[:k]
+
+
+def vplbm_group_step(handles, steps):
+    n = len(handles)
+    arr = (C.c_void_p * max(1, n))(*handles)
+    st = (C.c_int64 * max(1, n))(*[int(s) for s in steps])
+    _check(handles[0] if n else None, lib().vplbm_group_step(arr, n, st), "vplbm_group_step")
+
+
+def vplbm_launch_count(h) -> int:
+    return int(lib().vplbm_launch_count(h))
+
+
+def vplbm_enable_timing(h, enable: bool = True):
+    _check(h, lib().vplbm_enable_timing(h, int(enable)), "vplbm_enable_timing")
+
+
+def vplbm_fused_timing(h):
+    ms = C.c_double()
+    n = C.c_int64()
+    _check(h, lib().vplbm_fused_timing(h, C.byref(ms), C.byref(n)), "vplbm_fused_timing")
+    return ms.value, n.value
+
+
+def vplbm_last_error(h) -> str:
+    return lib().vplbm_last_error(h).decode()
+
+
+def vplbm_destroy(h):
+    lib().vplbm_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper
+# ---------------------------------------------------------------------------
+
+def make_config(nx, ny, collision="srt", storage="f32", tau=0.8, lam=3.0 / 16.0, eta=1e-7,
+                bc="periodic", u_in=(0.0, 0.0), u0=(0.0, 0.0), rho0=1.0, body_force=(0.0, 0.0),
+                rates=None, reduce_mass=True, ring_len=4096, stream=None) -> vplbm_config:
+    c = vplbm_config_init()
+    c.nx, c.ny = int(nx), int(ny)
+    c.collision = COLLISION[collision] if isinstance(collision, str) else int(collision)
+    c.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    if bc == "periodic":
+        c.bc_x, c.bc_y = VPLBM_BC_PERIODIC, VPLBM_BC_PERIODIC
+    elif bc == "channel":
+        c.bc_x, c.bc_y = VPLBM_BC_INLET_OUTLET, VPLBM_BC_FREE_SLIP
+    else:
+        c.bc_x, c.bc_y = bc
+    c.tau, c.lam, c.eta = tau, lam, eta
+    c.u_in[0], c.u_in[1] = u_in
+    c.u0[0], c.u0[1] = u0
+    c.rho0 = rho0
+    c.body_force[0], c.body_force[1] = body_force
+    if rates is not None:
+        c.use_rates = 1
+        for k in range(9):
+            c.rates[k] = rates[k]
+    c.reduce_mass = int(bool(reduce_mass))
+    c.force_ring_len = int(ring_len)
+    if stream is not None:
+        c.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    return c
+
+
+def config_from_workload(w, ring_len: int = 4096, stream=None, reduce_mass: bool = True):
+    """vplbm_config and body list for an inputs.Workload (tau from its
+    Reynolds number when it gives one)."""
+    tau = w.tau if w.tau is not None else vplbm_tau_from_reynolds(w.u_ref, w.l_ref, w.re)
+    u_in = (w.u_ref, 0.0) if w.bc == "channel" else (0.0, 0.0)
+    cfg = make_config(w.nx, w.ny, w.collision, w.storage, tau, w.lam, bc=w.bc, u_in=u_in,
+                      ring_len=ring_len, stream=stream, reduce_mass=reduce_mass)
+    return cfg, list(w.bodies)
+
+
+class Solver:
+    """One vplbm solver; arrays are numpy (host) unless a call says otherwise."""
+
+    def __init__(self, cfg: vplbm_config, bodies=(), u_init=None):
+        self.cfg = cfg
+        self.nx, self.ny = cfg.nx, cfg.ny
+        self.h = vplbm_create(cfg)
+        try:
+            if u_init is not None:
+                vplbm_set_initial_velocity(self.h, u_init)
+            if bodies:
+                vplbm_set_bodies(self.h, list(bodies))
+        except Exception:
+            self.close()
+            raise
+
+    @classmethod
+    def from_workload(cls, w, stream=None, ring_len: int = 4096, reduce_mass: bool = True,
+                      with_initial_velocity: bool = True):
+        cfg, bodies = config_from_workload(w, ring_len, stream, reduce_mass)
+        return cls(cfg, bodies, w.initial_velocity() if with_initial_velocity else None)
+
+    def close(self):
+        if getattr(self, "h", None):
+            vplbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def t(self) -> int:
+        return vplbm_step_count(self.h)
+
+    def step(self, n: int = 1):
+        vplbm_step(self.h, n)
+        return self
+
+    def synchronize(self):
+        vplbm_synchronize(self.h)
+
+    def set_mask(self, chi, us=None):
+        vplbm_set_mask_and_solid_velocity(self.h, chi, us)
+
+    def set_bodies(self, bodies):
+        vplbm_set_bodies(self.h, list(bodies))
+
+    def set_initial_velocity(self, u=None):
+        vplbm_set_initial_velocity(self.h, u)
+
+    def moments(self):
+        rho = np.empty((self.ny, self.nx))
+        ux = np.empty_like(rho)
+        uy = np.empty_like(rho)
+        vplbm_moments(self.h, rho, ux, uy)
+        return rho, ux, uy
+
+    def populations(self):
+        f = np.empty((9, self.ny, self.nx))
+        vplbm_populations(self.h, f)
+        return f
+
+    def set_populations(self, f):
+        vplbm_set_populations(self.h, f)
+
+    def mask(self):
+        chi = np.empty((self.ny, self.nx), dtype=np.uint8)
+        vplbm_mask(self.h, chi)
+        return chi
+
+    def forces(self, cap: int | None = None):
+        return vplbm_forces(self.h, cap or self.cfg.force_ring_len)
+
+    @property
+    def launches(self) -> int:
+        return vplbm_launch_count(self.h)

@@ -1,0 +1,72 @@
+"""CPU checks of the C ABI library: it loads without a GPU, exports every entry
+point include/vplbm.h declares, and its host-only helpers behave."""
+import os
+import re
+
+import pytest
+
+from paper_1812_05401_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(vplbm_\w+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    from paper_1812_05401_gb300 import vplbm as V
+    return V.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("vplbm_create", "vplbm_set_mask_and_solid_velocity", "vplbm_step",
+                     "vplbm_moments", "vplbm_forces", "vplbm_destroy", "vplbm_group_step"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_helpers(lib):
+    from paper_1812_05401_gb300 import vplbm as V
+    assert V.vplbm_tau_from_reynolds(0.05, 40.0, 100.0) == pytest.approx(0.56)
+    c = V.make_config(1024, 256, "mrt", "f32")
+    fp = V.vplbm_footprint_bytes(c)
+    # two population buffers of 9 x 1024 x 256 FP32 dominate
+    assert 2 * 9 * 1024 * 256 * 4 < fp < 2 * 9 * 1024 * 256 * 4 * 1.05
+    c16 = V.make_config(1024, 256, "mrt", "f16")
+    assert V.vplbm_footprint_bytes(c16) < 0.55 * fp
+    bad = V.make_config(0, 10)
+    assert V.vplbm_footprint_bytes(bad) == 0
+    assert V.lib().vplbm_status_string(4) == b"diverged"
+
+
+def test_invalid_configs_rejected_without_gpu(lib):
+    from paper_1812_05401_gb300 import vplbm as V
+    for kw in (dict(nx=0, ny=4), dict(nx=4, ny=4, tau=0.5), dict(nx=4, ny=4, eta=0.0),
+               dict(nx=4, ny=4, storage=7), dict(nx=4, ny=4, ring_len=0)):
+        nx, ny = kw.pop("nx"), kw.pop("ny")
+        c = V.make_config(nx, ny, **kw)
+        with pytest.raises(V.VplbmError) as e:
+            V.vplbm_create(c)
+        assert e.value.status == V.VPLBM_ERR_INVALID
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    from paper_1812_05401_gb300 import vplbm as V
+    monkeypatch.setattr(V, "_lib", None)
+    monkeypatch.setattr(V, "LIB_PATH", str(tmp_path / "libvplbm.so"))
+    with pytest.raises(ImportError):
+        V.lib()
