@@ -377,7 +377,8 @@ vplbm_status validate(const vplbm_config* c, std::string* why) {
 }
 
 void tiles_of(const vplbm_config* c, int* tx, int* ty, int* nt, int* ng) {
-  *tx = (c->nx + kTileX - 1) / kTileX;
+  const int tw = tile_x(c->storage);
+  *tx = (c->nx + tw - 1) / tw;
   *ty = (c->ny + kTileY - 1) / kTileY;
   *nt = *tx * *ty;
   *ng = (*nt + kGroup - 1) / kGroup;

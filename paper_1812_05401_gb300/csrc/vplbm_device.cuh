@@ -44,24 +44,79 @@ template <int S> struct Store;
 template <> struct Store<kF64> {
   using E = double;
   using T = double;
-  static __device__ __forceinline__ T load(const E* p, int a) { return __ldg(p) - wgt<T>(a); }
-  static __device__ __forceinline__ void store(E* p, T h, int a) { *p = h + wgt<T>(a); }
+  static __device__ __forceinline__ T in(E e, int a) { return e - wgt<T>(a); }
+  static __device__ __forceinline__ E out(T h, int a) { return h + wgt<T>(a); }
   static __device__ __forceinline__ double to_f64(const E* p, int) { return *p; }
   static __device__ __forceinline__ void from_f64(E* p, double f, int) { *p = f; }
+  // npt = 2 consecutive elements as one 16-byte access
+  static __device__ __forceinline__ void load_chunk(const E* p, E e[2]) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    e[0] = v.x;
+    e[1] = v.y;
+  }
+  static __device__ __forceinline__ void store_chunk(E* p, const E e[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(e[0], e[1]);
+  }
 };
 template <> struct Store<kF32> {
   using E = float;
   using T = float;
-  static __device__ __forceinline__ T load(const E* p, int a) { return __ldg(p) - wgt<T>(a); }
-  static __device__ __forceinline__ void store(E* p, T h, int a) { *p = h + wgt<T>(a); }
+  static __device__ __forceinline__ T in(E e, int a) { return e - wgt<T>(a); }
+  static __device__ __forceinline__ E out(T h, int a) { return h + wgt<T>(a); }
   static __device__ __forceinline__ double to_f64(const E* p, int) { return double(*p); }
   static __device__ __forceinline__ void from_f64(E* p, double f, int) { *p = float(f); }
+  // npt = 4 consecutive elements as one 16-byte access
+  static __device__ __forceinline__ void load_chunk(const E* p, E e[4]) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    e[0] = v.x;
+    e[1] = v.y;
+    e[2] = v.z;
+    e[3] = v.w;
+  }
+  static __device__ __forceinline__ void store_chunk(E* p, const E e[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(e[0], e[1], e[2], e[3]);
+  }
 };
-template <> struct Store<kF16> {
-  using E = __half;
+// 16-bit offset forms: npt = 4 elements as one 8-byte access.
+template <class H>
+struct Store16 {
+  using E = H;
   using T = float;
-  static __device__ __forceinline__ T load(const E* p, int) { return __half2float(__ldg(p)); }
-  static __device__ __forceinline__ void store(E* p, T h, int) { *p = __float2half_rn(h); }
+  static __device__ __forceinline__ void load_chunk(const E* p, E e[4]) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+    e[0] = __ushort_as_half_or_bf16(static_cast<unsigned short>(v.x & 0xffffu));
+    e[1] = __ushort_as_half_or_bf16(static_cast<unsigned short>(v.x >> 16));
+    e[2] = __ushort_as_half_or_bf16(static_cast<unsigned short>(v.y & 0xffffu));
+    e[3] = __ushort_as_half_or_bf16(static_cast<unsigned short>(v.y >> 16));
+  }
+  static __device__ __forceinline__ void store_chunk(E* p, const E e[4]) {
+    uint2 v;
+    v.x = unsigned(bits(e[0])) | (unsigned(bits(e[1])) << 16);
+    v.y = unsigned(bits(e[2])) | (unsigned(bits(e[3])) << 16);
+    *reinterpret_cast<uint2*>(p) = v;
+  }
+  static __device__ __forceinline__ E __ushort_as_half_or_bf16(unsigned short u);
+  static __device__ __forceinline__ unsigned short bits(E e);
+};
+template <>
+__device__ __forceinline__ __half Store16<__half>::__ushort_as_half_or_bf16(unsigned short u) {
+  return __ushort_as_half(u);
+}
+template <>
+__device__ __forceinline__ unsigned short Store16<__half>::bits(__half e) {
+  return __half_as_ushort(e);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 Store16<__nv_bfloat16>::__ushort_as_half_or_bf16(unsigned short u) {
+  return __ushort_as_bfloat16(u);
+}
+template <>
+__device__ __forceinline__ unsigned short Store16<__nv_bfloat16>::bits(__nv_bfloat16 e) {
+  return __bfloat16_as_ushort(e);
+}
+template <> struct Store<kF16> : Store16<__half> {
+  static __device__ __forceinline__ T in(E e, int) { return __half2float(e); }
+  static __device__ __forceinline__ E out(T h, int) { return __float2half_rn(h); }
   static __device__ __forceinline__ double to_f64(const E* p, int a) {
     return wgt<double>(a) + double(__half2float(*p));
   }
@@ -69,11 +124,9 @@ template <> struct Store<kF16> {
     *p = __double2half(f - wgt<double>(a));
   }
 };
-template <> struct Store<kBF16> {
-  using E = __nv_bfloat16;
-  using T = float;
-  static __device__ __forceinline__ T load(const E* p, int) { return __bfloat162float(__ldg(p)); }
-  static __device__ __forceinline__ void store(E* p, T h, int) { *p = __float2bfloat16_rn(h); }
+template <> struct Store<kBF16> : Store16<__nv_bfloat16> {
+  static __device__ __forceinline__ T in(E e, int) { return __bfloat162float(e); }
+  static __device__ __forceinline__ E out(T h, int) { return __float2bfloat16_rn(h); }
   static __device__ __forceinline__ double to_f64(const E* p, int a) {
     return wgt<double>(a) + double(__bfloat162float(*p));
   }
@@ -81,6 +134,25 @@ template <> struct Store<kBF16> {
     *p = __double2bfloat16(f - wgt<double>(a));
   }
 };
+
+// Finite test in the value's own type (an overload that widened a float to
+// double would run on the FP64 pipe, at a small fraction of the FP32 rate).
+__device__ __forceinline__ bool finite_value(float v) {
+  return (__float_as_uint(v) & 0x7f800000u) != 0x7f800000u;
+}
+__device__ __forceinline__ bool finite_value(double v) {
+  return (__double_as_longlong(v) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+}
+
+// Scalar offset load/store of one population.
+template <class S>
+__device__ __forceinline__ typename S::T load_h(const typename S::E* p, int a) {
+  return S::in(__ldg(p), a);
+}
+template <class S>
+__device__ __forceinline__ void store_h(typename S::E* p, typename S::T h, int a) {
+  *p = S::out(h, a);
+}
 
 // ---------------------------------------------------------------------------
 // Pull with boundary conditions (streaming, left-hand side of Eq. LatticeBoltz)
@@ -110,13 +182,13 @@ __device__ __forceinline__ typename S::T pull_bc(const StepParams& p, const type
       xs = p.nx - 1;
     }
   }
-  return S::load(src + (long long)as * p.plane + (long long)ys * p.pitch + xs, A);
+  return load_h<S>(src + (long long)as * p.plane + (long long)ys * p.pitch + xs, A);
 }
 
 template <class S, int A>
 __device__ __forceinline__ typename S::T pull_interior(const StepParams& p,
                                                        const typename S::E* src, long long i) {
-  return S::load(src + (long long)A * p.plane + i - cx(A) - (long long)cy(A) * p.pitch, A);
+  return load_h<S>(src + (long long)A * p.plane + i - cx(A) - (long long)cy(A) * p.pitch, A);
 }
 
 template <class S>
@@ -410,21 +482,63 @@ __device__ __forceinline__ void finish_reduction(const StepParams& p, int tile, 
 }
 
 // ---------------------------------------------------------------------------
-// The fused time step of one tile (kTileX x kTileY nodes; each thread takes
-// one column of the tile and kRows rows, kBlockY rows apart).
+// The fused time step of one tile: (32 N) x 32 nodes, N = npt(STORE). Lane l
+// of warp w takes nodes x0 + N l .. x0 + N l + N - 1 of rows y0 + w + 8 r,
+// r = 0..kRows-1.
+//
+// Interior tiles (no boundary within one node) pull with one N-element vector
+// load per direction: a direction with xi_x = +1 takes its first node's value
+// from the lane to the left (warp shuffle), one with xi_x = -1 its last
+// node's value from the lane to the right, and only the edge lanes 0 and 31
+// load that one value themselves. Tiles touching a boundary pull node by node
+// through the boundary remaps. The arithmetic per node is the same on both
+// paths.
 // ---------------------------------------------------------------------------
+template <class S, int N, int A>
+__device__ __forceinline__ void pull_dir_vec(const StepParams& p, const typename S::E* src, int xb,
+                                             int y, int lane, typename S::T (&h)[N][9]) {
+  using T = typename S::T;
+  using E = typename S::E;
+  const E* row = src + (long long)A * p.plane + (long long)(y - cy(A)) * p.pitch;
+  E e[N];
+  S::load_chunk(row + xb, e);
+  T v[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) v[k] = S::in(e[k], A);
+  if (cx(A) == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) h[k][A] = v[k];
+  } else if (cx(A) == 1) {  // node k pulls from x - 1
+    T left = __shfl_up_sync(0xffffffffu, v[N - 1], 1);
+    if (lane == 0) left = load_h<S>(row + xb - 1, A);
+    h[0][A] = left;
+#pragma unroll
+    for (int k = 1; k < N; ++k) h[k][A] = v[k - 1];
+  } else {  // node k pulls from x + 1
+    T right = __shfl_down_sync(0xffffffffu, v[0], 1);
+    if (lane == kLanes - 1) right = load_h<S>(row + xb + N, A);
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) h[k][A] = v[k + 1];
+    h[N - 1][A] = right;
+  }
+}
+
 template <int STORE, int COLL>
 __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long long t) {
   using S = Store<STORE>;
   using T = typename S::T;
   using E = typename S::E;
+  constexpr int N = npt(STORE);
+  constexpr int TX = kLanes * N;
   __shared__ double sm[kThreads / 32][3];
+  __shared__ T smass[kThreads / 32];
 
+  const int lane = threadIdx.x, warp = threadIdx.y;
   const int tx = tile % p.tiles_x;
   const int ty = tile / p.tiles_x;
-  const int x0 = tx * kTileX, y0 = ty * kTileY;
-  const int x = x0 + threadIdx.x;
-  const bool interior = x0 >= 1 && x0 + kTileX <= p.nx - 1 && y0 >= 1 && y0 + kTileY <= p.ny - 1;
+  const int x0 = tx * TX, y0 = ty * kTileY;
+  const int xb = x0 + lane * N;
+  const bool interior = x0 >= 1 && x0 + TX <= p.nx - 1 && y0 >= 1 && y0 + kTileY <= p.ny - 1;
   const E* __restrict__ src = static_cast<const E*>(p.src);
   E* __restrict__ dst = static_cast<E*>(p.dst);
 
@@ -432,43 +546,93 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
   double bfx = 0.0, bfy = 0.0;  // force on solid nodes (FP64 from the node up)
   bool any_solid = false;
 
-#pragma unroll 2
-  for (int r = 0; r < kRows; ++r) {
-    const int y = y0 + threadIdx.y + r * kBlockY;
-    const bool active = x < p.nx && y < p.ny;
-    if (!active) continue;
-    T h[9];
-    pull_node<S>(p, src, interior, x, y, h);
-    const long long i = (long long)y * p.pitch + x;
-    const uint8_t m = p.mask[i];
-    const Macro<T> q = macros<T>(p, h, m, x, y);
-    if (COLL == kSrt)
-      collide_srt<T>(p, h, q);
-    else
-      collide_mrt<T>(p, h, q);
-#pragma unroll
-    for (int a = 0; a < 9; ++a) S::store(dst + (long long)a * p.plane + i, h[a], a);
-    if (!(q.rho > T(0)) || !isfinite(q.ux) || !isfinite(q.uy)) atomicOr(p.flag, 1);
+  auto finish_node = [&](const Macro<T>& q, uint8_t m) {
+    if (!(q.rho > T(0)) || !finite_value(q.ux) || !finite_value(q.uy)) atomicOr(p.flag, 1);
     dm += q.drho;
     if (m) {
       any_solid = true;
       bfx -= double(q.fpx);
       bfy -= double(q.fpy);
     }
+  };
+
+  if (interior) {
+#pragma unroll 1
+    for (int r = 0; r < kRows; ++r) {
+      const int y = y0 + warp + r * kWarps;
+      T h[N][9];
+      pull_dir_vec<S, N, 0>(p, src, xb, y, lane, h);
+      pull_dir_vec<S, N, 1>(p, src, xb, y, lane, h);
+      pull_dir_vec<S, N, 2>(p, src, xb, y, lane, h);
+      pull_dir_vec<S, N, 3>(p, src, xb, y, lane, h);
+      pull_dir_vec<S, N, 4>(p, src, xb, y, lane, h);
+      pull_dir_vec<S, N, 5>(p, src, xb, y, lane, h);
+      pull_dir_vec<S, N, 6>(p, src, xb, y, lane, h);
+      pull_dir_vec<S, N, 7>(p, src, xb, y, lane, h);
+      pull_dir_vec<S, N, 8>(p, src, xb, y, lane, h);
+      const long long i = (long long)y * p.pitch + xb;
+      uint8_t m[N];
+      if (N == 4) {
+        const uchar4 mv = *reinterpret_cast<const uchar4*>(p.mask + i);
+        m[0] = mv.x;
+        m[1] = mv.y;
+        m[2 % N] = mv.z;
+        m[3 % N] = mv.w;
+      } else {
+        const uchar2 mv = *reinterpret_cast<const uchar2*>(p.mask + i);
+        m[0] = mv.x;
+        m[1 % N] = mv.y;
+      }
+      E o[9][N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const Macro<T> q = macros<T>(p, h[k], m[k], xb + k, y);
+        if (COLL == kSrt)
+          collide_srt<T>(p, h[k], q);
+        else
+          collide_mrt<T>(p, h[k], q);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) o[a][k] = S::out(h[k][a], a);
+        finish_node(q, m[k]);
+      }
+#pragma unroll
+      for (int a = 0; a < 9; ++a) S::store_chunk(dst + (long long)a * p.plane + i, o[a]);
+    }
+  } else {
+#pragma unroll 1
+    for (int r = 0; r < kRows; ++r) {
+      const int y = y0 + warp + r * kWarps;
+      if (y >= p.ny) break;
+#pragma unroll 1
+      for (int k = 0; k < N; ++k) {
+        const int x = xb + k;
+        if (x >= p.nx) break;
+        T h[9];
+        pull_node<S>(p, src, false, x, y, h);
+        const long long i = (long long)y * p.pitch + x;
+        const uint8_t m = p.mask[i];
+        const Macro<T> q = macros<T>(p, h, m, x, y);
+        if (COLL == kSrt)
+          collide_srt<T>(p, h, q);
+        else
+          collide_mrt<T>(p, h, q);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) store_h<S>(dst + (long long)a * p.plane + i, h[a], a);
+        finish_node(q, m);
+      }
+    }
   }
 
   // Per-step record: the block's force on solid nodes (FP64) and total density
   // (the arithmetic type within the block, FP64 from the tile up). Blocks
   // without solid nodes skip the FP64 work.
-  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5;
+  const int tid = lane + warp * kLanes;
   const bool warp_solid = __any_sync(0xffffffffu, any_solid);
   if (p.reduce_mass) dm = warp_sum(dm);
   if (warp_solid) {
     bfx = warp_sum(bfx);
     bfy = warp_sum(bfy);
   }
-  __shared__ T smass[kThreads / 32];
   if (lane == 0) {
     smass[warp] = dm;
     sm[warp][0] = bfx;
@@ -479,17 +643,17 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
   if (tid == 0) {
     T msum = T(0);
 #pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) msum += smass[w];
+    for (int w = 0; w < kWarps; ++w) msum += smass[w];
     if (block_solid) {
 #pragma unroll
-      for (int w = 0; w < kThreads / 32; ++w) {
+      for (int w = 0; w < kWarps; ++w) {
         ts[0] += sm[w][0];
         ts[1] += sm[w][1];
       }
     }
     if (p.reduce_mass) {
       // sum rho = active nodes + sum drho
-      const int nact = min(kTileX, p.nx - x0) * min(kTileY, p.ny - y0);
+      const int nact = min(TX, p.nx - x0) * min(kTileY, p.ny - y0);
       ts[2] = double(nact) + double(msum);
     }
   }
@@ -498,7 +662,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
 }
 
 template <int STORE, int COLL>
-__global__ void __launch_bounds__(kThreads, 4) fused_step_kernel(const __grid_constant__ StepParams p) {
+__global__ void __launch_bounds__(kThreads, 2) fused_step_kernel(const __grid_constant__ StepParams p) {
   step_tile<STORE, COLL>(p, blockIdx.x, p.t);
 }
 
@@ -507,7 +671,7 @@ __global__ void __launch_bounds__(kThreads, 4) fused_step_kernel(const __grid_co
 // parameter sets in a device array, for even and odd k (source and destination
 // buffers swapped); params[].t is the solver's step index at k = 0.
 template <int STORE, int COLL>
-__global__ void __launch_bounds__(kThreads, 4) fused_group_kernel(const StepParams* __restrict__ params,
+__global__ void __launch_bounds__(kThreads, 2) fused_group_kernel(const StepParams* __restrict__ params,
                                                                   const GroupTile* __restrict__ table,
                                                                   long long k) {
   const GroupTile gt = table[blockIdx.x];
@@ -556,7 +720,7 @@ __global__ void init_kernel(const __grid_constant__ StepParams p, void* dst, con
   for (int a = 0; a < 9; ++a) {
     const T xu = T(cx(a)) * ux + T(cy(a)) * uy;
     const T heq = wgt<T>(a) * (common + rho * xu * (T(3) + T(4.5) * xu));
-    S::store(d + (long long)a * p.plane + i, heq, a);
+    store_h<S>(d + (long long)a * p.plane + i, heq, a);
   }
 }
 

@@ -15,9 +15,9 @@ static dim3 node_grid(const StepParams& p) {
 
 cudaError_t VPLBM_FN(launch_fused_)(int coll, const StepParams& p, cudaStream_t st) {
   if (coll == kSrt)
-    fused_step_kernel<VPLBM_STORE, kSrt><<<p.n_tiles, dim3(kBlockX, kBlockY), 0, st>>>(p);
+    fused_step_kernel<VPLBM_STORE, kSrt><<<p.n_tiles, dim3(kLanes, kWarps), 0, st>>>(p);
   else
-    fused_step_kernel<VPLBM_STORE, kMrt><<<p.n_tiles, dim3(kBlockX, kBlockY), 0, st>>>(p);
+    fused_step_kernel<VPLBM_STORE, kMrt><<<p.n_tiles, dim3(kLanes, kWarps), 0, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -25,9 +25,9 @@ cudaError_t VPLBM_FN(launch_group_)(int coll, const StepParams* d_params, const 
                                     int n_blocks, long long k, cudaStream_t st) {
   if (n_blocks <= 0) return cudaSuccess;
   if (coll == kSrt)
-    fused_group_kernel<VPLBM_STORE, kSrt><<<n_blocks, dim3(kBlockX, kBlockY), 0, st>>>(d_params, d_table, k);
+    fused_group_kernel<VPLBM_STORE, kSrt><<<n_blocks, dim3(kLanes, kWarps), 0, st>>>(d_params, d_table, k);
   else
-    fused_group_kernel<VPLBM_STORE, kMrt><<<n_blocks, dim3(kBlockX, kBlockY), 0, st>>>(d_params, d_table, k);
+    fused_group_kernel<VPLBM_STORE, kMrt><<<n_blocks, dim3(kLanes, kWarps), 0, st>>>(d_params, d_table, k);
   return cudaGetLastError();
 }
 

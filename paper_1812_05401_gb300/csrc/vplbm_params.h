@@ -11,12 +11,21 @@ enum { kSrt = 0, kMrt = 1 };
 enum { kBcPeriodic = 0, kBcInletOutlet = 1, kBcFreeSlip = 2 };
 
 constexpr int kMaxBodies = 8;
-constexpr int kBlockX = 64;             // threads per block along x (one node each)
-constexpr int kBlockY = 4;              // threads per block along y
-constexpr int kRows = 8;                // rows each thread processes
-constexpr int kThreads = kBlockX * kBlockY;
-constexpr int kTileX = kBlockX;         // tile of one block: kTileX x kTileY nodes
-constexpr int kTileY = kBlockY * kRows;
+// Fused-step tiles: a block is 8 warps; each warp covers one row segment of
+// 32 lanes x npt(storage) consecutive nodes and kRows rows (8 apart), so a
+// tile is (32 npt) x 32 nodes. npt makes each lane's access 16 bytes for
+// FP32/FP64 storage (8 bytes for the 16-bit forms).
+constexpr int kLanes = 32;
+constexpr int kWarps = 8;
+constexpr int kRows = 4;
+constexpr int kThreads = kLanes * kWarps;
+constexpr int kTileY = kWarps * kRows;
+__host__ __device__ constexpr int npt(int storage) { return storage == kF64 ? 2 : 4; }
+__host__ __device__ constexpr int tile_x(int storage) { return kLanes * npt(storage); }
+
+// Block shape of the per-node kernels (initialisation, moments, import/export).
+constexpr int kBlockX = 64;
+constexpr int kBlockY = 4;
 constexpr int kGroup = 256;             // tiles per first-level reduction group
 constexpr uint8_t kStaticSolid = 255;   // mask value of a node solid through the static mask
 
