@@ -189,6 +189,51 @@ int64_t vplbm_launch_count(const vplbm_solver* s);
 vplbm_status vplbm_enable_timing(vplbm_solver* s, int32_t enable);
 vplbm_status vplbm_fused_timing(vplbm_solver* s, double* total_ms, int64_t* launches);
 
+/* One fused time step that allocates nothing (the paper has no counterpart:
+ * this is a service for callers that cannot allocate device memory when they
+ * step, such as code being captured into a CUDA graph, a host callback, a
+ * real-time loop with a fixed memory budget, or a framework that owns every
+ * allocation itself). The caller owns all the state; the library only runs
+ * the fused kernel of vplbm_step on it.
+ *
+ *  cfg       the solver's configuration (nx, ny, collision, storage, boundary
+ *            conditions, tau, lambda, eta, u_in, body_force, rates,
+ *            reduce_mass, stream); rho0, u0 and force_ring_len are unused.
+ *  bodies    host array of n_bodies <= VPLBM_MAX_BODIES rigid bodies, evaluated
+ *            at step t, or NULL with n_bodies = 0.
+ *  f_src     device populations f*(t) in the storage type, [9][ny][pitch]
+ *            (offsets f - w for the 16-bit forms), 16-byte aligned.
+ *  f_dst     device output f*(t+1), same layout; must not alias f_src.
+ *  mask      device [ny][pitch] bytes: 0 fluid, k = 1..n_bodies solid of body
+ *            k (solid velocity from its motion), 255 solid with the velocity
+ *            from us. Other values are not allowed.
+ *  us        device solid velocity, float2 (double2 for VPLBM_F64 storage)
+ *            [ny][pitch], read at mask = 255 nodes, or NULL for u_s = 0.
+ *  pitch     row length in elements: >= nx and a multiple of 8.
+ *  t         step index (body positions and the record's meaning).
+ *  record    device output of 3 doubles: F_x, F_y on the solids and the total
+ *            density (0 if reduce_mass = 0), as in vplbm_forces.
+ *  flag      device int set to 1 if the step produced rho <= 0 or a
+ *            non-finite velocity (never cleared here), or NULL.
+ *
+ * Scratch: the per-tile and per-group reduction sums live in a fixed 1 MiB
+ * device array inside the library, which every GPU that loads the library
+ * holds until the process exits. Grids needing more than that (about 40,000
+ * tiles, e.g. 160M nodes with FP32 storage) are rejected with
+ * VPLBM_ERR_INVALID and a message; use vplbm_create/vplbm_step for them.
+ * The first call on a device looks up the array's device address (done once
+ * per device, with that device current); make that first call before any
+ * stream capture. Each call clears the array's counters on cfg->stream
+ * before launching. All calls share the one array, so calls whose kernels
+ * can overlap on the GPU (different streams without ordering) race and give
+ * wrong results: order them on one stream. Asynchronous on cfg->stream;
+ * returns VPLBM_ERR_INVALID for bad arguments and VPLBM_ERR_CUDA if a CUDA
+ * call fails. Calls no allocating routine. */
+vplbm_status vplbm_step_noalloc(const vplbm_config* cfg, const vplbm_body* bodies,
+                                int32_t n_bodies, const void* f_src, void* f_dst,
+                                const uint8_t* mask, const void* us, int32_t pitch,
+                                int64_t t, double* record, int* flag);
+
 /* Message for the last failing call on this handle (never NULL). */
 const char* vplbm_last_error(const vplbm_solver* s);
 const char* vplbm_status_string(vplbm_status st);

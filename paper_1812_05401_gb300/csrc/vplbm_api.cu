@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -960,3 +961,174 @@ void vplbm_destroy(vplbm_solver* s) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free single step (vplbm_step_noalloc)
+//
+// For callers that cannot allocate device memory at the point where they
+// step: code running inside a CUDA graph being built, a host callback, a
+// real-time loop with a fixed memory budget, or a framework that owns every
+// allocation itself. The reduction scratch of the fused step (per-tile and
+// per-group partial sums and the arrival counters) lives in the fixed array
+// below instead of per-solver cudaMalloc'd buffers. Every GPU that loads this
+// library holds the array until the process exits.
+// ===========================================================================
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(1) << 20;  // 1 MiB
+
+// Shared by every call on a device; the last call's contents stay in it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+
+// Byte layout of the scratch for n_tiles tiles: partials, group partials,
+// counters, divergence flag. Returns the bytes used.
+size_t noalloc_layout(int n_tiles, size_t* off_group, size_t* off_counters, size_t* off_flag) {
+  const int n_groups = (n_tiles + kGroup - 1) / kGroup;
+  size_t off = 3 * sizeof(double) * size_t(n_tiles);
+  *off_group = off;
+  off += 3 * sizeof(double) * size_t(n_groups);
+  *off_counters = off;
+  off += sizeof(unsigned) * size_t(n_groups + 1);
+  off = (off + 15) & ~size_t(15);
+  *off_flag = off;
+  off += sizeof(int);
+  return off;
+}
+
+}  // namespace
+
+extern "C" vplbm_status vplbm_step_noalloc(const vplbm_config* cfg, const vplbm_body* bodies,
+                                           int32_t n_bodies, const void* f_src, void* f_dst,
+                                           const uint8_t* mask, const void* us, int32_t pitch,
+                                           int64_t t, double* record, int* flag) {
+  std::string why;
+  if (validate(cfg, &why) != VPLBM_OK) {
+    std::fprintf(stderr, "vplbm_step_noalloc: %s\n", why.c_str());
+    return VPLBM_ERR_INVALID;
+  }
+  if (!f_src || !f_dst || !mask || !record || f_src == f_dst || t < 0 ||
+      n_bodies < 0 || n_bodies > kMaxBodies || (n_bodies > 0 && !bodies)) {
+    std::fprintf(stderr, "vplbm_step_noalloc: invalid pointer, step index or body count\n");
+    return VPLBM_ERR_INVALID;
+  }
+  if (pitch < cfg->nx || pitch % 8 != 0) {
+    std::fprintf(stderr, "vplbm_step_noalloc: pitch must be >= nx and a multiple of 8\n");
+    return VPLBM_ERR_INVALID;
+  }
+  int tx, ty, nt, ng;
+  tiles_of(cfg, &tx, &ty, &nt, &ng);
+  size_t off_group, off_counters, off_flag;
+  const size_t need = noalloc_layout(nt, &off_group, &off_counters, &off_flag);
+  if (need > kNoAllocScratchBytes) {
+    std::fprintf(stderr,
+                 "vplbm_step_noalloc: grid of %d x %d needs %zu bytes of reduction scratch; the "
+                 "fixed scratch holds %zu (use vplbm_create / vplbm_step for this size)\n",
+                 cfg->nx, cfg->ny, need, kNoAllocScratchBytes);
+    return VPLBM_ERR_INVALID;
+  }
+
+  // Set-up, once per device: the device address of the scratch array. The
+  // array's name is only a host-side stand-in in this code.
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    std::fprintf(stderr, "vplbm_step_noalloc: cudaGetDevice: %s\n", cudaGetErrorString(e));
+    return VPLBM_ERR_CUDA;
+  }
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess || !ptr) {
+        std::fprintf(stderr, "vplbm_step_noalloc: cudaGetSymbolAddress: %s\n", cudaGetErrorString(e));
+        return VPLBM_ERR_CUDA;
+      }
+      g_noalloc_addr[dev] = ptr;
+    }
+    base = g_noalloc_addr[dev];
+  }
+  unsigned char* sb = static_cast<unsigned char*>(base);
+  cudaStream_t stream = static_cast<cudaStream_t>(cfg->stream);
+
+  // The arrival counters must start at zero (a failed earlier call could have
+  // left them mid-count); the divergence slot too when the caller gives none.
+  const size_t zero_bytes = off_flag + sizeof(int) - off_counters;
+  if ((e = cudaMemsetAsync(sb + off_counters, 0, zero_bytes, stream)) != cudaSuccess) {
+    std::fprintf(stderr, "vplbm_step_noalloc: cudaMemsetAsync: %s\n", cudaGetErrorString(e));
+    return VPLBM_ERR_CUDA;
+  }
+
+  StepParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.src = f_src;
+  p.dst = f_dst;
+  p.mask = mask;
+  p.us = us;
+  p.nx = cfg->nx;
+  p.ny = cfg->ny;
+  p.pitch = pitch;
+  p.plane = (long long)pitch * cfg->ny;
+  p.bc_x = cfg->bc_x;
+  p.bc_y = cfg->bc_y;
+  p.tiles_x = tx;
+  p.n_tiles = nt;
+  Consts<double>& cd = p.cd;
+  cd.omega = 1.0 / cfg->tau;
+  cd.srt_pre = 1.0 - 1.0 / (2.0 * cfg->tau);
+  if (cfg->use_rates) {
+    cd.s_e = cfg->rates[1];
+    cd.s_eps = cfg->rates[2];
+    cd.s_qx = cfg->rates[4];
+    cd.s_qy = cfg->rates[6];
+    cd.s_pxx = cfg->rates[7];
+    cd.s_pxy = cfg->rates[8];
+  } else {
+    const double sn = 1.0 / cfg->tau;
+    const double sq = 1.0 / (0.5 + cfg->lambda / (1.0 / sn - 0.5));
+    cd.s_e = cd.s_eps = cd.s_pxx = cd.s_pxy = sn;
+    cd.s_qx = cd.s_qy = sq;
+  }
+  cd.a_s = 0.5 / cfg->eta;
+  cd.kappa_s = (1.0 / cfg->eta) / (1.0 + 0.5 / cfg->eta);
+  cd.gx = cfg->body_force[0];
+  cd.gy = cfg->body_force[1];
+  heq_host(1.0, cfg->u_in[0], cfg->u_in[1], cd.heq_in);
+  round_consts(&p);
+  p.n_bodies = n_bodies;
+  for (int b = 0; b < n_bodies; ++b) {
+    BodyState st;
+    body_state(bodies[b], t, &st);
+    const double v[5] = {st.cx, st.cy, st.vx, st.vy, st.omega};
+    for (int k = 0; k < 5; ++k) {
+      cd.body[b][k] = v[k];
+      p.cf.body[b][k] = float(v[k]);
+    }
+  }
+  p.partials = reinterpret_cast<double*>(sb);
+  p.group_partials = reinterpret_cast<double*>(sb + off_group);
+  p.counters = reinterpret_cast<unsigned*>(sb + off_counters);
+  p.flag = flag ? flag : reinterpret_cast<int*>(sb + off_flag);
+  p.ring = record;  // one record: ring of length 1
+  p.ring_len = 1;
+  p.reduce_mass = cfg->reduce_mass ? 1 : 0;
+  p.t = t;
+
+  switch (cfg->storage) {
+    case kF64: e = launch_fused_f64(cfg->collision, p, stream); break;
+    case kF32: e = launch_fused_f32(cfg->collision, p, stream); break;
+    case kF16: e = launch_fused_f16(cfg->collision, p, stream); break;
+    default: e = launch_fused_bf16(cfg->collision, p, stream); break;
+  }
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "vplbm_step_noalloc: launch: %s\n", cudaGetErrorString(e));
+    return VPLBM_ERR_CUDA;
+  }
+  return VPLBM_OK;
+}
