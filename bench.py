@@ -351,6 +351,35 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_serving(args, n_requests=None, rate=None, storage=None, quiet=False):
+    """The serving mix (Poisson arrivals; Couette or cylinder channel 50/50;
+    side log-uniform in 64..1024; Re in 20..500; SRT/MRT 50/50; 2000..20000
+    steps; FP32 or FP16-offset storage) through the continuous-batching
+    server. rate = 0: every request arrives at t = 0 (closed loop, capacity)."""
+    import torch
+
+    from paper_1812_05401_gb300 import inputs as I
+    from paper_1812_05401_gb300 import serve
+    n = n_requests or args.serve_requests
+    rate = args.serve_rate if rate is None else rate
+    reqs = I.serving_mix(n, rate=rate if rate > 0 else 1.0, seed=1234, storage=storage)
+    if rate <= 0:
+        for r in reqs:
+            r.arrival = 0.0
+    free, total = torch.cuda.mem_get_info()
+    srv = serve.Server(budget_bytes=int(0.5 * free), max_active=args.serve_slots,
+                       round_steps=args.serve_round)
+    torch.cuda.synchronize()
+    results, rep = srv.run(reqs, realtime=rate > 0)
+    rep.update({"requests": n, "arrival_rate_per_s": rate if rate > 0 else "all at t=0",
+                "storage": storage or "f32/f16 50-50", "budget_bytes": int(0.5 * free),
+                "slots": args.serve_slots, "round_steps": args.serve_round,
+                "rejected": len(srv.rejected)})
+    if not quiet:
+        print(json.dumps({"metric": "served solves/s (VP-LBM serving mix)", "serving": rep}), flush=True)
+    return rep
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -388,6 +417,11 @@ def main():
     ap.add_argument("--no-compare-f16", dest="compare_f16", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--serving", action="store_true", help="run only the serving mix")
+    ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--serve-rate", type=float, default=0.0)
+    ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--serve-round", type=int, default=500)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -397,7 +431,10 @@ def main():
         from paper_1812_05401_gb300 import build as B
         if not B.up_to_date():
             B.build()
-        run_gpu(args)
+        if args.serving:
+            run_serving(args)
+        else:
+            run_gpu(args)
 
 
 if __name__ == "__main__":

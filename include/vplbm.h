@@ -54,8 +54,9 @@ enum { VPLBM_SRT = 0, /* BGK, Eq. LatticeBoltz with Guo forcing, Eq. Guo1 */
        VPLBM_MRT = 1  /* Eq. equa_lbl_mrt with Lu forcing, Eq. Guo2 */ };
 
 /* Population storage. Arithmetic is FP64 for VPLBM_F64 and FP32 otherwise.
- * The *_OFFSET forms store f_alpha - w_alpha in 16 bits (round to nearest
- * even). */
+ * VPLBM_F64 stores f_alpha; VPLBM_F32 stores f_alpha - w_alpha in 32 bits
+ * (the same bytes, a finer rounding step); the *_OFFSET forms store
+ * f_alpha - w_alpha in 16 bits (round to nearest even). */
 enum { VPLBM_F64 = 0, VPLBM_F32 = 1, VPLBM_F16_OFFSET = 2, VPLBM_BF16_OFFSET = 3 };
 
 /* Boundary conditions, applied inside the pull (streaming) of each step.
@@ -202,7 +203,7 @@ vplbm_status vplbm_fused_timing(vplbm_solver* s, double* total_ms, int64_t* laun
  *  bodies    host array of n_bodies <= VPLBM_MAX_BODIES rigid bodies, evaluated
  *            at step t, or NULL with n_bodies = 0.
  *  f_src     device populations f*(t) in the storage type, [9][ny][pitch]
- *            (offsets f - w for the 16-bit forms), 16-byte aligned.
+ *            (f for FP64, offsets f - w otherwise), 16-byte aligned.
  *  f_dst     device output f*(t+1), same layout; must not alias f_src.
  *  mask      device [ny][pitch] bytes: 0 fluid, k = 1..n_bodies solid of body
  *            k (solid velocity from its motion), 255 solid with the velocity

@@ -7,8 +7,8 @@
 // (w: the D2Q9 weights). Equilibrium, forcing and both collision operators are
 // affine in f with the rest state w as a fixed point, so colliding h is the
 // same operation, and it keeps the small deviations from the rest state out of
-// the rounding of numbers near w. For FP32 storage h is formed exactly
-// (Sterbenz) when f lies within a factor two of w.
+// the rounding of numbers near w. FP32 and the 16-bit storage forms store h
+// itself; FP64 storage stores f.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -59,12 +59,18 @@ template <> struct Store<kF64> {
   }
 };
 template <> struct Store<kF32> {
+  // FP32 elements hold the offsets h = f - w as well: the same bytes as f,
+  // with the rounding step of |h| <~ 0.1 instead of that of f ~ w.
   using E = float;
   using T = float;
-  static __device__ __forceinline__ T in(E e, int a) { return e - wgt<T>(a); }
-  static __device__ __forceinline__ E out(T h, int a) { return h + wgt<T>(a); }
-  static __device__ __forceinline__ double to_f64(const E* p, int) { return double(*p); }
-  static __device__ __forceinline__ void from_f64(E* p, double f, int) { *p = float(f); }
+  static __device__ __forceinline__ T in(E e, int) { return e; }
+  static __device__ __forceinline__ E out(T h, int) { return h; }
+  static __device__ __forceinline__ double to_f64(const E* p, int a) {
+    return wgt<double>(a) + double(*p);
+  }
+  static __device__ __forceinline__ void from_f64(E* p, double f, int a) {
+    *p = float(f - wgt<double>(a));
+  }
   // npt = 4 consecutive elements as one 16-byte access
   static __device__ __forceinline__ void load_chunk(const E* p, E e[4]) {
     const float4 v = __ldg(reinterpret_cast<const float4*>(p));

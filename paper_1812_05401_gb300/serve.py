@@ -1,0 +1,157 @@
+"""Continuous-batching serving loop over grouped VP-LBM launches.
+
+Requests (inputs.Request: an arrival time and a workload) are admitted while
+both a slot and device memory (vplbm_footprint_bytes against a budget) are
+free, first come first served. Admitted solves stay resident on the device
+and advance together: each round is one vplbm_group_step call in which every
+active solve runs min(remaining, round_steps) steps, one grouped launch per
+time step and storage/collision class. Requests that arrive while rounds are
+on the GPU join at the next round boundary, so their work overlaps with the
+solves already running. A finished solve's force series is read back and its
+memory released once the GPU has completed its last round (CUDA event), which
+is the request's completion time; latency = completion - arrival.
+
+All solves share one CUDA stream (grouped launches require it); the host keeps
+up to two rounds in flight so that admission and retirement overlap with GPU
+work. Results do not depend on the mix: the grouped kernel is the same code
+as the single-solver step, with deterministic fixed-order reductions.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import vplbm as V
+
+
+@dataclass
+class Result:
+    rid: int
+    name: str
+    arrival: float
+    admitted: float
+    finished: float
+    steps: int
+    nodes: int
+    storage: str
+    collision: str
+    fx: np.ndarray = field(repr=False, default=None)
+    fy: np.ndarray = field(repr=False, default=None)
+    populations: np.ndarray | None = field(repr=False, default=None)
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+@dataclass
+class _Active:
+    req: object
+    solver: V.Solver
+    remaining: int
+    admitted: float
+    footprint: int
+
+
+class Server:
+    def __init__(self, budget_bytes: int, max_active: int = 64, round_steps: int = 500,
+                 stream=None, keep_populations: bool = False):
+        import torch
+        self.torch = torch
+        self.budget = int(budget_bytes)
+        self.max_active = int(max_active)
+        self.round_steps = int(round_steps)
+        self.stream = stream or torch.cuda.Stream()
+        self.keep_populations = keep_populations
+        self.rejected = []
+
+    def _create(self, w):
+        cfg, bodies = V.config_from_workload(w, ring_len=max(1, w.steps), stream=self.stream,
+                                             reduce_mass=False)
+        return V.Solver(cfg, bodies, w.initial_velocity()), V.vplbm_footprint_bytes(cfg)
+
+    def run(self, requests, realtime: bool = True):
+        """Serves the requests; returns (results, report). With realtime=False
+        every request counts as arrived at time 0."""
+        torch = self.torch
+        pending = deque(sorted(requests, key=lambda r: r.arrival))
+        active: list[_Active] = []
+        inflight = deque()  # (event, [finished _Active])
+        results = []
+        used = 0
+        t0 = time.perf_counter()
+
+        def now():
+            return time.perf_counter() - t0
+
+        def retire(block: bool):
+            nonlocal used
+            while inflight and (block or inflight[0][0].query() or len(inflight) > 2):
+                ev, fin = inflight.popleft()
+                ev.synchronize()
+                for a in fin:
+                    fx, fy, _ = a.solver.forces()
+                    pops = a.solver.populations() if self.keep_populations else None
+                    t_done = now()
+                    w = a.req.workload
+                    results.append(Result(a.req.rid, w.name, a.req.arrival if realtime else 0.0,
+                                          a.admitted, t_done, w.steps, w.nx * w.ny, w.storage,
+                                          w.collision, fx, fy, pops))
+                    a.solver.close()
+                    used -= a.footprint
+                if not block and not inflight:
+                    break
+
+        while pending or active or inflight:
+            t = now()
+            # admission: FIFO while a slot and memory are free
+            while pending and (not realtime or pending[0].arrival <= t) and len(active) < self.max_active:
+                req = pending[0]
+                cfg, _ = V.config_from_workload(req.workload, ring_len=max(1, req.workload.steps))
+                fp = V.vplbm_footprint_bytes(cfg)
+                if fp > self.budget:
+                    self.rejected.append(req.rid)
+                    pending.popleft()
+                    continue
+                if used + fp > self.budget:
+                    break
+                pending.popleft()
+                s, fp = self._create(req.workload)
+                used += fp
+                active.append(_Active(req, s, req.workload.steps, now(), fp))
+            if not active:
+                if inflight:
+                    retire(block=True)
+                    continue
+                if pending:
+                    time.sleep(max(0.0, min(0.01, pending[0].arrival - now())))
+                continue
+            steps = [min(a.remaining, self.round_steps) for a in active]
+            V.vplbm_group_step([a.solver.h for a in active], steps)
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
+            for a, k in zip(active, steps):
+                a.remaining -= k
+            done = [a for a in active if a.remaining == 0]
+            active = [a for a in active if a.remaining > 0]
+            inflight.append((ev, done))
+            retire(block=False)
+        retire(block=True)
+        t_end = now()
+        return results, self.report(results, t_end)
+
+    @staticmethod
+    def report(results, makespan: float):
+        lat = np.array([r.latency for r in results]) if results else np.zeros(1)
+        updates = float(sum(r.nodes * r.steps for r in results))
+        return {
+            "completed": len(results),
+            "makespan_s": round(makespan, 3),
+            "solves_per_s": round(len(results) / makespan, 3) if makespan > 0 else None,
+            "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
+            "p99_latency_s": round(float(np.percentile(lat, 99)), 4),
+            "mlups": round(updates / makespan / 1e6, 1) if makespan > 0 else None,
+        }

@@ -1,0 +1,80 @@
+"""Serving: continuous batching over grouped launches. Each solve's result is
+the same alone and in the mix (bitwise: the grouped kernel is the single-solver
+kernel with deterministic reductions), admission respects the memory budget,
+and requests arriving while others run are admitted and finish."""
+import numpy as np
+import pytest
+
+from paper_1812_05401_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1812_05401_gb300 import build as B
+    B.build()
+    from paper_1812_05401_gb300 import serve, vplbm
+    return serve, vplbm
+
+
+def _small_mix(n=14, seed=7):
+    reqs = I.serving_mix(n, rate=400.0, seed=seed, side_min=24, side_max=96, steps_min=40,
+                         steps_max=260)
+    return reqs
+
+
+def test_results_identical_alone_and_in_the_mix(mods):
+    serve, V = mods
+    reqs = _small_mix()
+    srv = serve.Server(budget_bytes=1 << 30, max_active=6, round_steps=64, keep_populations=True)
+    results, rep = srv.run(reqs, realtime=False)
+    assert rep["completed"] == len(reqs) and not srv.rejected
+    by_id = {r.rid: r for r in results}
+    for req in reqs[::3]:
+        with V.Solver.from_workload(req.workload, ring_len=max(1, req.workload.steps),
+                                    reduce_mass=False) as s:
+            s.step(req.workload.steps)
+            f = s.populations()
+            fx, fy, _ = s.forces()
+        r = by_id[req.rid]
+        assert np.array_equal(f, r.populations), req.workload.name
+        assert np.array_equal(fx, r.fx) and np.array_equal(fy, r.fy)
+
+
+def test_admission_by_memory_budget(mods):
+    serve, V = mods
+    reqs = _small_mix(8, seed=11)
+    fps = []
+    for r in reqs:
+        cfg, _ = V.config_from_workload(r.workload, ring_len=max(1, r.workload.steps))
+        fps.append(V.vplbm_footprint_bytes(cfg))
+    budget = max(fps) + min(fps)  # at most about two solves at a time
+    srv = serve.Server(budget_bytes=budget, max_active=8, round_steps=32)
+    results, rep = srv.run(reqs, realtime=False)
+    assert rep["completed"] == len(reqs)
+    # a request larger than the whole budget is rejected, not served
+    big = I.serving_mix(1, seed=3, side_min=900, side_max=1000, steps_min=10, steps_max=10)
+    srv2 = serve.Server(budget_bytes=budget, max_active=8, round_steps=32)
+    res2, rep2 = srv2.run(big, realtime=False)
+    assert rep2["completed"] == 0 and srv2.rejected == [big[0].rid]
+
+
+def test_late_arrivals_join_running_rounds(mods):
+    serve, V = mods
+    reqs = I.serving_mix(10, rate=400.0, seed=5, side_min=24, side_max=64, steps_min=1500,
+                         steps_max=3000)
+    # spread arrivals so that later ones arrive while earlier ones run
+    for i, r in enumerate(reqs):
+        r.arrival = 0.003 * i
+    srv = serve.Server(budget_bytes=1 << 30, max_active=8, round_steps=100)
+    results, rep = srv.run(reqs, realtime=True)
+    assert rep["completed"] == len(reqs)
+    assert all(r.finished >= r.arrival for r in results)
+    overlapped = sum(1 for a in results for b in results
+                     if a.rid != b.rid and a.admitted < b.finished and b.admitted < a.finished)
+    assert overlapped > 0
+    assert rep["p99_latency_s"] >= rep["p50_latency_s"] > 0

@@ -58,7 +58,8 @@ def _state(V, nx, ny, pitch, coll):
     assert np.array_equal(mask_host[:, :nx] != 0, m != 0)
     dev = torch.device("cuda")
     src = torch.zeros((9, ny, pitch), dtype=torch.float32, device=dev)
-    src[:, :, :nx] = torch.from_numpy(ref.populations().astype(np.float32)).to(dev)
+    # FP32 storage holds the offsets f - w
+    src[:, :, :nx] = torch.from_numpy((ref.populations() - w[:, None, None]).astype(np.float32)).to(dev)
     dst = torch.zeros_like(src)
     mask_d = torch.from_numpy(mask_host).to(dev)
     us_d = torch.zeros((ny, pitch, 2), dtype=torch.float32, device=dev)
@@ -66,14 +67,14 @@ def _state(V, nx, ny, pitch, coll):
     record = torch.zeros(3, dtype=torch.float64, device=dev)
     flag = torch.zeros(1, dtype=torch.int32, device=dev)
     bodies = (V.vplbm_body * 1)(V.vplbm_body(body.cx, body.cy, body.radius, 0, 0, 0, body.omega, 0, 0))
-    return cfg, ref, src, dst, mask_d, us_d, record, flag, bodies
+    return cfg, ref, src, dst, mask_d, us_d, record, flag, bodies, w
 
 
 @pytest.mark.parametrize("coll", ["mrt", "srt"])
 def test_noalloc_step_matches_regular_step_twice(V, coll):
     import torch
     nx, ny, pitch = 300, 70, 320
-    cfg, ref, src, dst, mask_d, us_d, record, flag, bodies = _state(V, nx, ny, pitch, coll)
+    cfg, ref, src, dst, mask_d, us_d, record, flag, bodies, w = _state(V, nx, ny, pitch, coll)
     L = V.lib()
     try:
         for t in range(2):
@@ -84,7 +85,7 @@ def test_noalloc_step_matches_regular_step_twice(V, coll):
             ref.step(1)
             torch.cuda.synchronize()
             f_ref = ref.populations()
-            f_new = dst[:, :, :nx].double().cpu().numpy()
+            f_new = dst[:, :, :nx].double().cpu().numpy() + w[:, None, None]
             assert np.abs(f_new - f_ref).max() < 4e-7
             fx, fy, ms = ref.forces()
             rec = record.cpu().numpy()
