@@ -59,6 +59,14 @@ enum { VPLBM_SRT = 0, /* BGK, Eq. LatticeBoltz with Guo forcing, Eq. Guo1 */
  * f_alpha - w_alpha in 16 bits (round to nearest even). */
 enum { VPLBM_F64 = 0, VPLBM_F32 = 1, VPLBM_F16_OFFSET = 2, VPLBM_BF16_OFFSET = 3 };
 
+/* Rounding of the 16-bit stores. NEAREST: round to nearest even.
+ * STOCHASTIC (the default): round up or down with probabilities given by the
+ * distance to the two neighbouring 16-bit values, from counter-based random
+ * bits (a hash of the node, the direction and the step), so rounding errors
+ * average out instead of acting as a systematic forcing. Ignored for
+ * FP64/FP32 storage. */
+enum { VPLBM_ROUND_NEAREST = 0, VPLBM_ROUND_STOCHASTIC = 1 };
+
 /* Boundary conditions, applied inside the pull (streaming) of each step.
  * x: PERIODIC, or INLET_OUTLET: a ghost column x = -1 held at f_eq(1, u_in)
  *    (uniform velocity inlet) and a ghost column x = nx that repeats column
@@ -99,14 +107,15 @@ typedef struct {
   double body_force[2];    /* uniform force per unit mass g (f_tot = f_pen + rho g) */
   double rates[9];         /* explicit MRT S diagonal when use_rates = 1 */
   int32_t force_ring_len;  /* steps of (F_x, F_y, mass) kept on the device; >= 1 */
-  int32_t reserved;
+  int32_t rounding;        /* VPLBM_ROUND_NEAREST | VPLBM_ROUND_STOCHASTIC (16-bit stores) */
   void* stream;            /* cudaStream_t to run on, or NULL for a private stream */
 } vplbm_config;
 
 typedef struct vplbm_solver vplbm_solver;
 
 /* Fills cfg with defaults: SRT, FP32, periodic, tau 0.8, Lambda 3/16,
- * eta 1e-7, rho0 1, mass reduction on, ring of 4096 steps. nx = ny = 0. */
+ * eta 1e-7, rho0 1, mass reduction on, ring of 4096 steps, stochastic
+ * rounding of 16-bit stores. nx = ny = 0. */
 void vplbm_config_init(vplbm_config* cfg);
 
 /* Relaxation time for a reference speed u_ref, length l_ref and Reynolds

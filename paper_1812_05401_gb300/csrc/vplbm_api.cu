@@ -374,6 +374,8 @@ vplbm_status validate(const vplbm_config* c, std::string* why) {
     return *why = "lambda must be > 0", VPLBM_ERR_INVALID;
   if (!(c->rho0 > 0.0)) return *why = "rho0 must be > 0", VPLBM_ERR_INVALID;
   if (c->force_ring_len < 1) return *why = "force_ring_len must be >= 1", VPLBM_ERR_INVALID;
+  if (c->rounding != VPLBM_ROUND_NEAREST && c->rounding != VPLBM_ROUND_STOCHASTIC)
+    return *why = "unknown rounding", VPLBM_ERR_INVALID;
   return VPLBM_OK;
 }
 
@@ -445,6 +447,7 @@ void vplbm_config_init(vplbm_config* c) {
   c->eta = 1e-7;
   c->rho0 = 1.0;
   c->force_ring_len = 4096;
+  c->rounding = VPLBM_ROUND_STOCHASTIC;
 }
 
 double vplbm_tau_from_reynolds(double u_ref, double l_ref, double re) {
@@ -565,6 +568,7 @@ vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
   p.flag = s->flag;
   p.ring_len = cfg->force_ring_len;
   p.reduce_mass = cfg->reduce_mass ? 1 : 0;
+  p.stochastic = cfg->rounding == VPLBM_ROUND_STOCHASTIC ? 1 : 0;
 
   if ((st = vplbm_set_initial_velocity(s, nullptr)) != VPLBM_OK) return bail(st);
   *out = s;
@@ -1118,6 +1122,7 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_config* cfg, const vplbm_
   p.ring = record;  // one record: ring of length 1
   p.ring_len = 1;
   p.reduce_mass = cfg->reduce_mass ? 1 : 0;
+  p.stochastic = cfg->rounding == VPLBM_ROUND_STOCHASTIC ? 1 : 0;
   p.t = t;
 
   switch (cfg->storage) {

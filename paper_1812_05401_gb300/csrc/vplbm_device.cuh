@@ -44,6 +44,8 @@ template <int S> struct Store;
 template <> struct Store<kF64> {
   using E = double;
   using T = double;
+  static constexpr bool kSixteen = false;
+  static __device__ __forceinline__ E out_sr(T h, int a, unsigned) { return out(h, a); }
   static __device__ __forceinline__ T in(E e, int a) { return e - wgt<T>(a); }
   static __device__ __forceinline__ E out(T h, int a) { return h + wgt<T>(a); }
   static __device__ __forceinline__ double to_f64(const E* p, int) { return *p; }
@@ -63,8 +65,10 @@ template <> struct Store<kF32> {
   // with the rounding step of |h| <~ 0.1 instead of that of f ~ w.
   using E = float;
   using T = float;
+  static constexpr bool kSixteen = false;
   static __device__ __forceinline__ T in(E e, int) { return e; }
   static __device__ __forceinline__ E out(T h, int) { return h; }
+  static __device__ __forceinline__ E out_sr(T h, int a, unsigned) { return out(h, a); }
   static __device__ __forceinline__ double to_f64(const E* p, int a) {
     return wgt<double>(a) + double(*p);
   }
@@ -88,6 +92,7 @@ template <class H>
 struct Store16 {
   using E = H;
   using T = float;
+  static constexpr bool kSixteen = true;
   static __device__ __forceinline__ void load_chunk(const E* p, E e[4]) {
     const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
     e[0] = __ushort_as_half_or_bf16(static_cast<unsigned short>(v.x & 0xffffu));
@@ -120,9 +125,23 @@ template <>
 __device__ __forceinline__ unsigned short Store16<__nv_bfloat16>::bits(__nv_bfloat16 e) {
   return __bfloat16_as_ushort(e);
 }
+// Stochastic rounding of an FP32 value to a format keeping the top 23 - DROP
+// significand bits: add DROP uniformly random bits (the top bits of r) below
+// the kept ones to the magnitude and truncate, so the value rounds up with
+// probability equal to its distance from the lower neighbour (exact for
+// normal results).
+template <int DROP>
+__device__ __forceinline__ float dither(float h, unsigned r) {
+  const unsigned b = __float_as_uint(h);
+  const unsigned mag = (b & 0x7fffffffu) + (r >> (32 - DROP));
+  return __uint_as_float((b & 0x80000000u) | mag);
+}
 template <> struct Store<kF16> : Store16<__half> {
   static __device__ __forceinline__ T in(E e, int) { return __half2float(e); }
   static __device__ __forceinline__ E out(T h, int) { return __float2half_rn(h); }
+  static __device__ __forceinline__ E out_sr(T h, int, unsigned r) {
+    return __float2half_rz(dither<13>(h, r));
+  }
   static __device__ __forceinline__ double to_f64(const E* p, int a) {
     return wgt<double>(a) + double(__half2float(*p));
   }
@@ -133,6 +152,9 @@ template <> struct Store<kF16> : Store16<__half> {
 template <> struct Store<kBF16> : Store16<__nv_bfloat16> {
   static __device__ __forceinline__ T in(E e, int) { return __bfloat162float(e); }
   static __device__ __forceinline__ E out(T h, int) { return __float2bfloat16_rn(h); }
+  static __device__ __forceinline__ E out_sr(T h, int, unsigned r) {
+    return __float2bfloat16_rz(dither<16>(h, r));
+  }
   static __device__ __forceinline__ double to_f64(const E* p, int a) {
     return wgt<double>(a) + double(__bfloat162float(*p));
   }
@@ -158,6 +180,35 @@ __device__ __forceinline__ typename S::T load_h(const typename S::E* p, int a) {
 template <class S>
 __device__ __forceinline__ void store_h(typename S::E* p, typename S::T h, int a) {
   *p = S::out(h, a);
+}
+
+// Random bits of the stochastic rounding: the MurmurHash3 32-bit finalizer
+// (Appleby) of the node's index mixed with the step's key gives one uniform
+// 32-bit word per node; direction alpha uses the word times a distinct odd
+// constant (a bijection of 32-bit words, so each direction's bits are again
+// uniform) and takes its top bits.
+__device__ __forceinline__ unsigned round_bits(unsigned counter, unsigned key) {
+  unsigned h = counter ^ key;
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+__device__ __forceinline__ constexpr unsigned round_mul(int a) {
+  return a == 0 ? 0x9e3779b1u : a == 1 ? 0x85ebca77u : a == 2 ? 0xc2b2ae3du : a == 3 ? 0x27d4eb2fu
+       : a == 4 ? 0x165667b1u : a == 5 ? 0xd3a2646du : a == 6 ? 0xfd7046c5u : a == 7 ? 0xb55a4f09u
+       : 0x68e31da5u;
+}
+
+// node_bits: round_bits(node, key of the step), so every step draws fresh bits.
+template <class S>
+__device__ __forceinline__ typename S::E out_value(const StepParams& p, typename S::T h, int a,
+                                                   unsigned node_bits) {
+  if (S::kSixteen && p.stochastic) return S::out_sr(h, a, node_bits * round_mul(a));
+  return S::out(h, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -551,6 +602,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
   T dm = T(0);                 // sum of drho over this thread's nodes
   double bfx = 0.0, bfy = 0.0;  // force on solid nodes (FP64 from the node up)
   bool any_solid = false;
+  const unsigned key = round_bits(unsigned(t), 0x9e3779b9u);
 
   auto finish_node = [&](const Macro<T>& q, uint8_t m) {
     if (!(q.rho > T(0)) || !finite_value(q.ux) || !finite_value(q.uy)) atomicOr(p.flag, 1);
@@ -597,8 +649,10 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
           collide_srt<T>(p, h[k], q);
         else
           collide_mrt<T>(p, h[k], q);
+        const unsigned nb = (S::kSixteen && p.stochastic)
+                                ? round_bits(unsigned((long long)y * p.nx + (xb + k)), key) : 0u;
 #pragma unroll
-        for (int a = 0; a < 9; ++a) o[a][k] = S::out(h[k][a], a);
+        for (int a = 0; a < 9; ++a) o[a][k] = out_value<S>(p, h[k][a], a, nb);
         finish_node(q, m[k]);
       }
 #pragma unroll
@@ -622,8 +676,10 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
           collide_srt<T>(p, h, q);
         else
           collide_mrt<T>(p, h, q);
+        const unsigned nb = (S::kSixteen && p.stochastic)
+                                ? round_bits(unsigned((long long)y * p.nx + x), key) : 0u;
 #pragma unroll
-        for (int a = 0; a < 9; ++a) store_h<S>(dst + (long long)a * p.plane + i, h[a], a);
+        for (int a = 0; a < 9; ++a) dst[(long long)a * p.plane + i] = out_value<S>(p, h[a], a, nb);
         finish_node(q, m);
       }
     }

@@ -69,6 +69,7 @@ struct StepParams {
   long long t;              // index of this step
   int ring_len;
   int reduce_mass;
+  int stochastic;           // 16-bit stores: 1 = stochastic rounding, 0 = nearest even
 };
 
 template <class T> __host__ __device__ inline const Consts<T>& consts(const StepParams& p);

@@ -26,6 +26,7 @@ VPLBM_SRT, VPLBM_MRT = 0, 1
 VPLBM_F64, VPLBM_F32, VPLBM_F16_OFFSET, VPLBM_BF16_OFFSET = 0, 1, 2, 3
 VPLBM_BC_PERIODIC, VPLBM_BC_INLET_OUTLET, VPLBM_BC_FREE_SLIP = 0, 1, 2
 VPLBM_MAX_BODIES = 8
+VPLBM_ROUND_NEAREST, VPLBM_ROUND_STOCHASTIC = 0, 1
 
 STORAGE = {"f64": VPLBM_F64, "f32": VPLBM_F32, "f16": VPLBM_F16_OFFSET, "bf16": VPLBM_BF16_OFFSET}
 COLLISION = {"srt": VPLBM_SRT, "mrt": VPLBM_MRT}
@@ -45,7 +46,7 @@ class vplbm_config(C.Structure):
                 ("tau", C.c_double), ("lam", C.c_double), ("eta", C.c_double),
                 ("u_in", C.c_double * 2), ("rho0", C.c_double), ("u0", C.c_double * 2),
                 ("body_force", C.c_double * 2), ("rates", C.c_double * 9),
-                ("force_ring_len", C.c_int32), ("reserved", C.c_int32), ("stream", C.c_void_p)]
+                ("force_ring_len", C.c_int32), ("rounding", C.c_int32), ("stream", C.c_void_p)]
 
 
 class VplbmError(RuntimeError):
@@ -255,7 +256,8 @@ def vplbm_destroy(h):
 
 def make_config(nx, ny, collision="srt", storage="f32", tau=0.8, lam=3.0 / 16.0, eta=1e-7,
                 bc="periodic", u_in=(0.0, 0.0), u0=(0.0, 0.0), rho0=1.0, body_force=(0.0, 0.0),
-                rates=None, reduce_mass=True, ring_len=4096, stream=None) -> vplbm_config:
+                rates=None, reduce_mass=True, ring_len=4096, stream=None,
+                rounding="stochastic") -> vplbm_config:
     c = vplbm_config_init()
     c.nx, c.ny = int(nx), int(ny)
     c.collision = COLLISION[collision] if isinstance(collision, str) else int(collision)
@@ -277,18 +279,21 @@ def make_config(nx, ny, collision="srt", storage="f32", tau=0.8, lam=3.0 / 16.0,
             c.rates[k] = rates[k]
     c.reduce_mass = int(bool(reduce_mass))
     c.force_ring_len = int(ring_len)
+    c.rounding = {"nearest": VPLBM_ROUND_NEAREST, "stochastic": VPLBM_ROUND_STOCHASTIC}[rounding] \
+        if isinstance(rounding, str) else int(rounding)
     if stream is not None:
         c.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     return c
 
 
-def config_from_workload(w, ring_len: int = 4096, stream=None, reduce_mass: bool = True):
+def config_from_workload(w, ring_len: int = 4096, stream=None, reduce_mass: bool = True,
+                         rounding: str = "stochastic"):
     """vplbm_config and body list for an inputs.Workload (tau from its
     Reynolds number when it gives one)."""
     tau = w.tau if w.tau is not None else vplbm_tau_from_reynolds(w.u_ref, w.l_ref, w.re)
     u_in = (w.u_ref, 0.0) if w.bc == "channel" else (0.0, 0.0)
     cfg = make_config(w.nx, w.ny, w.collision, w.storage, tau, w.lam, bc=w.bc, u_in=u_in,
-                      ring_len=ring_len, stream=stream, reduce_mass=reduce_mass)
+                      ring_len=ring_len, stream=stream, reduce_mass=reduce_mass, rounding=rounding)
     return cfg, list(w.bodies)
 
 
@@ -310,8 +315,8 @@ class Solver:
 
     @classmethod
     def from_workload(cls, w, stream=None, ring_len: int = 4096, reduce_mass: bool = True,
-                      with_initial_velocity: bool = True):
-        cfg, bodies = config_from_workload(w, ring_len, stream, reduce_mass)
+                      with_initial_velocity: bool = True, rounding: str = "stochastic"):
+        cfg, bodies = config_from_workload(w, ring_len, stream, reduce_mass, rounding)
         return cls(cfg, bodies, w.initial_velocity() if with_initial_velocity else None)
 
     def close(self):

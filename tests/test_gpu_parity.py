@@ -97,10 +97,46 @@ def test_one_step_random_state(storage, coll, bc):
         assert fx[0] == pytest.approx(fx_ref[0], rel=1e-5, abs=1e-6)
         assert ms[0] == pytest.approx(m_ref[0], rel=1e-7)
     else:
-        # stored offsets h = f - w: half an ulp of |h| <= 0.06 plus FP32 arithmetic
-        ulp = 2.0 ** -11 if storage == "f16" else 2.0 ** -8
+        # stored offsets h = f - w, stochastically rounded: one ulp of
+        # |h| <= 0.06 plus FP32 arithmetic
+        ulp = 2.0 ** -10 if storage == "f16" else 2.0 ** -7
         assert np.abs(f - f_ref).max() < 0.06 * ulp + 1e-6
         assert fx[0] == pytest.approx(fx_ref[0], rel=1e-5, abs=1e-6)
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_one_step_16bit_nearest_rounding(storage):
+    """Round-to-nearest-even 16-bit stores: within half an ulp of |h|."""
+    nx, ny = 300, 37
+    ocfg, _ = _pair(nx, ny, "mrt", "f64", "channel", tau=0.62)
+    cfg = V.make_config(nx, ny, "mrt", storage, 0.62, bc=VBC["channel"], u_in=(0.04, 0.0),
+                        rounding="nearest")
+    with V.Solver(cfg) as s:
+        s.set_populations(I.random_populations(nx, ny, 13, 0.05))
+        f_ref = s.populations()
+        O.run(ocfg, f_ref, 1)
+        s.step(1)
+        f = s.populations()
+    ulp = 2.0 ** -11 if storage == "f16" else 2.0 ** -8
+    assert np.abs(f - f_ref).max() < 0.06 * ulp + 1e-6
+
+
+def test_stochastic_rounding_is_unbiased():
+    """Stochastic 16-bit rounding: the mean rounding error over many nodes is
+    far below the rounding step (nearest rounding of the same values is not
+    required to be; both stay within their per-value bounds)."""
+    nx, ny = 512, 256
+    ocfg, _ = _pair(nx, ny, "srt", "f64", "periodic", tau=0.9)
+    with V.Solver(V.make_config(nx, ny, "srt", "f16", 0.9, rounding="stochastic")) as s:
+        s.set_populations(I.random_populations(nx, ny, 17, 0.05))
+        f_ref = s.populations()
+        O.run(ocfg, f_ref, 1)
+        s.step(1)
+        err = s.populations() - f_ref
+    ulp = 2.0 ** -10 * 0.06
+    assert np.abs(err).max() < ulp + 1e-6
+    # per direction, the mean error of 131072 independent roundings is ~0
+    assert np.abs(err.reshape(9, -1).mean(axis=1)).max() < 2e-2 * 2.0 ** -11 * 0.02
 
 
 @pytest.mark.parametrize("nx,ny", [(1, 1), (1, 5), (7, 1), (2, 2), (128, 2), (129, 3), (256, 4), (3, 130)])

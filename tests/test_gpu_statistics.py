@@ -12,12 +12,16 @@ same state and runs 60,000 more steps (~14 shedding periods), all of which
 enter the statistics. The FP64 GPU path is the reference: it is held to the
 FP64 oracle within 1e-12 over 1000 steps in test_gpu_parity.
 
-Tolerance: 1e-3 relative on C_Dave and St for FP32 storage (measured:
-4.5e-4 and 3.5e-4). The 16-bit offset forms with round-to-nearest-even do not
-reach 1e-3 on this flow: rounding f - w (~0.02) to 11 significant bits is about
-20 times the viscous change of a population per step, and the deterministic
-rounding acts as a small systematic forcing (measured: FP16 C_Dave +4.5%,
-St +3%; BF16 C_Dave +8%). Their bounds here are the measured ones with margin.
+Tolerances (relative, C_Dave and St from the spectral peak):
+  FP32 storage                       1e-3 (measured 4.5e-4, 3.6e-4)
+  FP16 offsets, stochastic rounding  1e-3 (measured 6.5e-4, 8.7e-4)
+  BF16 offsets, stochastic rounding  1e-2 (measured 4.4e-3, 3.7e-3)
+With round-to-nearest-even the 16-bit forms do not reach 1e-3 on this flow:
+rounding f - w (~0.02) to 11 significant bits is about 20 times the viscous
+change of a population per step, and a deterministic rounding acts as a small
+systematic forcing (measured: FP16 C_Dave +4.5%, St +3%; BF16 C_Dave +8%,
+St -1.2%). Those bounds are the measured ones with margin. Stochastic
+rounding, the default for the 16-bit forms, removes the correlation.
 """
 import numpy as np
 import pytest
@@ -30,9 +34,9 @@ DEVELOP, MEASURE = 60_000, 60_000
 _cache = {}
 
 
-def _run(storage):
-    if storage in _cache:
-        return _cache[storage]
+def _run(storage, rounding="nearest"):
+    if (storage, rounding) in _cache:
+        return _cache[(storage, rounding)]
     import torch
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
@@ -50,13 +54,13 @@ def _run(storage):
     w = I.c2_cylinder_re100()
     w.storage = storage
     with V.Solver.from_workload(w, ring_len=MEASURE, reduce_mass=False,
-                                with_initial_velocity=False) as s:
+                                with_initial_velocity=False, rounding=rounding) as s:
         s.set_populations(_cache["developed"])
         s.step(MEASURE)
         s.synchronize()
         fx, fy, _ = s.forces()
     st = diag.wake_statistics(fx, fy, w.u_ref, w.l_ref, discard=0.0)
-    _cache[storage] = st
+    _cache[(storage, rounding)] = st
     return st
 
 
@@ -69,10 +73,21 @@ def test_fp64_wake_is_periodic_shedding():
 
 
 @pytest.mark.parametrize("storage,tol_cd,tol_st", [("f32", 1e-3, 1e-3), ("f16", 0.06, 0.05),
-                                                   ("bf16", 0.12, 0.08)])
-def test_reduced_precision_statistics(storage, tol_cd, tol_st):
+                                                   ("bf16", 0.12, 0.03)])
+def test_nearest_rounding_statistics(storage, tol_cd, tol_st):
     ref = _run("f64")
-    s = _run(storage)
-    print(storage, s, "ref", ref)
+    s = _run(storage, "nearest")
+    print(storage, "nearest", s, "ref", ref)
     assert s["C_D_ave"] == pytest.approx(ref["C_D_ave"], rel=tol_cd)
-    assert s["St_crossings"] == pytest.approx(ref["St_crossings"], rel=tol_st)
+    assert s["St"] == pytest.approx(ref["St"], rel=tol_st)
+
+
+@pytest.mark.parametrize("storage,tol_cd,tol_st", [("f16", 1e-3, 1e-3), ("bf16", 1e-2, 1e-2)])
+def test_stochastic_rounding_statistics(storage, tol_cd, tol_st):
+    """16-bit offsets with stochastic rounding: the rounding errors no longer
+    correlate with the flow, so they average out of the statistics."""
+    ref = _run("f64")
+    s = _run(storage, "stochastic")
+    print(storage, "stochastic", s, "ref", ref)
+    assert s["C_D_ave"] == pytest.approx(ref["C_D_ave"], rel=tol_cd)
+    assert s["St"] == pytest.approx(ref["St"], rel=tol_st)
