@@ -724,7 +724,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
 }
 
 template <int STORE, int COLL>
-__global__ void __launch_bounds__(kThreads, 2) fused_step_kernel(const __grid_constant__ StepParams p) {
+__global__ void __launch_bounds__(kThreads, min_blocks_per_sm(STORE)) fused_step_kernel(const __grid_constant__ StepParams p) {
   step_tile<STORE, COLL>(p, blockIdx.x, p.t);
 }
 
@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(kThreads, 2) fused_step_kernel(const __grid_co
 // parameter sets in a device array, for even and odd k (source and destination
 // buffers swapped); params[].t is the solver's step index at k = 0.
 template <int STORE, int COLL>
-__global__ void __launch_bounds__(kThreads, 2) fused_group_kernel(const StepParams* __restrict__ params,
+__global__ void __launch_bounds__(kThreads, min_blocks_per_sm(STORE)) fused_group_kernel(const StepParams* __restrict__ params,
                                                                   const GroupTile* __restrict__ table,
                                                                   long long k) {
   const GroupTile gt = table[blockIdx.x];
