@@ -138,6 +138,22 @@ def dist_env():
     return rank, world, local
 
 
+def replica_totals(units: float, ms: float, device=None):
+    """Whole-job totals of independent replicas: the units all ranks processed
+    (sum) and the slowest rank's time (max). Works on any initialised process
+    group (NCCL with CUDA tensors, gloo with CPU tensors); without one it
+    returns its inputs."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(units), float(ms)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    m = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(m.item())
+
+
 def make_workload(name: str, storage: str):
     from paper_1812_05401_gb300 import inputs as I
     if name == "moving-cylinder":
@@ -212,11 +228,7 @@ def run_gpu(args):
             dist.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replica_totals(0.0, x, dev)[1]
 
     w = make_workload(args.workload, args.storage)
     nodes = w.nx * w.ny
@@ -251,8 +263,8 @@ def run_gpu(args):
         s.synchronize()  # raises if the run diverged
         fused_ms, fused_n = V.vplbm_fused_timing(s.h)
         V.vplbm_enable_timing(s.h, False)
-        ms = max_over_ranks(ms)
-        value = world * nodes * args.steps / (ms / 1e3) / 1e6
+        units, ms = replica_totals(nodes * args.steps, ms, dev)
+        value = units / (ms / 1e3) / 1e6
 
         # ---- end to end through the public API: each step's force record is
         # read back to the host (synchronizing), the body state goes in as the
@@ -267,8 +279,8 @@ def run_gpu(args):
             fx, fy, ms_ = s.forces(cap=1)
         torch.cuda.synchronize()
         barrier()
-        e_s = max_over_ranks(time.perf_counter() - t0)
-        e2e = world * nodes * e_steps / e_s / 1e6
+        e_units, e_ms = replica_totals(nodes * e_steps, (time.perf_counter() - t0) * 1e3, dev)
+        e2e = e_units / (e_ms / 1e3) / 1e6
     finally:
         s.close()
 
@@ -321,7 +333,7 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32" if args.storage != "f64" else "f64",
         "data": "synthetic",
-        "config": {"workload": w.name + f" MRT {args.storage.upper()}" + (" (populations as FP16 offsets)" if args.storage == "f16" else ""),
+        "config": {"workload": w.name + f" {w.collision.upper()} {args.storage.upper()}",
                    "nx": w.nx, "ny": w.ny, "nodes": nodes, "storage": args.storage,
                    "collision": w.collision, "re": w.re, "u_in": w.u_ref,
                    "step": "mask update of the moving body + fused pull/penalize/collide/reduce kernel",
@@ -381,25 +393,58 @@ def run_serving(args, n_requests=None, rate=None, storage=None, quiet=False):
 
 
 def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores. One step = one oracle
+    step over a window of the workload's grid (rows around the body, at most
+    8192 columns); the window's height is sized from a calibration step so
+    that the W + K steps take about args.ref_budget seconds."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    import numpy as np
+
+    import oracle as O
     w = make_workload(args.workload, args.storage)
-    vals = []
-    for _ in range(args.warmup):
-        oracle_sample(w, budget_s=2.0, max_steps=1)
-    desc, cores = "", 1
-    for _ in range(args.steps):
-        v, desc, cores = oracle_sample(w, budget_s=args.cpu_budget / max(args.steps, 1), max_steps=20)
-        vals.append(v)
-    value = statistics.median(vals)
+    tau = O.tau_from_reynolds(w.u_ref, w.l_ref, w.re) if w.re else w.tau
+    chan = w.bc == "channel"
+
+    def window(rows):
+        ny = max(8, min(w.ny, rows))
+        nx = min(w.nx, 8192)
+        y_off = max(0, int(w.bodies[0].cy) - ny // 2) if w.bodies else 0
+        bodies = [O.Body(b.cx, b.cy - y_off, b.radius, b.amp_x, b.amp_y, b.period, b.omega,
+                         b.outside) for b in w.bodies]
+        cfg = O.Config(nx=nx, ny=ny, collision=O.MRT if w.collision == "mrt" else O.SRT, tau=tau,
+                       lam=w.lam, bc_x=O.BC_INLET_OUTLET if chan else O.BC_PERIODIC,
+                       bc_y=O.BC_FREE_SLIP if chan else O.BC_PERIODIC,
+                       u_in=(w.u_ref, 0.0) if chan else (0.0, 0.0), bodies=bodies)
+        u0 = np.zeros((2, ny, nx))
+        if chan:
+            u0[0] = w.u_ref
+        return cfg, O.init_equilibrium(cfg, 1.0, u0)
+
+    cfg, f = window(256)
+    t0 = time.perf_counter()
+    O.run(cfg, f, 1)
+    rate = cfg.nx * cfg.ny / max(time.perf_counter() - t0, 1e-6)  # node updates per second
+    per_step = args.ref_budget / max(1, args.steps + args.warmup)
+    rows = int(rate * per_step / cfg.nx)
+    cfg, f = window(rows)
+    O.run(cfg, f, args.warmup)
+    t0 = time.perf_counter()
+    O.run(cfg, f, args.steps, t0=args.warmup)
+    dt = time.perf_counter() - t0
+    value = cfg.nx * cfg.ny * args.steps / dt / 1e6
+    desc = (f"FP64 oracle, {cfg.nx}x{cfg.ny} window of the {w.nx}x{w.ny} grid (rows around the "
+            f"body), {args.steps} timed steps after {args.warmup}, {dt:.1f} s")
     out = {"impl": "reference", "metric": "VP-LBM MLUPS (node updates per second / 1e6)",
            "value": round(value, 3), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic",
-           "config": {"workload": w.name + f" MRT {args.storage.upper()}", "nx": w.nx, "ny": w.ny},
-           "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                            "sample": desc},
+           "config": {"workload": w.name + f" {w.collision.upper()} {args.storage.upper()}",
+                      "nx": w.nx, "ny": w.ny, "oracle_window": f"{cfg.nx}x{cfg.ny}"},
+           "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": O.num_threads(),
+                            "kind": "oracle", "sample": desc},
            "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -417,6 +462,8 @@ def main():
     ap.add_argument("--no-compare-f16", dest="compare_f16", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--ref-budget", type=float, default=90.0,
+                    help="reference arm: seconds of oracle work for the warm-up and timed steps")
     ap.add_argument("--serving", action="store_true", help="run only the serving mix")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-rate", type=float, default=0.0)
