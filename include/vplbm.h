@@ -134,6 +134,15 @@ vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out);
  * (NULL: the uniform u0). Resets the step counter and the force record. */
 vplbm_status vplbm_set_initial_velocity(vplbm_solver* s, const double* u);
 
+/* Restarts like vplbm_set_initial_velocity with the seeded field
+ * u = (u0x, u0y) + amp (2 r - 1), r in [0, 1) drawn on the device by SplitMix64
+ * (Steele, Lea, Flood 2014) from `seed`: output number i + 1 for
+ * i = (y nx + x) 2 + component, scaled by its top 53 bits. Bit-identical to
+ * the same generator on the host, and needs no host-to-device copy of a field
+ * (for admitting many solves quickly). */
+vplbm_status vplbm_set_initial_perturbation(vplbm_solver* s, double u0x, double u0y, double amp,
+                                            uint64_t seed);
+
 /* Static mask and solid velocity (Section 2.2, Eq. 261): chi [ny][nx] bytes,
  * nonzero = solid; us [2][ny][nx] doubles or NULL (u_s = 0). on_device = 1:
  * both are device pointers. Replaces any earlier static mask; bodies set with
@@ -180,6 +189,13 @@ vplbm_status vplbm_mask(vplbm_solver* s, uint8_t* chi);
  * went unread the oldest were overwritten. Any pointer may be NULL. */
 vplbm_status vplbm_forces(vplbm_solver* s, double* fx, double* fy, double* mass,
                           int64_t cap, int64_t* count);
+
+/* As vplbm_forces, but without synchronizing: enqueues on the solver's
+ * stream the copy of the records since the previous read into records
+ * ([count][3]: F_x, F_y, mass; host memory, page-locked for the copy to be
+ * asynchronous), returns their number in *count at once, and the data is
+ * valid once the stream has reached this point (an event or a sync). */
+vplbm_status vplbm_forces_async(vplbm_solver* s, double* records, int64_t cap, int64_t* count);
 
 /* Advances n solvers by steps[i] steps each, batching them into grouped
  * launches (one launch per time step per storage/collision class covering
@@ -248,8 +264,9 @@ vplbm_status vplbm_step_noalloc(const vplbm_config* cfg, const vplbm_body* bodie
 const char* vplbm_last_error(const vplbm_solver* s);
 const char* vplbm_status_string(vplbm_status st);
 
-/* Frees everything the solver owns. NULL is a no-op. Does not destroy a
- * caller-supplied stream. */
+/* Frees everything the solver owns, stream-ordered: the memory returns once
+ * the work already queued on the solver's stream completes; the host does not
+ * wait. NULL is a no-op. Does not destroy a caller-supplied stream. */
 void vplbm_destroy(vplbm_solver* s);
 
 #ifdef __cplusplus

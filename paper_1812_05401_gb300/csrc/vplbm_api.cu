@@ -96,6 +96,30 @@ __global__ void us_import_kernel(T2* us, int pitch, int nx, int ny, const double
   us[(long long)y * pitch + x] = v;
 }
 
+// Seeded initial velocity: u = u0 + amp (2 r - 1) per node and component, r
+// the SplitMix64 (Steele, Lea, Flood 2014) output number i + 1 of the seed
+// (i = (y nx + x) 2 + component) scaled to [0, 1) by its top 53 bits. The
+// operations are explicitly rounded, so the field is bit-identical to the
+// same generator evaluated on the host.
+__global__ void perturbation_kernel(double* u, int nx, int ny, double u0x, double u0y, double amp,
+                                    unsigned long long seed) {
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nn = (long long)nx * ny;
+  if (node >= nn) return;
+  double r2[2];
+  for (int c = 0; c < 2; ++c) {
+    const unsigned long long i = (unsigned long long)node * 2ull + (unsigned long long)c + 1ull;
+    unsigned long long z = seed + i * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    const double r = __dmul_rn(double(z >> 11), 1.0 / 9007199254740992.0);
+    r2[c] = __dmul_rn(amp, __dsub_rn(__dmul_rn(2.0, r), 1.0));
+  }
+  u[node] = amp > 0.0 ? __dadd_rn(u0x, r2[0]) : u0x;
+  u[nn + node] = amp > 0.0 ? __dadd_rn(u0y, r2[1]) : u0y;
+}
+
 dim3 grid2d(int w, int h, dim3 blk) {
   return dim3((w + blk.x - 1) / blk.x, (h + blk.y - 1) / blk.y);
 }
@@ -502,15 +526,18 @@ vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
   }
   const size_t pop = size_t(9) * size_t(s->plane) * s->esize;
   cudaError_t e = cudaSuccess;
-  if ((e = cudaMalloc(&s->f[0], pop)) != cudaSuccess ||
-      (e = cudaMalloc(&s->f[1], pop)) != cudaSuccess ||
-      (e = cudaMalloc(reinterpret_cast<void**>(&s->mask), size_t(s->plane))) != cudaSuccess ||
-      (e = cudaMalloc(reinterpret_cast<void**>(&s->partials), 3 * sizeof(double) * s->n_tiles)) != cudaSuccess ||
-      (e = cudaMalloc(reinterpret_cast<void**>(&s->group_partials), 3 * sizeof(double) * s->n_groups)) != cudaSuccess ||
-      (e = cudaMalloc(reinterpret_cast<void**>(&s->counters), sizeof(unsigned) * (s->n_groups + 1))) != cudaSuccess ||
-      (e = cudaMalloc(reinterpret_cast<void**>(&s->ring), 3 * sizeof(double) * cfg->force_ring_len)) != cudaSuccess ||
-      (e = cudaMalloc(reinterpret_cast<void**>(&s->flag), sizeof(int))) != cudaSuccess) {
-    return bail(cuda_fail(s, e, "cudaMalloc"));
+  // Stream-ordered allocations: neither allocation nor release synchronizes
+  // the device, so solvers can come and go while others run (serving).
+  cudaStream_t st0 = s->stream;
+  if ((e = cudaMallocAsync(&s->f[0], pop, st0)) != cudaSuccess ||
+      (e = cudaMallocAsync(&s->f[1], pop, st0)) != cudaSuccess ||
+      (e = cudaMallocAsync(reinterpret_cast<void**>(&s->mask), size_t(s->plane), st0)) != cudaSuccess ||
+      (e = cudaMallocAsync(reinterpret_cast<void**>(&s->partials), 3 * sizeof(double) * s->n_tiles, st0)) != cudaSuccess ||
+      (e = cudaMallocAsync(reinterpret_cast<void**>(&s->group_partials), 3 * sizeof(double) * s->n_groups, st0)) != cudaSuccess ||
+      (e = cudaMallocAsync(reinterpret_cast<void**>(&s->counters), sizeof(unsigned) * (s->n_groups + 1), st0)) != cudaSuccess ||
+      (e = cudaMallocAsync(reinterpret_cast<void**>(&s->ring), 3 * sizeof(double) * cfg->force_ring_len, st0)) != cudaSuccess ||
+      (e = cudaMallocAsync(reinterpret_cast<void**>(&s->flag), sizeof(int), st0)) != cudaSuccess) {
+    return bail(cuda_fail(s, e, "cudaMallocAsync"));
   }
   if ((e = cudaMemsetAsync(s->mask, 0, size_t(s->plane), s->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(s->counters, 0, sizeof(unsigned) * (s->n_groups + 1), s->stream)) != cudaSuccess ||
@@ -621,7 +648,7 @@ vplbm_status vplbm_set_mask_and_solid_velocity(vplbm_solver* s, const uint8_t* c
   VP_CUDA(s, cudaGetLastError());
   if (dus) {
     const size_t vs = s->cfg.storage == kF64 ? sizeof(double2) : sizeof(float2);
-    if (!s->us) VP_CUDA(s, cudaMalloc(&s->us, vs * size_t(s->plane)));
+    if (!s->us) VP_CUDA(s, cudaMallocAsync(&s->us, vs * size_t(s->plane), s->stream));
     if (s->cfg.storage == kF64)
       us_import_kernel<double2><<<grid2d(nx, ny, blk), blk, 0, s->stream>>>(
           static_cast<double2*>(s->us), s->pitch, nx, ny, dus);
@@ -808,6 +835,51 @@ vplbm_status vplbm_forces(vplbm_solver* s, double* fx, double* fy, double* mass,
   return VPLBM_OK;
 }
 
+vplbm_status vplbm_forces_async(vplbm_solver* s, double* records, int64_t cap, int64_t* count) {
+  vplbm_status st = check_usable(s);
+  if (st != VPLBM_OK) return st;
+  if (count) *count = 0;
+  if (cap < 0 || (cap > 0 && !records)) return fail(s, VPLBM_ERR_INVALID, "bad output buffer");
+  const int64_t L = s->cfg.force_ring_len;
+  const int64_t k = std::min(std::min(s->t - s->ring_read, L), cap);
+  int64_t done = 0;
+  while (done < k) {
+    const int64_t step = s->t - k + done;
+    const int64_t slot = step % L;
+    const int64_t run = std::min(k - done, L - slot);
+    VP_CUDA(s, cudaMemcpyAsync(records + 3 * done, s->ring + 3 * slot, 3 * sizeof(double) * run,
+                               cudaMemcpyDeviceToHost, s->stream));
+    done += run;
+  }
+  if (count) *count = k;
+  s->ring_read = s->t;
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_set_initial_perturbation(vplbm_solver* s, double u0x, double u0y, double amp,
+                                            uint64_t seed) {
+  vplbm_status st = check_usable(s);
+  if (st != VPLBM_OK) return st;
+  if (!(amp >= 0.0)) return fail(s, VPLBM_ERR_INVALID, "amp must be >= 0");
+  const size_t n = size_t(s->cfg.nx) * s->cfg.ny;
+  double* du = nullptr;
+  VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&du), 2 * n * sizeof(double), s->stream));
+  const int threads = 256;
+  const long long blocks = (long long)((n + threads - 1) / threads);
+  perturbation_kernel<<<unsigned(blocks), threads, 0, s->stream>>>(du, s->cfg.nx, s->cfg.ny, u0x, u0y,
+                                                                    amp, seed);
+  VP_CUDA(s, cudaGetLastError());
+  s->cur = 0;
+  VP_CUDA(s, launch_init(s, s->base, s->f[0], du));
+  VP_CUDA(s, cudaFreeAsync(du, s->stream));
+  s->t = 0;
+  s->ring_read = 0;
+  VP_CUDA(s, cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream));
+  VP_CUDA(s, cudaMemsetAsync(s->ring, 0, 3 * sizeof(double) * s->cfg.force_ring_len, s->stream));
+  if (s->moving) s->mask_t = -1;
+  return VPLBM_OK;
+}
+
 vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int64_t* steps) {
   if (n < 0 || (n > 0 && (!solvers || !steps))) return VPLBM_ERR_INVALID;
   if (n == 0) return VPLBM_OK;
@@ -945,22 +1017,20 @@ const char* vplbm_status_string(vplbm_status st) {
 
 void vplbm_destroy(vplbm_solver* s) {
   if (!s) return;
-  if (s->stream) cudaStreamSynchronize(s->stream);
+  // Stream-ordered release: the memory returns to the pool once the work
+  // already queued on the stream is done; the host does not wait.
   for (auto& pr : s->ev_pending) {
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);
   }
   for (auto e : s->ev_pool) cudaEventDestroy(e);
-  cudaFree(s->f[0]);
-  cudaFree(s->f[1]);
-  cudaFree(s->mask);
-  cudaFree(s->us);
-  cudaFree(s->partials);
-  cudaFree(s->group_partials);
-  cudaFree(s->counters);
-  cudaFree(s->ring);
-  cudaFree(s->flag);
-  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  if (s->stream) {
+    void* bufs[] = {s->f[0], s->f[1], s->mask, s->us, s->partials, s->group_partials,
+                    s->counters, s->ring, s->flag};
+    for (void* b : bufs)
+      if (b) cudaFreeAsync(b, s->stream);
+    if (s->own_stream) cudaStreamDestroy(s->stream);
+  }
   delete s;
 }
 

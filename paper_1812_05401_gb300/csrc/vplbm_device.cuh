@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "vplbm_params.h"
 
 namespace vplbm {
@@ -543,40 +545,83 @@ __device__ __forceinline__ void finish_reduction(const StepParams& p, int tile, 
 // of warp w takes nodes x0 + N l .. x0 + N l + N - 1 of rows y0 + w + 8 r,
 // r = 0..kRows-1.
 //
-// Interior tiles (no boundary within one node) pull with one N-element vector
-// load per direction: a direction with xi_x = +1 takes its first node's value
-// from the lane to the left (warp shuffle), one with xi_x = -1 its last
-// node's value from the lane to the right, and only the edge lanes 0 and 31
-// load that one value themselves. Tiles touching a boundary pull node by node
-// through the boundary remaps. The arithmetic per node is the same on both
-// paths.
+// Every direction is pulled with one N-element vector load per lane: a
+// direction with xi_x = +1 takes its first node's value from the lane to the
+// left (warp shuffle), one with xi_x = -1 its last node's value from the lane
+// to the right, and only the edge lanes 0 and 31 load that one value
+// themselves. Interior tiles (no boundary within one node) do nothing else.
+// Tiles touching a boundary (GEN) also remap: the source row of each direction
+// (periodic wrap or free-slip mirror, uniform across the warp), the edge
+// lanes' single values (periodic wrap, inlet ghost, outlet copy), and the value
+// entering the domain's last column; lanes past the last column load and
+// store nothing. The arithmetic per node is the same on both paths.
 // ---------------------------------------------------------------------------
-template <class S, int N, int A>
+template <class S, int A>
+__device__ __forceinline__ typename S::T edge_pull(const StepParams& p, const typename S::E* src,
+                                                   int as, int ys, int xs) {
+  if (xs < 0 || xs >= p.nx) {
+    if (p.bc_x == kBcPeriodic) {
+      xs %= p.nx;
+      if (xs < 0) xs += p.nx;
+    } else if (xs < 0) {  // inlet ghost column at f_eq(1, u_in)
+      const Consts<typename S::T>& c = consts<typename S::T>(p);
+      return as == A ? c.heq_in[A] : c.heq_in[mirror_y(A)];
+    } else {  // zero-gradient outlet ghost column
+      xs = p.nx - 1;
+    }
+  }
+  return load_h<S>(src + (long long)as * p.plane + (long long)ys * p.pitch + xs, A);
+}
+
+template <class S, int N, int A, bool GEN>
 __device__ __forceinline__ void pull_dir_vec(const StepParams& p, const typename S::E* src, int xb,
-                                             int y, int lane, typename S::T (&h)[N][9]) {
+                                             int y, int lane, bool lane_active,
+                                             typename S::T (&h)[N][9]) {
   using T = typename S::T;
   using E = typename S::E;
-  const E* row = src + (long long)A * p.plane + (long long)(y - cy(A)) * p.pitch;
-  E e[N];
-  S::load_chunk(row + xb, e);
+  int as = A;
+  int ys = y - cy(A);
+  if (GEN && (ys < 0 || ys >= p.ny)) {
+    if (p.bc_y == kBcPeriodic) {
+      ys = ys < 0 ? ys + p.ny : ys - p.ny;
+    } else {  // free slip: the mirror of the population that left this row
+      as = mirror_y(A);
+      ys = y;
+    }
+  }
+  const E* row = src + (long long)as * p.plane + (long long)ys * p.pitch;
   T v[N];
+  if (!GEN || lane_active) {
+    E e[N];
+    S::load_chunk(row + xb, e);
 #pragma unroll
-  for (int k = 0; k < N; ++k) v[k] = S::in(e[k], A);
+    for (int k = 0; k < N; ++k) v[k] = S::in(e[k], A);
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = T(0);
+  }
   if (cx(A) == 0) {
 #pragma unroll
     for (int k = 0; k < N; ++k) h[k][A] = v[k];
   } else if (cx(A) == 1) {  // node k pulls from x - 1
     T left = __shfl_up_sync(0xffffffffu, v[N - 1], 1);
-    if (lane == 0) left = load_h<S>(row + xb - 1, A);
+    if (lane == 0) left = GEN ? edge_pull<S, A>(p, src, as, ys, xb - 1) : load_h<S>(row + xb - 1, A);
     h[0][A] = left;
 #pragma unroll
     for (int k = 1; k < N; ++k) h[k][A] = v[k - 1];
   } else {  // node k pulls from x + 1
     T right = __shfl_down_sync(0xffffffffu, v[0], 1);
-    if (lane == kLanes - 1) right = load_h<S>(row + xb + N, A);
+    if (lane == kLanes - 1)
+      right = GEN ? edge_pull<S, A>(p, src, as, ys, xb + N) : load_h<S>(row + xb + N, A);
 #pragma unroll
     for (int k = 0; k < N - 1; ++k) h[k][A] = v[k + 1];
     h[N - 1][A] = right;
+    if (GEN) {
+      // the domain's last column pulls from beyond it, through the x boundary
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+        if (xb + k == p.nx - 1) h[k][A] = edge_pull<S, A>(p, src, as, ys, p.nx);
+    }
   }
 }
 
@@ -614,74 +659,65 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
     }
   };
 
+  auto do_row = [&](int y, auto gen) {
+    constexpr bool GEN = decltype(gen)::value;
+    const bool lane_active = !GEN || xb < p.nx;
+    T h[N][9];
+    pull_dir_vec<S, N, 0, GEN>(p, src, xb, y, lane, lane_active, h);
+    pull_dir_vec<S, N, 1, GEN>(p, src, xb, y, lane, lane_active, h);
+    pull_dir_vec<S, N, 2, GEN>(p, src, xb, y, lane, lane_active, h);
+    pull_dir_vec<S, N, 3, GEN>(p, src, xb, y, lane, lane_active, h);
+    pull_dir_vec<S, N, 4, GEN>(p, src, xb, y, lane, lane_active, h);
+    pull_dir_vec<S, N, 5, GEN>(p, src, xb, y, lane, lane_active, h);
+    pull_dir_vec<S, N, 6, GEN>(p, src, xb, y, lane, lane_active, h);
+    pull_dir_vec<S, N, 7, GEN>(p, src, xb, y, lane, lane_active, h);
+    pull_dir_vec<S, N, 8, GEN>(p, src, xb, y, lane, lane_active, h);
+    if (!lane_active) return;
+    const long long i = (long long)y * p.pitch + xb;
+    uint8_t m[N];
+    if (N == 4) {
+      const uchar4 mv = *reinterpret_cast<const uchar4*>(p.mask + i);
+      m[0] = mv.x;
+      m[1] = mv.y;
+      m[2 % N] = mv.z;
+      m[3 % N] = mv.w;
+    } else {
+      const uchar2 mv = *reinterpret_cast<const uchar2*>(p.mask + i);
+      m[0] = mv.x;
+      m[1 % N] = mv.y;
+    }
+    E o[9][N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      if (GEN && xb + k >= p.nx) {  // past the last column: keep the padding as it was
+#pragma unroll
+        for (int a = 0; a < 9; ++a) o[a][k] = S::out(h[k][a], a);
+        continue;
+      }
+      const Macro<T> q = macros<T>(p, h[k], m[k], xb + k, y);
+      if (COLL == kSrt)
+        collide_srt<T>(p, h[k], q);
+      else
+        collide_mrt<T>(p, h[k], q);
+      const unsigned nb = (S::kSixteen && p.stochastic)
+                              ? round_bits(unsigned((long long)y * p.nx + (xb + k)), key) : 0u;
+#pragma unroll
+      for (int a = 0; a < 9; ++a) o[a][k] = out_value<S>(p, h[k][a], a, nb);
+      finish_node(q, m[k]);
+    }
+#pragma unroll
+    for (int a = 0; a < 9; ++a) S::store_chunk(dst + (long long)a * p.plane + i, o[a]);
+  };
+
   if (interior) {
 #pragma unroll 1
-    for (int r = 0; r < kRows; ++r) {
-      const int y = y0 + warp + r * kWarps;
-      T h[N][9];
-      pull_dir_vec<S, N, 0>(p, src, xb, y, lane, h);
-      pull_dir_vec<S, N, 1>(p, src, xb, y, lane, h);
-      pull_dir_vec<S, N, 2>(p, src, xb, y, lane, h);
-      pull_dir_vec<S, N, 3>(p, src, xb, y, lane, h);
-      pull_dir_vec<S, N, 4>(p, src, xb, y, lane, h);
-      pull_dir_vec<S, N, 5>(p, src, xb, y, lane, h);
-      pull_dir_vec<S, N, 6>(p, src, xb, y, lane, h);
-      pull_dir_vec<S, N, 7>(p, src, xb, y, lane, h);
-      pull_dir_vec<S, N, 8>(p, src, xb, y, lane, h);
-      const long long i = (long long)y * p.pitch + xb;
-      uint8_t m[N];
-      if (N == 4) {
-        const uchar4 mv = *reinterpret_cast<const uchar4*>(p.mask + i);
-        m[0] = mv.x;
-        m[1] = mv.y;
-        m[2 % N] = mv.z;
-        m[3 % N] = mv.w;
-      } else {
-        const uchar2 mv = *reinterpret_cast<const uchar2*>(p.mask + i);
-        m[0] = mv.x;
-        m[1 % N] = mv.y;
-      }
-      E o[9][N];
-#pragma unroll
-      for (int k = 0; k < N; ++k) {
-        const Macro<T> q = macros<T>(p, h[k], m[k], xb + k, y);
-        if (COLL == kSrt)
-          collide_srt<T>(p, h[k], q);
-        else
-          collide_mrt<T>(p, h[k], q);
-        const unsigned nb = (S::kSixteen && p.stochastic)
-                                ? round_bits(unsigned((long long)y * p.nx + (xb + k)), key) : 0u;
-#pragma unroll
-        for (int a = 0; a < 9; ++a) o[a][k] = out_value<S>(p, h[k][a], a, nb);
-        finish_node(q, m[k]);
-      }
-#pragma unroll
-      for (int a = 0; a < 9; ++a) S::store_chunk(dst + (long long)a * p.plane + i, o[a]);
-    }
+    for (int r = 0; r < kRows; ++r) do_row(y0 + warp + r * kWarps, std::false_type());
   } else {
 #pragma unroll 1
     for (int r = 0; r < kRows; ++r) {
       const int y = y0 + warp + r * kWarps;
-      if (y >= p.ny) break;
-#pragma unroll 1
-      for (int k = 0; k < N; ++k) {
-        const int x = xb + k;
-        if (x >= p.nx) break;
-        T h[9];
-        pull_node<S>(p, src, false, x, y, h);
-        const long long i = (long long)y * p.pitch + x;
-        const uint8_t m = p.mask[i];
-        const Macro<T> q = macros<T>(p, h, m, x, y);
-        if (COLL == kSrt)
-          collide_srt<T>(p, h, q);
-        else
-          collide_mrt<T>(p, h, q);
-        const unsigned nb = (S::kSixteen && p.stochastic)
-                                ? round_bits(unsigned((long long)y * p.nx + x), key) : 0u;
-#pragma unroll
-        for (int a = 0; a < 9; ++a) dst[(long long)a * p.plane + i] = out_value<S>(p, h[a], a, nb);
-        finish_node(q, m);
-      }
+      if (y >= p.ny) break;  // warp-uniform: a warp is one row
+      do_row(y, std::true_type());
     }
   }
 

@@ -11,10 +11,13 @@ solves already running. A finished solve's force series is read back and its
 memory released once the GPU has completed its last round (CUDA event), which
 is the request's completion time; latency = completion - arrival.
 
-All solves share one CUDA stream (grouped launches require it); the host keeps
-up to two rounds in flight so that admission and retirement overlap with GPU
-work. Results do not depend on the mix: the grouped kernel is the same code
-as the single-solver step, with deterministic fixed-order reductions.
+All solves share one CUDA stream (grouped launches require it). The host never
+waits for the GPU except for the oldest round in flight: solver memory is
+allocated and released stream-ordered, the initial field is generated on the
+device, and a finished solve's force series is copied asynchronously into
+page-locked memory behind its last round. Results do not depend on the mix:
+the grouped kernel is the same code as the single-solver step, with
+deterministic fixed-order reductions.
 """
 from __future__ import annotations
 
@@ -54,10 +57,11 @@ class _Active:
     remaining: int
     admitted: float
     footprint: int
+    records: object = None  # pinned [steps][3] float64 tensor, filled behind the last round
 
 
 class Server:
-    def __init__(self, budget_bytes: int, max_active: int = 64, round_steps: int = 500,
+    def __init__(self, budget_bytes: int, max_active: int = 256, round_steps: int = 500,
                  stream=None, keep_populations: bool = False):
         import torch
         self.torch = torch
@@ -71,7 +75,9 @@ class Server:
     def _create(self, w):
         cfg, bodies = V.config_from_workload(w, ring_len=max(1, w.steps), stream=self.stream,
                                              reduce_mass=False)
-        return V.Solver(cfg, bodies, w.initial_velocity()), V.vplbm_footprint_bytes(cfg)
+        u0 = (w.u_ref, 0.0) if w.bc == "channel" else (0.0, 0.0)
+        s = V.Solver(cfg, bodies, perturbation=(u0[0], u0[1], w.perturbation, w.seed))
+        return s, V.vplbm_footprint_bytes(cfg)
 
     def run(self, requests, realtime: bool = True):
         """Serves the requests; returns (results, report). With realtime=False
@@ -93,7 +99,8 @@ class Server:
                 ev, fin = inflight.popleft()
                 ev.synchronize()
                 for a in fin:
-                    fx, fy, _ = a.solver.forces()
+                    rec = a.records.numpy()
+                    fx, fy = rec[:, 0].copy(), rec[:, 1].copy()
                     pops = a.solver.populations() if self.keep_populations else None
                     t_done = now()
                     w = a.req.workload
@@ -131,11 +138,15 @@ class Server:
                 continue
             steps = [min(a.remaining, self.round_steps) for a in active]
             V.vplbm_group_step([a.solver.h for a in active], steps)
-            ev = torch.cuda.Event()
-            ev.record(self.stream)
             for a, k in zip(active, steps):
                 a.remaining -= k
             done = [a for a in active if a.remaining == 0]
+            for a in done:  # force series copied behind the solve's last round
+                a.records = torch.empty((max(1, a.req.workload.steps), 3), dtype=torch.float64,
+                                        pin_memory=True)
+                V.vplbm_forces_async(a.solver.h, a.records.numpy())
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
             active = [a for a in active if a.remaining > 0]
             inflight.append((ev, done))
             retire(block=False)

@@ -79,6 +79,8 @@ def lib() -> C.CDLL:
         L.vplbm_footprint_bytes.restype = C.c_size_t
         L.vplbm_create.argtypes = [C.POINTER(vplbm_config), C.POINTER(P)]
         L.vplbm_set_initial_velocity.argtypes = [P, dp]
+        L.vplbm_set_initial_perturbation.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_uint64]
+        L.vplbm_forces_async.argtypes = [P, dp, C.c_int64, C.POINTER(C.c_int64)]
         L.vplbm_set_mask_and_solid_velocity.argtypes = [P, P, P, C.c_int32]
         L.vplbm_set_bodies.argtypes = [P, C.POINTER(vplbm_body), C.c_int32]
         L.vplbm_step.argtypes = [P, C.c_int64]
@@ -101,7 +103,8 @@ def lib() -> C.CDLL:
         L.vplbm_status_string.restype = C.c_char_p
         L.vplbm_destroy.argtypes = [P]
         L.vplbm_destroy.restype = None
-        for name in ("vplbm_create", "vplbm_set_initial_velocity", "vplbm_set_mask_and_solid_velocity",
+        for name in ("vplbm_create", "vplbm_set_initial_velocity", "vplbm_set_initial_perturbation",
+                     "vplbm_forces_async", "vplbm_set_mask_and_solid_velocity",
                      "vplbm_set_bodies", "vplbm_step", "vplbm_synchronize", "vplbm_moments",
                      "vplbm_populations", "vplbm_set_populations", "vplbm_mask", "vplbm_forces",
                      "vplbm_group_step", "vplbm_enable_timing", "vplbm_fused_timing"):
@@ -154,6 +157,20 @@ def vplbm_set_initial_velocity(h, u=None):
         u = np.ascontiguousarray(u, dtype=np.float64)
         dp = u.ctypes.data_as(C.POINTER(C.c_double))
     _check(h, lib().vplbm_set_initial_velocity(h, dp), "vplbm_set_initial_velocity")
+
+
+def vplbm_set_initial_perturbation(h, u0x: float, u0y: float, amp: float, seed: int):
+    _check(h, lib().vplbm_set_initial_perturbation(h, u0x, u0y, amp, int(seed) & ((1 << 64) - 1)),
+           "vplbm_set_initial_perturbation")
+
+
+def vplbm_forces_async(h, records) -> int:
+    """records: page-locked float64 array [cap][3] (e.g. a pinned torch
+    tensor's numpy view); valid once the solver's stream reaches this point."""
+    cnt = C.c_int64()
+    _check(h, lib().vplbm_forces_async(h, records.ctypes.data_as(C.POINTER(C.c_double)),
+                                       records.shape[0], C.byref(cnt)), "vplbm_forces_async")
+    return cnt.value
 
 
 def vplbm_set_mask_and_solid_velocity(h, chi, us=None, on_device: bool = False):
@@ -300,13 +317,17 @@ def config_from_workload(w, ring_len: int = 4096, stream=None, reduce_mass: bool
 class Solver:
     """One vplbm solver; arrays are numpy (host) unless a call says otherwise."""
 
-    def __init__(self, cfg: vplbm_config, bodies=(), u_init=None):
+    def __init__(self, cfg: vplbm_config, bodies=(), u_init=None, perturbation=None):
+        """u_init: host [2][ny][nx] initial velocity; or perturbation =
+        (u0x, u0y, amp, seed) for the seeded field generated on the device."""
         self.cfg = cfg
         self.nx, self.ny = cfg.nx, cfg.ny
         self.h = vplbm_create(cfg)
         try:
             if u_init is not None:
                 vplbm_set_initial_velocity(self.h, u_init)
+            elif perturbation is not None:
+                vplbm_set_initial_perturbation(self.h, *perturbation)
             if bodies:
                 vplbm_set_bodies(self.h, list(bodies))
         except Exception:
@@ -315,9 +336,17 @@ class Solver:
 
     @classmethod
     def from_workload(cls, w, stream=None, ring_len: int = 4096, reduce_mass: bool = True,
-                      with_initial_velocity: bool = True, rounding: str = "stochastic"):
+                      with_initial_velocity: bool = True, rounding: str = "stochastic",
+                      device_init: bool = False):
+        """device_init: generate the workload's seeded initial field on the
+        device (bit-identical to w.initial_velocity())."""
         cfg, bodies = config_from_workload(w, ring_len, stream, reduce_mass, rounding)
-        return cls(cfg, bodies, w.initial_velocity() if with_initial_velocity else None)
+        if not with_initial_velocity:
+            return cls(cfg, bodies)
+        if device_init:
+            u0 = (w.u_ref, 0.0) if w.bc == "channel" else (0.0, 0.0)
+            return cls(cfg, bodies, perturbation=(u0[0], u0[1], w.perturbation, w.seed))
+        return cls(cfg, bodies, w.initial_velocity())
 
     def close(self):
         if getattr(self, "h", None):
