@@ -333,13 +333,13 @@ cudaError_t launch_fused(const vplbm_solver* s, const StepParams& p) {
   }
 }
 
-cudaError_t launch_group(int storage, int coll, const StepParams* dp, const GroupTile* dt, int nb,
-                         long long k, cudaStream_t st) {
+cudaError_t launch_group(int storage, const StepParams* dp, const GroupTile* dt, int nb, long long k,
+                         cudaStream_t st) {
   switch (storage) {
-    case kF64: return launch_group_f64(coll, dp, dt, nb, k, st);
-    case kF32: return launch_group_f32(coll, dp, dt, nb, k, st);
-    case kF16: return launch_group_f16(coll, dp, dt, nb, k, st);
-    default: return launch_group_bf16(coll, dp, dt, nb, k, st);
+    case kF64: return launch_group_f64(dp, dt, nb, k, st);
+    case kF32: return launch_group_f32(dp, dt, nb, k, st);
+    case kF16: return launch_group_f16(dp, dt, nb, k, st);
+    default: return launch_group_bf16(dp, dt, nb, k, st);
   }
 }
 
@@ -596,6 +596,7 @@ vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
   p.ring_len = cfg->force_ring_len;
   p.reduce_mass = cfg->reduce_mass ? 1 : 0;
   p.stochastic = cfg->rounding == VPLBM_ROUND_STOCHASTIC ? 1 : 0;
+  p.collision = cfg->collision;
 
   if ((st = vplbm_set_initial_velocity(s, nullptr)) != VPLBM_OK) return bail(st);
   *out = s;
@@ -902,17 +903,17 @@ vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int
     int idx;
     int64_t steps;
   };
-  std::vector<Member> classes[4][2];
+  std::vector<Member> classes[4];  // one grouped launch per storage type and step
   std::vector<int> moving;
   for (int i = 0; i < n; ++i) {
     if (solvers[i]->moving) {
       moving.push_back(i);
       continue;
     }
-    classes[solvers[i]->cfg.storage][solvers[i]->cfg.collision].push_back({i, steps[i]});
+    classes[solvers[i]->cfg.storage].push_back({i, steps[i]});
   }
   struct Plan {
-    int storage, coll;
+    int storage;
     StepParams* d_params;
     GroupTile* d_table;
     std::vector<int64_t> prefix_steps;  // steps of the j-th member (descending)
@@ -920,8 +921,8 @@ vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int
   };
   std::vector<Plan> plans;
   for (int sg = 0; sg < 4; ++sg) {
-    for (int c = 0; c < 2; ++c) {
-      auto& mem = classes[sg][c];
+    {
+      auto& mem = classes[sg];
       if (mem.empty()) continue;
       std::stable_sort(mem.begin(), mem.end(),
                        [](const Member& a, const Member& b) { return a.steps > b.steps; });
@@ -929,7 +930,6 @@ vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int
       std::vector<GroupTile> ht;
       Plan pl;
       pl.storage = sg;
-      pl.coll = c;
       for (size_t j = 0; j < mem.size(); ++j) {
         vplbm_solver* s = solvers[mem[j].idx];
         hp.push_back(step_params(s, s->t, 0));
@@ -954,7 +954,7 @@ vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int
       while (active < int(pl.prefix_steps.size()) && pl.prefix_steps[active] > k) ++active;
       if (active == 0) continue;
       const int nb = pl.prefix_tiles[active - 1];
-      VP_CUDA(s0, launch_group(pl.storage, pl.coll, pl.d_params, pl.d_table, nb, k, stream));
+      VP_CUDA(s0, launch_group(pl.storage, pl.d_params, pl.d_table, nb, k, stream));
     }
     for (int i : moving) {
       if (steps[i] > k) {

@@ -644,8 +644,8 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
   const E* __restrict__ src = static_cast<const E*>(p.src);
   E* __restrict__ dst = static_cast<E*>(p.dst);
 
-  T dm = T(0);                 // sum of drho over this thread's nodes
-  double bfx = 0.0, bfy = 0.0;  // force on solid nodes (FP64 from the node up)
+  T dm = T(0);           // sum of drho over this thread's nodes
+  T tfx = T(0), tfy = T(0);  // force on this thread's solid nodes (<= 16, arithmetic type)
   bool any_solid = false;
   const unsigned key = round_bits(unsigned(t), 0x9e3779b9u);
 
@@ -654,8 +654,8 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
     dm += q.drho;
     if (m) {
       any_solid = true;
-      bfx -= double(q.fpx);
-      bfy -= double(q.fpy);
+      tfx -= q.fpx;
+      tfy -= q.fpy;
     }
   };
 
@@ -721,11 +721,18 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
     }
   }
 
-  // Per-step record: the block's force on solid nodes (FP64) and total density
-  // (the arithmetic type within the block, FP64 from the tile up). Blocks
-  // without solid nodes skip the FP64 work.
+  // Per-step record: the force on the solid nodes, summed per thread in the
+  // arithmetic type (each thread holds at most 16 nodes) and in FP64 from the
+  // thread up; the total density, in the arithmetic type within the block and
+  // FP64 from the tile up. Warps and blocks without solid nodes skip the FP64
+  // work (on GB300 FP64 runs at a small fraction of the FP32 rate).
   const int tid = lane + warp * kLanes;
   const bool warp_solid = __any_sync(0xffffffffu, any_solid);
+  double bfx = 0.0, bfy = 0.0;
+  if (warp_solid) {
+    bfx = double(tfx);
+    bfy = double(tfy);
+  }
   if (p.reduce_mass) dm = warp_sum(dm);
   if (warp_solid) {
     bfx = warp_sum(bfx);
@@ -767,14 +774,29 @@ __global__ void __launch_bounds__(kThreads, min_blocks_per_sm(STORE)) fused_step
 // Grouped launch for serving: block b runs tile table[b].tile of solver
 // table[b].solver at that solver's k-th step of the batch. Each solver has two
 // parameter sets in a device array, for even and odd k (source and destination
-// buffers swapped); params[].t is the solver's step index at k = 0.
-template <int STORE, int COLL>
-__global__ void __launch_bounds__(kThreads, min_blocks_per_sm(STORE)) fused_group_kernel(const StepParams* __restrict__ params,
-                                                                  const GroupTile* __restrict__ table,
-                                                                  long long k) {
+// buffers swapped); params[].t is the solver's step index at k = 0. The block
+// copies its solver's parameters to shared memory first (they are read many
+// times per node), and takes the collision operator from them, so one launch
+// covers SRT and MRT solvers of one storage type.
+template <int STORE>
+__global__ void __launch_bounds__(kThreads, min_blocks_per_sm(STORE))
+    fused_group_kernel(const StepParams* __restrict__ params, const GroupTile* __restrict__ table,
+                       long long k) {
+  __shared__ StepParams sp;
   const GroupTile gt = table[blockIdx.x];
-  const StepParams& p = params[2 * gt.solver + int(k & 1)];
-  step_tile<STORE, COLL>(p, gt.tile, p.t + k);
+  const StepParams* g = params + 2 * gt.solver + int(k & 1);
+  {
+    static_assert(sizeof(StepParams) % sizeof(int) == 0, "StepParams is copied in 4-byte words");
+    const int* from = reinterpret_cast<const int*>(g);
+    int* to = reinterpret_cast<int*>(&sp);
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    for (int w = tid; w < int(sizeof(StepParams) / sizeof(int)); w += kThreads) to[w] = __ldg(from + w);
+  }
+  __syncthreads();
+  if (sp.collision == kSrt)
+    step_tile<STORE, kSrt>(sp, gt.tile, sp.t + k);
+  else
+    step_tile<STORE, kMrt>(sp, gt.tile, sp.t + k);
 }
 
 // ---------------------------------------------------------------------------

@@ -21,13 +21,10 @@ cudaError_t VPLBM_FN(launch_fused_)(int coll, const StepParams& p, cudaStream_t 
   return cudaGetLastError();
 }
 
-cudaError_t VPLBM_FN(launch_group_)(int coll, const StepParams* d_params, const GroupTile* d_table,
+cudaError_t VPLBM_FN(launch_group_)(const StepParams* d_params, const GroupTile* d_table,
                                     int n_blocks, long long k, cudaStream_t st) {
   if (n_blocks <= 0) return cudaSuccess;
-  if (coll == kSrt)
-    fused_group_kernel<VPLBM_STORE, kSrt><<<n_blocks, dim3(kLanes, kWarps), 0, st>>>(d_params, d_table, k);
-  else
-    fused_group_kernel<VPLBM_STORE, kMrt><<<n_blocks, dim3(kLanes, kWarps), 0, st>>>(d_params, d_table, k);
+  fused_group_kernel<VPLBM_STORE><<<n_blocks, dim3(kLanes, kWarps), 0, st>>>(d_params, d_table, k);
   return cudaGetLastError();
 }
 

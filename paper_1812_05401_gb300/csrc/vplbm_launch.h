@@ -9,7 +9,7 @@ namespace vplbm {
 
 #define VPLBM_DECLARE_LAUNCHERS(SUFFIX)                                                         \
   cudaError_t launch_fused_##SUFFIX(int coll, const StepParams& p, cudaStream_t st);            \
-  cudaError_t launch_group_##SUFFIX(int coll, const StepParams* d_params,                       \
+  cudaError_t launch_group_##SUFFIX(const StepParams* d_params,                                 \
                                     const GroupTile* d_table, int n_blocks, long long k,         \
                                     cudaStream_t st);                                           \
   cudaError_t launch_moments_##SUFFIX(const StepParams& p, double* rho, double* ux, double* uy, \

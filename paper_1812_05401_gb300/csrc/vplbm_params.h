@@ -79,6 +79,7 @@ struct StepParams {
   int ring_len;
   int reduce_mass;
   int stochastic;           // 16-bit stores: 1 = stochastic rounding, 0 = nearest even
+  int collision;            // kSrt | kMrt (read by the grouped kernel)
 };
 
 template <class T> __host__ __device__ inline const Consts<T>& consts(const StepParams& p);
