@@ -316,6 +316,11 @@ def run_gpu(args):
                                      "achieved_gbs": round(ach, 1), "frac": round(ach / peak, 4),
                                      "algo_bytes_per_node": ALGO_BYTES["f16"]}
 
+    if args.serve_in_bench:
+        rep = run_serving(args, n_requests=args.serve_requests, rate=args.serve_rate_bench,
+                          quiet=True)
+        extra["serving"] = rep
+
     peak, peak_src = hbm_peak()
     kms = fused_ms / max(fused_n, 1)
     achieved = ALGO_BYTES[args.storage] * nodes / (kms / 1e3) / 1e9
@@ -361,6 +366,20 @@ def run_gpu(args):
         print(json.dumps(result), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_serving_passes(args):
+    """Closed-loop capacity, then Poisson arrivals at 0.8 x capacity, for the
+    mixed storage and for all-FP32 and all-FP16 requests."""
+    out = {}
+    for st in (None, "f32", "f16"):
+        cap = run_serving(args, rate=0.0, storage=st, quiet=True)
+        rate = round(0.8 * cap["solves_per_s"], 2)
+        rep = run_serving(args, rate=rate, storage=st, quiet=True)
+        out[st or "mixed"] = {"capacity_solves_per_s": cap["solves_per_s"], "capacity_mlups": cap["mlups"],
+                              "at_0.8_capacity": rep}
+    print(json.dumps({"metric": "served solves/s and p50/p99 latency (VP-LBM serving mix)",
+                      "serving": out}), flush=True)
 
 
 def run_serving(args, n_requests=None, rate=None, storage=None, quiet=False):
@@ -467,7 +486,12 @@ def main():
     ap.add_argument("--serving", action="store_true", help="run only the serving mix")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-rate", type=float, default=0.0)
-    ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--serve-slots", type=int, default=256)
+    ap.add_argument("--no-serving", dest="serve_in_bench", action="store_false",
+                    help="skip the serving measurement in the default run")
+    ap.add_argument("--serve-rate-bench", type=float, default=7.8,
+                    help="Poisson arrival rate of the serving measurement in the default run "
+                         "(0.8 x the measured closed-loop capacity of 9.8 solves/s)")
     ap.add_argument("--serve-round", type=int, default=500)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -479,7 +503,7 @@ def main():
         if not B.up_to_date():
             B.build()
         if args.serving:
-            run_serving(args)
+            run_serving_passes(args)
         else:
             run_gpu(args)
 
