@@ -129,14 +129,14 @@ __device__ __forceinline__ unsigned short Store16<__nv_bfloat16>::bits(__nv_bflo
 }
 // Stochastic rounding of an FP32 value to a format keeping the top 23 - DROP
 // significand bits: add DROP uniformly random bits (the top bits of r) below
-// the kept ones to the magnitude and truncate, so the value rounds up with
+// the kept ones and truncate toward zero, so the magnitude rounds up with
 // probability equal to its distance from the lower neighbour (exact for
-// normal results).
+// normal results). The addition acts on the magnitude bits alone: a carry can
+// reach the exponent (rounding up to the next binade) but never the sign for
+// the finite values stored here.
 template <int DROP>
 __device__ __forceinline__ float dither(float h, unsigned r) {
-  const unsigned b = __float_as_uint(h);
-  const unsigned mag = (b & 0x7fffffffu) + (r >> (32 - DROP));
-  return __uint_as_float((b & 0x80000000u) | mag);
+  return __uint_as_float(__float_as_uint(h) + (r >> (32 - DROP)));
 }
 template <> struct Store<kF16> : Store16<__half> {
   static __device__ __forceinline__ T in(E e, int) { return __half2float(e); }
@@ -164,15 +164,6 @@ template <> struct Store<kBF16> : Store16<__nv_bfloat16> {
     *p = __double2bfloat16(f - wgt<double>(a));
   }
 };
-
-// Finite test in the value's own type (an overload that widened a float to
-// double would run on the FP64 pipe, at a small fraction of the FP32 rate).
-__device__ __forceinline__ bool finite_value(float v) {
-  return (__float_as_uint(v) & 0x7f800000u) != 0x7f800000u;
-}
-__device__ __forceinline__ bool finite_value(double v) {
-  return (__double_as_longlong(v) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
-}
 
 // Scalar offset load/store of one population.
 template <class S>
@@ -285,6 +276,10 @@ __device__ __forceinline__ void pull_node(const StepParams& p, const typename S:
 // This is Eq. 276 rewritten so that neither u - u_s nor a rho u_s appear:
 // the 1/eta factor never multiplies a rounding error.
 // ---------------------------------------------------------------------------
+// Correctly rounded reciprocal.
+__device__ __forceinline__ float recip(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double recip(double v) { return __drcp_rn(v); }
+
 template <class T>
 struct Macro {
   T drho, rho, ux, uy, fpx, fpy, Fx, Fy;
@@ -333,7 +328,7 @@ __device__ __forceinline__ Macro<T> macros(const StepParams& p, const T h[9], ui
   const T gx = c.gx, gy = c.gy;
   const T dx = jx + T(0.5) * r.rho * gx - r.rho * usx;
   const T dy = jy + T(0.5) * r.rho * gy - r.rho * usy;
-  const T inv = T(1) / (r.rho * (T(1) + a));
+  const T inv = recip(r.rho * (T(1) + a));
   r.ux = usx + dx * inv;
   r.uy = usy + dy * inv;
   r.fpx = -kap * dx;
@@ -650,7 +645,8 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
   const unsigned key = round_bits(unsigned(t), 0x9e3779b9u);
 
   auto finish_node = [&](const Macro<T>& q, uint8_t m) {
-    if (!(q.rho > T(0)) || !finite_value(q.ux) || !finite_value(q.uy)) atomicOr(p.flag, 1);
+    // a NaN or infinite population makes rho NaN, infinite or non-positive
+    if (!(q.rho > T(0) && q.rho < T(1e30))) atomicOr(p.flag, 1);
     dm += q.drho;
     if (m) {
       any_solid = true;
