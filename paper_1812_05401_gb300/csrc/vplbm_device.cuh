@@ -47,19 +47,18 @@ template <> struct Store<kF64> {
   using E = double;
   using T = double;
   static constexpr bool kSixteen = false;
-  static __device__ __forceinline__ E out_sr(T h, int a, unsigned) { return out(h, a); }
   static __device__ __forceinline__ T in(E e, int a) { return e - wgt<T>(a); }
   static __device__ __forceinline__ E out(T h, int a) { return h + wgt<T>(a); }
   static __device__ __forceinline__ double to_f64(const E* p, int) { return *p; }
   static __device__ __forceinline__ void from_f64(E* p, double f, int) { *p = f; }
-  // npt = 2 consecutive elements as one 16-byte access
-  static __device__ __forceinline__ void load_chunk(const E* p, E e[2]) {
+  // npt = 2 consecutive elements as one 16-byte access, as offsets h = f - w
+  static __device__ __forceinline__ void load_h(const E* p, T h[2], int a) {
     const double2 v = __ldg(reinterpret_cast<const double2*>(p));
-    e[0] = v.x;
-    e[1] = v.y;
+    h[0] = v.x - wgt<T>(a);
+    h[1] = v.y - wgt<T>(a);
   }
-  static __device__ __forceinline__ void store_chunk(E* p, const E e[2]) {
-    *reinterpret_cast<double2*>(p) = make_double2(e[0], e[1]);
+  static __device__ __forceinline__ void store_h(E* p, const T h[2], int a, const unsigned*, bool) {
+    *reinterpret_cast<double2*>(p) = make_double2(h[0] + wgt<T>(a), h[1] + wgt<T>(a));
   }
 };
 template <> struct Store<kF32> {
@@ -70,7 +69,6 @@ template <> struct Store<kF32> {
   static constexpr bool kSixteen = false;
   static __device__ __forceinline__ T in(E e, int) { return e; }
   static __device__ __forceinline__ E out(T h, int) { return h; }
-  static __device__ __forceinline__ E out_sr(T h, int a, unsigned) { return out(h, a); }
   static __device__ __forceinline__ double to_f64(const E* p, int a) {
     return wgt<double>(a) + double(*p);
   }
@@ -78,55 +76,57 @@ template <> struct Store<kF32> {
     *p = float(f - wgt<double>(a));
   }
   // npt = 4 consecutive elements as one 16-byte access
-  static __device__ __forceinline__ void load_chunk(const E* p, E e[4]) {
+  static __device__ __forceinline__ void load_h(const E* p, T h[4], int) {
     const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    e[0] = v.x;
-    e[1] = v.y;
-    e[2] = v.z;
-    e[3] = v.w;
+    h[0] = v.x;
+    h[1] = v.y;
+    h[2] = v.z;
+    h[3] = v.w;
   }
-  static __device__ __forceinline__ void store_chunk(E* p, const E e[4]) {
-    *reinterpret_cast<float4*>(p) = make_float4(e[0], e[1], e[2], e[3]);
+  static __device__ __forceinline__ void store_h(E* p, const T h[4], int, const unsigned*, bool) {
+    *reinterpret_cast<float4*>(p) = make_float4(h[0], h[1], h[2], h[3]);
   }
 };
+// 16-bit offset forms: npt = 4 elements as one 8-byte access.
+// Multipliers deriving each direction's rounding bits from the node's word
+// (distinct odd constants: a bijection of 32-bit words per direction).
+__device__ __forceinline__ constexpr unsigned round_mul(int a) {
+  return a == 0 ? 0x9e3779b1u : a == 1 ? 0x85ebca77u : a == 2 ? 0xc2b2ae3du : a == 3 ? 0x27d4eb2fu
+       : a == 4 ? 0x165667b1u : a == 5 ? 0xd3a2646du : a == 6 ? 0xfd7046c5u : a == 7 ? 0xb55a4f09u
+       : 0x68e31da5u;
+}
+
+// Packed conversion of two FP32 values to two 16-bit values in one register
+// (lo in the low half, the lower address): round to nearest even or toward
+// zero.
+__device__ __forceinline__ unsigned pack_f16_rn(float lo, float hi) {
+  unsigned d;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+__device__ __forceinline__ unsigned pack_f16_rz(float lo, float hi) {
+  unsigned d;
+  asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+__device__ __forceinline__ unsigned pack_bf16_rn(float lo, float hi) {
+  unsigned d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+__device__ __forceinline__ unsigned pack_bf16_rz(float lo, float hi) {
+  unsigned d;
+  asm("cvt.rz.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
 // 16-bit offset forms: npt = 4 elements as one 8-byte access.
 template <class H>
 struct Store16 {
   using E = H;
   using T = float;
   static constexpr bool kSixteen = true;
-  static __device__ __forceinline__ void load_chunk(const E* p, E e[4]) {
-    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
-    e[0] = __ushort_as_half_or_bf16(static_cast<unsigned short>(v.x & 0xffffu));
-    e[1] = __ushort_as_half_or_bf16(static_cast<unsigned short>(v.x >> 16));
-    e[2] = __ushort_as_half_or_bf16(static_cast<unsigned short>(v.y & 0xffffu));
-    e[3] = __ushort_as_half_or_bf16(static_cast<unsigned short>(v.y >> 16));
-  }
-  static __device__ __forceinline__ void store_chunk(E* p, const E e[4]) {
-    uint2 v;
-    v.x = unsigned(bits(e[0])) | (unsigned(bits(e[1])) << 16);
-    v.y = unsigned(bits(e[2])) | (unsigned(bits(e[3])) << 16);
-    *reinterpret_cast<uint2*>(p) = v;
-  }
-  static __device__ __forceinline__ E __ushort_as_half_or_bf16(unsigned short u);
-  static __device__ __forceinline__ unsigned short bits(E e);
 };
-template <>
-__device__ __forceinline__ __half Store16<__half>::__ushort_as_half_or_bf16(unsigned short u) {
-  return __ushort_as_half(u);
-}
-template <>
-__device__ __forceinline__ unsigned short Store16<__half>::bits(__half e) {
-  return __half_as_ushort(e);
-}
-template <>
-__device__ __forceinline__ __nv_bfloat16 Store16<__nv_bfloat16>::__ushort_as_half_or_bf16(unsigned short u) {
-  return __ushort_as_bfloat16(u);
-}
-template <>
-__device__ __forceinline__ unsigned short Store16<__nv_bfloat16>::bits(__nv_bfloat16 e) {
-  return __bfloat16_as_ushort(e);
-}
 // Stochastic rounding of an FP32 value to a format keeping the top 23 - DROP
 // significand bits: add DROP uniformly random bits (the top bits of r) below
 // the kept ones and truncate toward zero, so the magnitude rounds up with
@@ -139,11 +139,31 @@ __device__ __forceinline__ float dither(float h, unsigned r) {
   return __uint_as_float(__float_as_uint(h) + (r >> (32 - DROP)));
 }
 template <> struct Store<kF16> : Store16<__half> {
+  static __device__ __forceinline__ void load_h(const E* p, T h[4], int) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+    h[0] = a.x;
+    h[1] = a.y;
+    h[2] = b.x;
+    h[3] = b.y;
+  }
+  // r[k]: the node's rounding word for node k (stochastic rounding only)
+  static __device__ __forceinline__ void store_h(E* p, const T h[4], int a, const unsigned* r,
+                                                 bool sr) {
+    uint2 v;
+    if (sr) {
+      const unsigned m = round_mul(a);
+      v.x = pack_f16_rz(dither<13>(h[0], r[0] * m), dither<13>(h[1], r[1] * m));
+      v.y = pack_f16_rz(dither<13>(h[2], r[2] * m), dither<13>(h[3], r[3] * m));
+    } else {
+      v.x = pack_f16_rn(h[0], h[1]);
+      v.y = pack_f16_rn(h[2], h[3]);
+    }
+    *reinterpret_cast<uint2*>(p) = v;
+  }
   static __device__ __forceinline__ T in(E e, int) { return __half2float(e); }
   static __device__ __forceinline__ E out(T h, int) { return __float2half_rn(h); }
-  static __device__ __forceinline__ E out_sr(T h, int, unsigned r) {
-    return __float2half_rz(dither<13>(h, r));
-  }
   static __device__ __forceinline__ double to_f64(const E* p, int a) {
     return wgt<double>(a) + double(__half2float(*p));
   }
@@ -152,11 +172,29 @@ template <> struct Store<kF16> : Store16<__half> {
   }
 };
 template <> struct Store<kBF16> : Store16<__nv_bfloat16> {
+  // a bf16 is the upper half of an FP32: widening is a shift or a mask
+  static __device__ __forceinline__ void load_h(const E* p, T h[4], int) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+    h[0] = __uint_as_float(v.x << 16);
+    h[1] = __uint_as_float(v.x & 0xffff0000u);
+    h[2] = __uint_as_float(v.y << 16);
+    h[3] = __uint_as_float(v.y & 0xffff0000u);
+  }
+  static __device__ __forceinline__ void store_h(E* p, const T h[4], int a, const unsigned* r,
+                                                 bool sr) {
+    uint2 v;
+    if (sr) {
+      const unsigned m = round_mul(a);
+      v.x = pack_bf16_rz(dither<16>(h[0], r[0] * m), dither<16>(h[1], r[1] * m));
+      v.y = pack_bf16_rz(dither<16>(h[2], r[2] * m), dither<16>(h[3], r[3] * m));
+    } else {
+      v.x = pack_bf16_rn(h[0], h[1]);
+      v.y = pack_bf16_rn(h[2], h[3]);
+    }
+    *reinterpret_cast<uint2*>(p) = v;
+  }
   static __device__ __forceinline__ T in(E e, int) { return __bfloat162float(e); }
   static __device__ __forceinline__ E out(T h, int) { return __float2bfloat16_rn(h); }
-  static __device__ __forceinline__ E out_sr(T h, int, unsigned r) {
-    return __float2bfloat16_rz(dither<16>(h, r));
-  }
   static __device__ __forceinline__ double to_f64(const E* p, int a) {
     return wgt<double>(a) + double(__bfloat162float(*p));
   }
@@ -190,19 +228,7 @@ __device__ __forceinline__ unsigned round_bits(unsigned counter, unsigned key) {
   return h;
 }
 
-__device__ __forceinline__ constexpr unsigned round_mul(int a) {
-  return a == 0 ? 0x9e3779b1u : a == 1 ? 0x85ebca77u : a == 2 ? 0xc2b2ae3du : a == 3 ? 0x27d4eb2fu
-       : a == 4 ? 0x165667b1u : a == 5 ? 0xd3a2646du : a == 6 ? 0xfd7046c5u : a == 7 ? 0xb55a4f09u
-       : 0x68e31da5u;
-}
 
-// node_bits: round_bits(node, key of the step), so every step draws fresh bits.
-template <class S>
-__device__ __forceinline__ typename S::E out_value(const StepParams& p, typename S::T h, int a,
-                                                   unsigned node_bits) {
-  if (S::kSixteen && p.stochastic) return S::out_sr(h, a, node_bits * round_mul(a));
-  return S::out(h, a);
-}
 
 // ---------------------------------------------------------------------------
 // Pull with boundary conditions (streaming, left-hand side of Eq. LatticeBoltz)
@@ -587,10 +613,7 @@ __device__ __forceinline__ void pull_dir_vec(const StepParams& p, const typename
   const E* row = src + (long long)as * p.plane + (long long)ys * p.pitch;
   T v[N];
   if (!GEN || lane_active) {
-    E e[N];
-    S::load_chunk(row + xb, e);
-#pragma unroll
-    for (int k = 0; k < N; ++k) v[k] = S::in(e[k], A);
+    S::load_h(row + xb, v, A);
   } else {
 #pragma unroll
     for (int k = 0; k < N; ++k) v[k] = T(0);
@@ -682,27 +705,26 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
       m[0] = mv.x;
       m[1 % N] = mv.y;
     }
-    E o[9][N];
+    const bool sr = S::kSixteen && p.stochastic;
+    unsigned nb[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      if (GEN && xb + k >= p.nx) {  // past the last column: keep the padding as it was
-#pragma unroll
-        for (int a = 0; a < 9; ++a) o[a][k] = S::out(h[k][a], a);
-        continue;
-      }
+      nb[k] = sr ? round_bits(unsigned((long long)y * p.nx + (xb + k)), key) : 0u;
+      if (GEN && xb + k >= p.nx) continue;  // past the last column: padding, stored as pulled
       const Macro<T> q = macros<T>(p, h[k], m[k], xb + k, y);
       if (COLL == kSrt)
         collide_srt<T>(p, h[k], q);
       else
         collide_mrt<T>(p, h[k], q);
-      const unsigned nb = (S::kSixteen && p.stochastic)
-                              ? round_bits(unsigned((long long)y * p.nx + (xb + k)), key) : 0u;
-#pragma unroll
-      for (int a = 0; a < 9; ++a) o[a][k] = out_value<S>(p, h[k][a], a, nb);
       finish_node(q, m[k]);
     }
 #pragma unroll
-    for (int a = 0; a < 9; ++a) S::store_chunk(dst + (long long)a * p.plane + i, o[a]);
+    for (int a = 0; a < 9; ++a) {
+      T o[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) o[k] = h[k][a];
+      S::store_h(dst + (long long)a * p.plane + i, o, a, nb, sr);
+    }
   };
 
   if (interior) {
