@@ -182,6 +182,17 @@ vplbm_status vplbm_set_populations(vplbm_solver* s, const double* f, int32_t on_
 /* Mask the next step uses: [ny][nx] bytes, 0 fluid, nonzero solid (host). */
 vplbm_status vplbm_mask(vplbm_solver* s, uint8_t* chi);
 
+/* Checkpoint and restart. vplbm_state_bytes: size of a saved state.
+ * vplbm_save_state writes into the caller's host buffer (synchronizes) the
+ * store f*(t) exactly as stored, the mask, the static solid-velocity field if
+ * one is set, and the step counter t. vplbm_load_state restores them into a
+ * solver created with the same grid and storage (and the same bodies, whose
+ * motion depends on t): stepping on from a loaded state is bitwise identical
+ * to never having stopped. INVALID if the state does not match the solver. */
+size_t vplbm_state_bytes(const vplbm_solver* s);
+vplbm_status vplbm_save_state(vplbm_solver* s, void* buf);
+vplbm_status vplbm_load_state(vplbm_solver* s, const void* buf);
+
 /* Per-step record since the previous call (synchronizes): F_x, F_y, the force
  * the fluid exerts on all solid nodes (minus the sum of Eq. 261 over them,
  * reduced in FP64), and the total density (0 if reduce_mass = 0). Returns up

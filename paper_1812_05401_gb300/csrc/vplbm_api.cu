@@ -836,6 +836,89 @@ vplbm_status vplbm_forces(vplbm_solver* s, double* fx, double* fy, double* mass,
   return VPLBM_OK;
 }
 
+namespace {
+// Checkpoint layout: header, the post-collision store f*(t) as stored (raw
+// elements, [9][ny][pitch]), the mask ([ny][pitch] bytes), and the static
+// solid-velocity field when one is set.
+struct StateHeader {
+  uint64_t magic;
+  int32_t nx, ny, pitch, storage, collision, has_us;
+  int64_t t;
+  uint64_t pop_bytes, mask_bytes, us_bytes;
+};
+constexpr uint64_t kStateMagic = 0x56504c424d535431ull;  // "VPLBMST1"
+
+size_t us_bytes(const vplbm_solver* s) {
+  if (!s->us) return 0;
+  return (s->cfg.storage == kF64 ? sizeof(double2) : sizeof(float2)) * size_t(s->plane);
+}
+}  // namespace
+
+size_t vplbm_state_bytes(const vplbm_solver* s) {
+  if (!s) return 0;
+  return sizeof(StateHeader) + 9 * size_t(s->plane) * s->esize + size_t(s->plane) + us_bytes(s);
+}
+
+vplbm_status vplbm_save_state(vplbm_solver* s, void* buf) {
+  vplbm_status st = check_usable(s);
+  if (st != VPLBM_OK) return st;
+  if (!buf) return fail(s, VPLBM_ERR_INVALID, "buffer is NULL");
+  if ((st = ensure_mask(s, s->t)) != VPLBM_OK) return st;
+  StateHeader h{};
+  h.magic = kStateMagic;
+  h.nx = s->cfg.nx;
+  h.ny = s->cfg.ny;
+  h.pitch = s->pitch;
+  h.storage = s->cfg.storage;
+  h.collision = s->cfg.collision;
+  h.has_us = s->us ? 1 : 0;
+  h.t = s->t;
+  h.pop_bytes = 9 * uint64_t(s->plane) * s->esize;
+  h.mask_bytes = uint64_t(s->plane);
+  h.us_bytes = us_bytes(s);
+  char* out = static_cast<char*>(buf);
+  std::memcpy(out, &h, sizeof(h));
+  out += sizeof(h);
+  VP_CUDA(s, cudaMemcpyAsync(out, s->f[s->cur], h.pop_bytes, cudaMemcpyDeviceToHost, s->stream));
+  out += h.pop_bytes;
+  VP_CUDA(s, cudaMemcpyAsync(out, s->mask, h.mask_bytes, cudaMemcpyDeviceToHost, s->stream));
+  out += h.mask_bytes;
+  if (h.us_bytes)
+    VP_CUDA(s, cudaMemcpyAsync(out, s->us, h.us_bytes, cudaMemcpyDeviceToHost, s->stream));
+  VP_CUDA(s, cudaStreamSynchronize(s->stream));
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_load_state(vplbm_solver* s, const void* buf) {
+  vplbm_status st = check_usable(s);
+  if (st != VPLBM_OK) return st;
+  if (!buf) return fail(s, VPLBM_ERR_INVALID, "buffer is NULL");
+  StateHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (h.magic != kStateMagic || h.nx != s->cfg.nx || h.ny != s->cfg.ny || h.pitch != s->pitch ||
+      h.storage != s->cfg.storage || h.pop_bytes != 9 * uint64_t(s->plane) * s->esize ||
+      h.mask_bytes != uint64_t(s->plane) || h.t < 0)
+    return fail(s, VPLBM_ERR_INVALID, "state does not match this solver's grid and storage");
+  const char* in = static_cast<const char*>(buf) + sizeof(h);
+  VP_CUDA(s, cudaMemcpyAsync(s->f[s->cur], in, h.pop_bytes, cudaMemcpyHostToDevice, s->stream));
+  in += h.pop_bytes;
+  VP_CUDA(s, cudaMemcpyAsync(s->mask, in, h.mask_bytes, cudaMemcpyHostToDevice, s->stream));
+  in += h.mask_bytes;
+  if (h.has_us) {
+    const size_t vs = s->cfg.storage == kF64 ? sizeof(double2) : sizeof(float2);
+    if (h.us_bytes != vs * size_t(s->plane))
+      return fail(s, VPLBM_ERR_INVALID, "state's solid-velocity field does not match");
+    if (!s->us) VP_CUDA(s, cudaMallocAsync(&s->us, h.us_bytes, s->stream));
+    VP_CUDA(s, cudaMemcpyAsync(s->us, in, h.us_bytes, cudaMemcpyHostToDevice, s->stream));
+    s->base.us = s->us;
+  }
+  // pageable host-to-device copies have been staged when they return
+  s->t = h.t;
+  s->ring_read = h.t;
+  s->mask_t = s->moving ? h.t : -1;
+  return VPLBM_OK;
+}
+
 vplbm_status vplbm_forces_async(vplbm_solver* s, double* records, int64_t cap, int64_t* count) {
   vplbm_status st = check_usable(s);
   if (st != VPLBM_OK) return st;

@@ -81,6 +81,10 @@ def lib() -> C.CDLL:
         L.vplbm_set_initial_velocity.argtypes = [P, dp]
         L.vplbm_set_initial_perturbation.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_uint64]
         L.vplbm_forces_async.argtypes = [P, dp, C.c_int64, C.POINTER(C.c_int64)]
+        L.vplbm_state_bytes.argtypes = [P]
+        L.vplbm_state_bytes.restype = C.c_size_t
+        L.vplbm_save_state.argtypes = [P, P]
+        L.vplbm_load_state.argtypes = [P, P]
         L.vplbm_set_mask_and_solid_velocity.argtypes = [P, P, P, C.c_int32]
         L.vplbm_set_bodies.argtypes = [P, C.POINTER(vplbm_body), C.c_int32]
         L.vplbm_step.argtypes = [P, C.c_int64]
@@ -104,7 +108,8 @@ def lib() -> C.CDLL:
         L.vplbm_destroy.argtypes = [P]
         L.vplbm_destroy.restype = None
         for name in ("vplbm_create", "vplbm_set_initial_velocity", "vplbm_set_initial_perturbation",
-                     "vplbm_forces_async", "vplbm_set_mask_and_solid_velocity",
+                     "vplbm_forces_async", "vplbm_save_state", "vplbm_load_state",
+                     "vplbm_set_mask_and_solid_velocity",
                      "vplbm_set_bodies", "vplbm_step", "vplbm_synchronize", "vplbm_moments",
                      "vplbm_populations", "vplbm_set_populations", "vplbm_mask", "vplbm_forces",
                      "vplbm_group_step", "vplbm_enable_timing", "vplbm_fused_timing"):
@@ -171,6 +176,21 @@ def vplbm_forces_async(h, records) -> int:
     _check(h, lib().vplbm_forces_async(h, records.ctypes.data_as(C.POINTER(C.c_double)),
                                        records.shape[0], C.byref(cnt)), "vplbm_forces_async")
     return cnt.value
+
+
+def vplbm_state_bytes(h) -> int:
+    return int(lib().vplbm_state_bytes(h))
+
+
+def vplbm_save_state(h) -> bytes:
+    buf = (C.c_char * vplbm_state_bytes(h))()
+    _check(h, lib().vplbm_save_state(h, buf), "vplbm_save_state")
+    return bytes(buf)
+
+
+def vplbm_load_state(h, state: bytes):
+    buf = (C.c_char * len(state)).from_buffer_copy(state)
+    _check(h, lib().vplbm_load_state(h, buf), "vplbm_load_state")
 
 
 def vplbm_set_mask_and_solid_velocity(h, chi, us=None, on_device: bool = False):

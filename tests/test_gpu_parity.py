@@ -372,3 +372,32 @@ def test_forces_async_matches_forces():
         r = rec.numpy()[:n]
         assert n == 37
         assert np.array_equal(r[:, 0], fx) and np.array_equal(r[:, 1], fy) and np.array_equal(r[:, 2], ms)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+def test_checkpoint_restart_is_bitwise(storage):
+    """Save after n steps, run n more; a new solver loaded from the saved state
+    and run n steps gives the same store and force records bit for bit
+    (moving body: its motion and the rounding bits depend on the step index)."""
+    w = I.moving_cylinder_channel(256, 64, 10.0, 0.05, 100.0, 0, period=500.0, storage=storage)
+    chi = I.random_mask(256, 64, 3, 0.02)
+    us = I.random_solid_velocity(256, 64, 4, 0.01)
+    n = 40
+    with V.Solver.from_workload(w) as a:
+        a.set_mask(chi, us)
+        a.step(n)
+        a.forces()
+        state = V.vplbm_save_state(a.h)
+        a.step(n)
+        fa = a.populations()
+        ra = a.forces()
+    with V.Solver.from_workload(w, with_initial_velocity=False) as b:
+        V.vplbm_load_state(b.h, state)
+        assert b.t == n
+        b.step(n)
+        assert np.array_equal(b.populations(), fa)
+        for x, y in zip(b.forces(), ra):
+            assert np.array_equal(x, y)
+    with V.Solver(V.make_config(128, 64, "mrt", storage)) as c:
+        with pytest.raises(V.VplbmError):
+            V.vplbm_load_state(c.h, state)
