@@ -113,6 +113,10 @@ typedef struct {
 
 typedef struct vplbm_solver vplbm_solver;
 
+/* Environment: VPLBM_TMA=1 (read by vplbm_create) stages the interior tiles
+ * of the single-solver step through shared memory with TMA tensor copies
+ * instead of pulling them with vector loads; results are bitwise the same. */
+
 /* Fills cfg with defaults: SRT, FP32, periodic, tau 0.8, Lambda 3/16,
  * eta 1e-7, rho0 1, mass reduction on, ring of 4096 steps, stochastic
  * rounding of 16-bit stores. nx = ny = 0. */

@@ -52,6 +52,11 @@ template <> struct Store<kF64> {
   static __device__ __forceinline__ double to_f64(const E* p, int) { return *p; }
   static __device__ __forceinline__ void from_f64(E* p, double f, int) { *p = f; }
   // npt = 2 consecutive elements as one 16-byte access, as offsets h = f - w
+  static __device__ __forceinline__ void load_h_shared(const E* p, T h[2], int a) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    h[0] = v.x - wgt<T>(a);
+    h[1] = v.y - wgt<T>(a);
+  }
   static __device__ __forceinline__ void load_h(const E* p, T h[2], int a) {
     const double2 v = __ldg(reinterpret_cast<const double2*>(p));
     h[0] = v.x - wgt<T>(a);
@@ -76,6 +81,13 @@ template <> struct Store<kF32> {
     *p = float(f - wgt<double>(a));
   }
   // npt = 4 consecutive elements as one 16-byte access
+  static __device__ __forceinline__ void load_h_shared(const E* p, T h[4], int) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    h[0] = v.x;
+    h[1] = v.y;
+    h[2] = v.z;
+    h[3] = v.w;
+  }
   static __device__ __forceinline__ void load_h(const E* p, T h[4], int) {
     const float4 v = __ldg(reinterpret_cast<const float4*>(p));
     h[0] = v.x;
@@ -139,8 +151,13 @@ __device__ __forceinline__ float dither(float h, unsigned r) {
   return __uint_as_float(__float_as_uint(h) + (r >> (32 - DROP)));
 }
 template <> struct Store<kF16> : Store16<__half> {
+  static __device__ __forceinline__ void load_h_shared(const E* p, T h[4], int a) {
+    unpack(*reinterpret_cast<const uint2*>(p), h);
+  }
   static __device__ __forceinline__ void load_h(const E* p, T h[4], int) {
-    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+    unpack(__ldg(reinterpret_cast<const uint2*>(p)), h);
+  }
+  static __device__ __forceinline__ void unpack(const uint2 v, T h[4]) {
     const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
     const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
     h[0] = a.x;
@@ -172,9 +189,14 @@ template <> struct Store<kF16> : Store16<__half> {
   }
 };
 template <> struct Store<kBF16> : Store16<__nv_bfloat16> {
-  // a bf16 is the upper half of an FP32: widening is a shift or a mask
+  static __device__ __forceinline__ void load_h_shared(const E* p, T h[4], int) {
+    unpack(*reinterpret_cast<const uint2*>(p), h);
+  }
   static __device__ __forceinline__ void load_h(const E* p, T h[4], int) {
-    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+    unpack(__ldg(reinterpret_cast<const uint2*>(p)), h);
+  }
+  // a bf16 is the upper half of an FP32: widening is a shift or a mask
+  static __device__ __forceinline__ void unpack(const uint2 v, T h[4]) {
     h[0] = __uint_as_float(v.x << 16);
     h[1] = __uint_as_float(v.x & 0xffff0000u);
     h[2] = __uint_as_float(v.y << 16);
@@ -643,8 +665,89 @@ __device__ __forceinline__ void pull_dir_vec(const StepParams& p, const typename
   }
 }
 
-template <int STORE, int COLL>
-__device__ __forceinline__ void step_tile(const StepParams& p, int tile, long long t) {
+// ---------------------------------------------------------------------------
+// TMA (cp.async.bulk.tensor) staging of interior tiles through shared memory.
+// One elected thread arms an mbarrier with the stage's byte count and issues
+// one 3D tensor copy per plane; the block waits on the barrier's phase. Every
+// wait is bounded: on expiry the block records a timeout in the error flag,
+// waits (bounded) for its copies still in flight, and skips its tile.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* ptr) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(ptr));
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait on a barrier phase: at most 2^20 polls and about one second
+// (2^31 SM clock cycles), whichever comes first.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  const long long start = clock64();
+  for (int i = 0; i < (1 << 20); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (clock64() - start > (1ll << 31)) break;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map, int x, int y,
+                                            int z, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+// Pull of direction A for the 8-row chunk in shared memory: `row` is this
+// warp's row of plane A (box of halo + tile + halo elements).
+template <class S, int N, int A>
+__device__ __forceinline__ void pull_dir_smem(const typename S::E* row, int lane,
+                                              typename S::T (&h)[N][9]) {
+  using T = typename S::T;
+  using E = typename S::E;
+  constexpr int HALO = 16 / int(sizeof(E));
+  T v[N];
+  S::load_h_shared(row + HALO + lane * N, v, A);
+  if (cx(A) == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) h[k][A] = v[k];
+  } else if (cx(A) == 1) {  // node k pulls from x - 1
+    T left = __shfl_up_sync(0xffffffffu, v[N - 1], 1);
+    if (lane == 0) left = S::in(row[HALO - 1], A);
+    h[0][A] = left;
+#pragma unroll
+    for (int k = 1; k < N; ++k) h[k][A] = v[k - 1];
+  } else {  // node k pulls from x + 1
+    T right = __shfl_down_sync(0xffffffffu, v[0], 1);
+    if (lane == kLanes - 1) right = S::in(row[HALO + kLanes * N], A);
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) h[k][A] = v[k + 1];
+    h[N - 1][A] = right;
+  }
+}
+
+// TMA: interior tiles are staged through shared memory (tma_smem, the
+// kernel's dynamic shared memory of tma_smem_bytes(STORE)); a separate kernel
+// instantiation, so the direct-pull kernel carries none of its code.
+template <int STORE, int COLL, bool TMA = false>
+__device__ __forceinline__ void step_tile(const StepParams& p, int tile, long long t,
+                                          unsigned char* tma_smem) {
   using S = Store<STORE>;
   using T = typename S::T;
   using E = typename S::E;
@@ -652,6 +755,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
   constexpr int TX = kLanes * N;
   __shared__ double sm[kThreads / 32][3];
   __shared__ T smass[kThreads / 32];
+  __shared__ __align__(8) unsigned long long tma_bar[kTmaStages];
 
   const int lane = threadIdx.x, warp = threadIdx.y;
   const int tx = tile % p.tiles_x;
@@ -678,20 +782,10 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
     }
   };
 
-  auto do_row = [&](int y, auto gen) {
+  // Collide and store one row of pulled populations (lane_active: the lane's
+  // first node lies in the domain).
+  auto process_row = [&](int y, auto& h, auto gen) {
     constexpr bool GEN = decltype(gen)::value;
-    const bool lane_active = !GEN || xb < p.nx;
-    T h[N][9];
-    pull_dir_vec<S, N, 0, GEN>(p, src, xb, y, lane, lane_active, h);
-    pull_dir_vec<S, N, 1, GEN>(p, src, xb, y, lane, lane_active, h);
-    pull_dir_vec<S, N, 2, GEN>(p, src, xb, y, lane, lane_active, h);
-    pull_dir_vec<S, N, 3, GEN>(p, src, xb, y, lane, lane_active, h);
-    pull_dir_vec<S, N, 4, GEN>(p, src, xb, y, lane, lane_active, h);
-    pull_dir_vec<S, N, 5, GEN>(p, src, xb, y, lane, lane_active, h);
-    pull_dir_vec<S, N, 6, GEN>(p, src, xb, y, lane, lane_active, h);
-    pull_dir_vec<S, N, 7, GEN>(p, src, xb, y, lane, lane_active, h);
-    pull_dir_vec<S, N, 8, GEN>(p, src, xb, y, lane, lane_active, h);
-    if (!lane_active) return;
     const long long i = (long long)y * p.pitch + xb;
     uint8_t m[N];
     if (N == 4) {
@@ -727,7 +821,81 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
     }
   };
 
-  if (interior) {
+  auto do_row = [&](int y, auto gen) {
+    constexpr bool GEN = decltype(gen)::value;
+    const bool lane_active = !GEN || xb < p.nx;
+    T h[N][9];
+    pull_dir_vec<S, N, 0, GEN>(p, src, xb, y, lane, lane_active, h);
+    pull_dir_vec<S, N, 1, GEN>(p, src, xb, y, lane, lane_active, h);
+    pull_dir_vec<S, N, 2, GEN>(p, src, xb, y, lane, lane_active, h);
+    pull_dir_vec<S, N, 3, GEN>(p, src, xb, y, lane, lane_active, h);
+    pull_dir_vec<S, N, 4, GEN>(p, src, xb, y, lane, lane_active, h);
+    pull_dir_vec<S, N, 5, GEN>(p, src, xb, y, lane, lane_active, h);
+    pull_dir_vec<S, N, 6, GEN>(p, src, xb, y, lane, lane_active, h);
+    pull_dir_vec<S, N, 7, GEN>(p, src, xb, y, lane, lane_active, h);
+    pull_dir_vec<S, N, 8, GEN>(p, src, xb, y, lane, lane_active, h);
+    if (!lane_active) return;
+    process_row(y, h, gen);
+  };
+
+  if (TMA && interior) {
+    // Chunk c (rows y0 + 8c .. y0 + 8c + 7, one per warp) of all nine planes
+    // goes to stage c % kTmaStages; plane A's box starts at row y0 + 8c - cy(A)
+    // and column x0 - halo, so the box row of warp w is the source row of
+    // direction A for node row y0 + 8c + w.
+    constexpr int HALO = tma_halo(STORE);
+    constexpr int BOX = tma_box_x(STORE);
+    constexpr unsigned STAGE = unsigned(tma_stage_bytes(STORE));
+    constexpr int PLANE = kTmaRows * BOX;  // elements of one plane's box
+    const int tid = lane + warp * kLanes;
+    auto issue = [&](int c) {
+      const unsigned bar = smem_u32(&tma_bar[c % kTmaStages]);
+      mbar_expect_tx(bar, STAGE);
+      const unsigned base = smem_u32(tma_smem + (c % kTmaStages) * STAGE);
+#pragma unroll
+      for (int a = 0; a < 9; ++a)
+        tma_load_3d(base + unsigned(a * PLANE * int(sizeof(E))), &p.tmap, x0 - HALO,
+                    y0 + c * kTmaRows - cy(a), a, bar);
+    };
+    if (tid == 0) {
+      for (int st = 0; st < kTmaStages; ++st) mbar_init(smem_u32(&tma_bar[st]), 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0)
+      for (int c = 0; c < kTmaStages && c < kRows; ++c) issue(c);
+    bool ok = true;
+#pragma unroll 1
+    for (int c = 0; c < kRows; ++c) {
+      const unsigned bar = smem_u32(&tma_bar[c % kTmaStages]);
+      const unsigned parity = unsigned(c / kTmaStages) & 1u;
+      ok = __syncthreads_and(ok && mbar_wait(bar, parity)) != 0;
+      if (!ok) {
+        // give up on this tile: record the timeout, let the copies in flight land
+        if (tid == 0) {
+          atomicOr(p.flag, 2);
+          for (int d = c; d < kRows && d < c + kTmaStages; ++d)  // issued, not yet landed
+            mbar_wait(smem_u32(&tma_bar[d % kTmaStages]), unsigned(d / kTmaStages) & 1u);
+        }
+        __syncthreads();
+        break;
+      }
+      const E* stage = reinterpret_cast<const E*>(tma_smem + (c % kTmaStages) * STAGE) + warp * BOX;
+      T h[N][9];
+      pull_dir_smem<S, N, 0>(stage + 0 * PLANE, lane, h);
+      pull_dir_smem<S, N, 1>(stage + 1 * PLANE, lane, h);
+      pull_dir_smem<S, N, 2>(stage + 2 * PLANE, lane, h);
+      pull_dir_smem<S, N, 3>(stage + 3 * PLANE, lane, h);
+      pull_dir_smem<S, N, 4>(stage + 4 * PLANE, lane, h);
+      pull_dir_smem<S, N, 5>(stage + 5 * PLANE, lane, h);
+      pull_dir_smem<S, N, 6>(stage + 6 * PLANE, lane, h);
+      pull_dir_smem<S, N, 7>(stage + 7 * PLANE, lane, h);
+      pull_dir_smem<S, N, 8>(stage + 8 * PLANE, lane, h);
+      __syncthreads();  // every warp has read stage c % kTmaStages
+      if (tid == 0 && c + kTmaStages < kRows) issue(c + kTmaStages);
+      process_row(y0 + warp + c * kWarps, h, std::false_type());
+    }
+  } else if (interior) {
 #pragma unroll 1
     for (int r = 0; r < kRows; ++r) do_row(y0 + warp + r * kWarps, std::false_type());
   } else {
@@ -784,9 +952,10 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
   finish_reduction(p, tile, t, ts, sm);
 }
 
-template <int STORE, int COLL>
+template <int STORE, int COLL, bool TMA>
 __global__ void __launch_bounds__(kThreads, min_blocks_per_sm(STORE)) fused_step_kernel(const __grid_constant__ StepParams p) {
-  step_tile<STORE, COLL>(p, blockIdx.x, p.t);
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  step_tile<STORE, COLL, TMA>(p, blockIdx.x, p.t, dyn_smem);
 }
 
 // Grouped launch for serving: block b runs tile table[b].tile of solver
@@ -811,10 +980,11 @@ __global__ void __launch_bounds__(kThreads, min_blocks_per_sm(STORE))
     for (int w = tid; w < int(sizeof(StepParams) / sizeof(int)); w += kThreads) to[w] = __ldg(from + w);
   }
   __syncthreads();
+  // grouped launches pull directly (use_tma is off in their parameters)
   if (sp.collision == kSrt)
-    step_tile<STORE, kSrt>(sp, gt.tile, sp.t + k);
+    step_tile<STORE, kSrt>(sp, gt.tile, sp.t + k, nullptr);
   else
-    step_tile<STORE, kMrt>(sp, gt.tile, sp.t + k);
+    step_tile<STORE, kMrt>(sp, gt.tile, sp.t + k, nullptr);
 }
 
 // ---------------------------------------------------------------------------

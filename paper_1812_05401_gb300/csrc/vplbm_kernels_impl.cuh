@@ -13,12 +13,34 @@ static dim3 node_grid(const StepParams& p) {
   return dim3((p.nx + kBlockX - 1) / kBlockX, (p.ny + kBlockY - 1) / kBlockY);
 }
 
-cudaError_t VPLBM_FN(launch_fused_)(int coll, const StepParams& p, cudaStream_t st) {
-  if (coll == kSrt)
-    fused_step_kernel<VPLBM_STORE, kSrt><<<p.n_tiles, dim3(kLanes, kWarps), 0, st>>>(p);
-  else
-    fused_step_kernel<VPLBM_STORE, kMrt><<<p.n_tiles, dim3(kLanes, kWarps), 0, st>>>(p);
+// Dynamic shared memory of the TMA-staged interior tiles (set once per
+// kernel: more than the default 48 KB needs an opt-in).
+template <int COLL>
+static cudaError_t allow_tma_smem() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fused_step_kernel<VPLBM_STORE, COLL, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       tma_smem_bytes(VPLBM_STORE));
+  done = e == cudaSuccess;
+  return e;
+}
+
+template <int COLL>
+static cudaError_t launch_fused_coll(const StepParams& p, cudaStream_t st) {
+  if (p.use_tma) {
+    const cudaError_t e = allow_tma_smem<COLL>();
+    if (e != cudaSuccess) return e;
+    fused_step_kernel<VPLBM_STORE, COLL, true>
+        <<<p.n_tiles, dim3(kLanes, kWarps), tma_smem_bytes(VPLBM_STORE), st>>>(p);
+  } else {
+    fused_step_kernel<VPLBM_STORE, COLL, false><<<p.n_tiles, dim3(kLanes, kWarps), 0, st>>>(p);
+  }
   return cudaGetLastError();
+}
+
+cudaError_t VPLBM_FN(launch_fused_)(int coll, const StepParams& p, cudaStream_t st) {
+  return coll == kSrt ? launch_fused_coll<kSrt>(p, st) : launch_fused_coll<kMrt>(p, st);
 }
 
 cudaError_t VPLBM_FN(launch_group_)(const StepParams* d_params, const GroupTile* d_table,
