@@ -44,6 +44,7 @@ class Result:
     fx: np.ndarray = field(repr=False, default=None)
     fy: np.ndarray = field(repr=False, default=None)
     populations: np.ndarray | None = field(repr=False, default=None)
+    error: str | None = None  # set if the solve diverged (its results are not valid)
 
     @property
     def latency(self) -> float:
@@ -62,7 +63,9 @@ class _Active:
 
 class Server:
     def __init__(self, budget_bytes: int, max_active: int = 256, round_steps: int = 500,
-                 stream=None, keep_populations: bool = False):
+                 stream=None, keep_populations: bool = False, on_admit=None):
+        """on_admit(request, solver): optional hook called right after a solve is
+        created (before its first step)."""
         import torch
         self.torch = torch
         self.budget = int(budget_bytes)
@@ -70,7 +73,9 @@ class Server:
         self.round_steps = int(round_steps)
         self.stream = stream or torch.cuda.Stream()
         self.keep_populations = keep_populations
+        self.on_admit = on_admit
         self.rejected = []
+        self.errors = {}
 
     def _create(self, w):
         cfg, bodies = V.config_from_workload(w, ring_len=max(1, w.steps), stream=self.stream,
@@ -102,11 +107,16 @@ class Server:
                     rec = a.records.numpy()
                     fx, fy = rec[:, 0].copy(), rec[:, 1].copy()
                     pops = a.solver.populations() if self.keep_populations else None
+                    err = None
+                    try:  # the stream is past this solve's last round: no wait
+                        a.solver.synchronize()
+                    except V.VplbmError as e:  # this solve diverged; the others are unaffected
+                        err = str(e)
                     t_done = now()
                     w = a.req.workload
                     results.append(Result(a.req.rid, w.name, a.req.arrival if realtime else 0.0,
                                           a.admitted, t_done, w.steps, w.nx * w.ny, w.storage,
-                                          w.collision, fx, fy, pops))
+                                          w.collision, fx, fy, pops, err))
                     a.solver.close()
                     used -= a.footprint
                 if not block and not inflight:
@@ -126,7 +136,14 @@ class Server:
                 if used + fp > self.budget:
                     break
                 pending.popleft()
-                s, fp = self._create(req.workload)
+                try:
+                    s, fp = self._create(req.workload)
+                except V.VplbmError as e:  # e.g. out of device memory: refuse this request only
+                    self.rejected.append(req.rid)
+                    self.errors[req.rid] = str(e)
+                    continue
+                if self.on_admit:
+                    self.on_admit(req, s)
                 used += fp
                 active.append(_Active(req, s, req.workload.steps, now(), fp))
             if not active:
@@ -160,6 +177,7 @@ class Server:
         updates = float(sum(r.nodes * r.steps for r in results))
         return {
             "completed": len(results),
+            "failed": sum(1 for r in results if r.error),
             "makespan_s": round(makespan, 3),
             "solves_per_s": round(len(results) / makespan, 3) if makespan > 0 else None,
             "p50_latency_s": round(float(np.percentile(lat, 50)), 4),

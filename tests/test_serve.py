@@ -78,3 +78,34 @@ def test_late_arrivals_join_running_rounds(mods):
                      if a.rid != b.rid and a.admitted < b.finished and b.admitted < a.finished)
     assert overlapped > 0
     assert rep["p99_latency_s"] >= rep["p50_latency_s"] > 0
+
+
+def test_a_diverging_solve_fails_alone(mods):
+    """Failure isolation: one request is given a non-finite state (written from
+    the host right after admission); it is reported as diverged and every other
+    request in the same grouped launches completes with the result it has alone."""
+    serve, V = mods
+    import numpy as np
+    reqs = _small_mix(8, seed=21)
+    bad = reqs[3].rid
+
+    def poison(req, solver):
+        if req.rid == bad:
+            f = solver.populations()
+            f[:, 2, 2] = np.nan
+            solver.set_populations(f)
+
+    srv = serve.Server(budget_bytes=1 << 30, max_active=8, round_steps=32, keep_populations=True,
+                       on_admit=poison)
+    results, rep = srv.run(reqs, realtime=False)
+    assert rep["completed"] == len(reqs) and rep["failed"] == 1
+    by_id = {r.rid: r for r in results}
+    assert by_id[bad].error and "diverged" in by_id[bad].error
+    for req in reqs:
+        if req.rid == bad:
+            continue
+        assert by_id[req.rid].error is None
+        with V.Solver.from_workload(req.workload, ring_len=max(1, req.workload.steps),
+                                    reduce_mass=False, device_init=True) as s:
+            s.step(req.workload.steps)
+            assert np.array_equal(s.populations(), by_id[req.rid].populations)
