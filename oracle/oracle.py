@@ -83,6 +83,8 @@ def lib():
             L.orc_run.argtypes = [cp, dp, C.c_int64, C.c_int64, dp, dp, dp]
             L.orc_moments.argtypes = [cp, dp, C.c_int64, dp, dp, dp]
             L.orc_num_threads.restype = C.c_int
+            L.orc_momentum_exchange.argtypes = [cp, dp, C.c_int64, dp, dp]
+            L.orc_momentum_exchange.restype = C.c_int
             for name in ("orc_mask", "orc_init_equilibrium", "orc_run", "orc_moments"):
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -274,6 +276,16 @@ def moments(cfg: Config, f: np.ndarray, t: int = 0):
     rc = lib().orc_moments(C.byref(s), _dp(f), t, _dp(rho), _dp(ux), _dp(uy))
     assert rc == 0
     return rho, ux, uy
+
+
+def momentum_exchange(cfg: Config, f: np.ndarray, t: int = 0):
+    """Momentum-exchange force on the solids from the store f*(t)."""
+    s, keep = cfg.c_struct()
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    fx, fy = C.c_double(), C.c_double()
+    rc = lib().orc_momentum_exchange(C.byref(s), _dp(f), t, C.byref(fx), C.byref(fy))
+    assert rc == 0
+    return fx.value, fy.value
 
 
 def num_threads() -> int:

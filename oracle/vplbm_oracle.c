@@ -558,6 +558,46 @@ int orc_moments(const orc_config* c, const double* f, int64_t t, double* rho,
   return 0;
 }
 
+int orc_momentum_exchange(const orc_config* c, const double* f, int64_t t, double* fx,
+                          double* fy) {
+  const int nx = c->nx, ny = c->ny;
+  const size_t plane = (size_t)nx * (size_t)ny;
+  uint8_t* chi = (uint8_t*)malloc(plane);
+  if (!chi) return 2;
+  orc_model m;
+  model_init(c, &m);
+  orc_mask(c, t, chi, NULL);
+  double sx = 0.0, sy = 0.0;
+  for (int y = 0; y < ny; ++y) {
+    for (int x = 0; x < nx; ++x) {
+      if (chi[(size_t)y * nx + x]) continue; /* links start at fluid nodes */
+      for (int a = 1; a < 9; ++a) {
+        int xs = x + m.xi[a][0], ys = y + m.xi[a][1];
+        if (xs < 0 || xs >= nx) {
+          if (c->bc_x != ORC_BC_PERIODIC) continue;
+          xs = (xs + nx) % nx;
+        }
+        if (ys < 0 || ys >= ny) {
+          if (c->bc_y != ORC_BC_PERIODIC) continue;
+          ys = (ys + ny) % ny;
+        }
+        if (!chi[(size_t)ys * nx + xs]) continue;
+        int abar = 0;
+        for (int b = 0; b < 9; ++b)
+          if (m.xi[b][0] == -m.xi[a][0] && m.xi[b][1] == -m.xi[a][1]) abar = b;
+        const double flow = f[(size_t)a * plane + (size_t)y * nx + x] +
+                            f[(size_t)abar * plane + (size_t)ys * nx + xs];
+        sx += m.xi[a][0] * flow;
+        sy += m.xi[a][1] * flow;
+      }
+    }
+  }
+  free(chi);
+  *fx = sx;
+  *fy = sy;
+  return 0;
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

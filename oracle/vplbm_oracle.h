@@ -100,6 +100,14 @@ int orc_run(const orc_config* c, double* f, int64_t t0, int64_t n,
 int orc_moments(const orc_config* c, const double* f, int64_t t,
                 double* rho, double* ux, double* uy);
 
+/* Momentum-exchange force on the solids at step index t (the force measure of
+ * Section 3.3, after Ladd): over every link from a fluid node x_f to a solid
+ * node x_s = x_f + xi_alpha, the momentum xi_alpha [f*_alpha(x_f) +
+ * f*_abar(x_s)] of the store f*(t) crosses into the solid (abar: the opposite
+ * direction). Links that leave the grid through a non-periodic side are not
+ * counted. */
+int orc_momentum_exchange(const orc_config* c, const double* f, int64_t t, double* fx, double* fy);
+
 int orc_num_threads(void);
 
 #ifdef __cplusplus

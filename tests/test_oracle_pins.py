@@ -513,3 +513,70 @@ def test_splitmix64_published_vectors():
     assert int(I.splitmix64(0, 1)[0]) == 0xE220A8397B1DCDAF
     a = I.uniform01(5, 1000)
     assert a.min() >= 0.0 and a.max() < 1.0 and abs(a.mean() - 0.5) < 0.03
+
+
+@pytest.mark.parametrize("coll", [O.SRT, O.MRT])
+def test_momentum_exchange_balances_solid_momentum(coll):
+    """Momentum balance of the solid region over one step (exact up to
+    round-off, periodic grid): the momentum the links carry into the solid
+    (momentum exchange, Section 3.3) plus the total force on the solid nodes
+    (penalization and the uniform body force rho g) is the change of the solid
+    region's stored momentum,
+      P*_solid(t+1) - P*_solid(t) = F_ME(t) - F_body(t) + sum_solid rho g,
+    where F_body = -sum_solid f_pen is the force record of the step. A wrong
+    link, direction or sign in the momentum exchange breaks it."""
+    n, g = 40, (1e-6, -2e-6)
+    cfg = O.Config(nx=n, ny=n, collision=coll, tau=0.7, lam=3 / 16, g=g,
+                   bodies=[O.Body(19.5, 20.0, 6.3, omega=0.002), O.Body(8.0, 30.0, 3.0)])
+    f = O.init_equilibrium(cfg, 1.0, I.velocity_field(n, n, (0.02, -0.01), 5e-3, seed=8))
+    O.run(cfg, f, 20)  # develop some flow around the bodies
+    xi = O.velocity_set().astype(float)
+    for t in range(20, 23):
+        chi, _ = O.mask(cfg, t)
+        solid = chi.astype(bool)[None]
+        p0 = np.einsum("ai,ayx->i", xi, f * solid)
+        me = np.array(O.momentum_exchange(cfg, f, t))
+        fx, fy, _ = O.run(cfg, f, 1, t0=t)
+        p1 = np.einsum("ai,ayx->i", xi, f * solid)
+        mass_solid = (f * solid).sum()  # the collision keeps each node's mass
+        expect = me - np.array([fx[0], fy[0]]) + mass_solid * np.array(g)
+        np.testing.assert_allclose(p1 - p0, expect, rtol=0, atol=1e-13)
+        assert np.hypot(*me) > 1e-5  # the links carry momentum to check
+
+
+def test_momentum_exchange_single_node_closed_form():
+    """One solid node at rest (its store at f_eq(rho, 0)) in a uniform stream
+    (the fluid store at f_eq(rho, u)): the eight links bring in
+    sum_a xi_a f_a^eq(rho, u) = rho u and take out
+    sum_a xi_a f_abar^eq(rho, 0) = 0, so F = rho u exactly. With the solid
+    node in the stream as well, the two sums cancel and F = 0."""
+    n, rho, u0 = 9, 1.02, (0.03, -0.02)
+    chi = np.zeros((n, n), np.uint8)
+    chi[4, 4] = 1
+    cfg = O.Config(nx=n, ny=n, chi=chi)
+    u = np.zeros((2, n, n))
+    u[0], u[1] = u0
+    f_all = O.init_equilibrium(cfg, rho, u)
+    np.testing.assert_allclose(O.momentum_exchange(cfg, f_all, 0), [0, 0], rtol=0, atol=1e-15)
+    u[:, 4, 4] = 0.0
+    f = O.init_equilibrium(cfg, rho, u)
+    np.testing.assert_allclose(O.momentum_exchange(cfg, f, 0), [rho * u0[0], rho * u0[1]],
+                               rtol=0, atol=1e-15)
+    # a node at the edge of a periodic grid takes its links across the seam;
+    # with walls in y (free slip) the links leaving the grid are dropped
+    chi2 = np.zeros((n, n), np.uint8)
+    chi2[0, 4] = 1
+    u2 = np.zeros((2, n, n))
+    u2[0], u2[1] = u0
+    u2[:, 0, 4] = 0.0
+    per = O.Config(nx=n, ny=n, chi=chi2)
+    np.testing.assert_allclose(O.momentum_exchange(per, O.init_equilibrium(per, rho, u2), 0),
+                               [rho * u0[0], rho * u0[1]], rtol=0, atol=1e-15)
+    slip = O.Config(nx=n, ny=n, chi=chi2, bc_y=O.BC_FREE_SLIP)
+    fs = O.init_equilibrium(slip, rho, u2)
+    xi = O.velocity_set()
+    feq_u, feq_0 = O.equilibrium(rho, *u0), O.equilibrium(rho, 0.0, 0.0)
+    opp = [int(np.flatnonzero((xi == -xi[a]).all(1))[0]) for a in range(9)]
+    # links from y = -1 leave the grid: only directions with xi_y <= 0 remain
+    ex = sum(xi[a] * (feq_u[a] + feq_0[opp[a]]) for a in range(1, 9) if xi[a][1] <= 0)
+    np.testing.assert_allclose(O.momentum_exchange(slip, fs, 0), ex, rtol=0, atol=1e-15)
