@@ -19,7 +19,8 @@ _SRC = os.path.join(_HERE, "vplbm_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
 SRT, MRT = 0, 1
-BC_PERIODIC, BC_INLET_OUTLET, BC_FREE_SLIP = 0, 1, 2
+BC_PERIODIC, BC_INLET_OUTLET, BC_FREE_SLIP, BC_INLET_CONVECTIVE = 0, 1, 2, 3
+OUTLET_DIRS = (3, 6, 7)  # directions entering through the outlet, rows of the outlet state
 
 
 class OrcBody(C.Structure):
@@ -38,6 +39,7 @@ class OrcConfig(C.Structure):
         ("u_in", C.c_double * 2), ("g", C.c_double * 2), ("rates", C.c_double * 9),
         ("chi", C.POINTER(C.c_uint8)), ("us", C.POINTER(C.c_double)),
         ("bodies", C.POINTER(OrcBody)), ("n_bodies", C.c_int32), ("pad_", C.c_int32),
+        ("u_conv", C.c_double), ("outlet", C.POINTER(C.c_double)),
     ]
 
 
@@ -124,6 +126,8 @@ class Config:
     chi: np.ndarray | None = None     # uint8 [ny][nx]
     us: np.ndarray | None = None      # float64 [2][ny][nx]
     bodies: list = field(default_factory=list)
+    u_conv: float = 0.0               # convective outlet velocity U_c
+    outlet: np.ndarray | None = None  # convective outlet state [3][ny], updated by run()
 
     def c_struct(self):
         """Returns (struct, keepalive) — keepalive holds the arrays it points to."""
@@ -148,6 +152,12 @@ class Config:
             assert us.shape == (2, self.ny, self.nx)
             keep.append(us)
             s.us = _dp(us)
+        if self.outlet is not None:
+            # the state is updated in place: it must be the caller's own array
+            assert self.outlet.dtype == np.float64 and self.outlet.flags.c_contiguous
+            assert self.outlet.shape == (3, self.ny)
+            s.outlet = _dp(self.outlet)
+        s.u_conv = self.u_conv
         if self.bodies:
             arr = (OrcBody * len(self.bodies))()
             for i, b in enumerate(self.bodies):
@@ -286,6 +296,12 @@ def momentum_exchange(cfg: Config, f: np.ndarray, t: int = 0):
     rc = lib().orc_momentum_exchange(C.byref(s), _dp(f), t, C.byref(fx), C.byref(fy))
     assert rc == 0
     return fx.value, fy.value
+
+
+def outlet_from_store(f: np.ndarray) -> np.ndarray:
+    """Convective outlet state that starts as a zero-gradient copy of the last
+    column of the store f[9][ny][nx]."""
+    return np.ascontiguousarray(f[list(OUTLET_DIRS), :, -1], dtype=np.float64)
 
 
 def num_threads() -> int:

@@ -421,11 +421,12 @@ int orc_mask(const orc_config* c, int64_t t, uint8_t* chi, double* us) {
  *    first and last rows: a population arriving from beyond the wall is the
  *    mirror image (xi_y -> -xi_y) of the one that left the same row.
  * x: periodic, or a ghost column x = -1 held at f_eq(1, u_in) (uniform inlet)
- *    and a ghost column x = nx that copies column nx - 1 (zero-gradient outlet).
+ *    and a ghost column x = nx that copies column nx - 1 (zero-gradient outlet)
+ *    or holds the convective outlet state of this step (ghost, [9][ny]).
  * ------------------------------------------------------------------------- */
 
 static double pull_one(const orc_model* m, const orc_config* c, const double* src,
-                       int a, int x, int y) {
+                       const double* ghost, int a, int x, int y) {
   const int nx = c->nx, ny = c->ny;
   const size_t plane = (size_t)nx * (size_t)ny;
   int as = a;
@@ -444,11 +445,35 @@ static double pull_one(const orc_model* m, const orc_config* c, const double* sr
       xs = (xs + nx) % nx;
     } else if (xs < 0) {
       return m->feq_in[as];
+    } else if (c->bc_x == ORC_BC_INLET_CONVECTIVE) {
+      return ghost[(size_t)as * ny + ys];
     } else {
       xs = nx - 1;
     }
   }
   return src[(size_t)as * plane + (size_t)ys * nx + xs];
+}
+
+/* The three directions entering through the outlet, in the order of the
+ * outlet state's rows. */
+static const int OUTLET_DIRS[3] = {3, 6, 7};
+
+/* Convective outlet: ghost[as][y] := (g^{t-1} + U_c f*_as(nx - 1, y)) / (1 + U_c)
+ * for the directions entering through the outlet (see vplbm_oracle.h). */
+static int outlet_advance(const orc_config* c, const double* src, double* ghost) {
+  if (c->bc_x != ORC_BC_INLET_CONVECTIVE) return 0;
+  if (!c->outlet || !(c->u_conv >= 0.0)) return 1;
+  const int nx = c->nx, ny = c->ny;
+  const size_t plane = (size_t)nx * (size_t)ny;
+  for (int k = 0; k < 3; ++k) {
+    const int a = OUTLET_DIRS[k];
+    for (int y = 0; y < ny; ++y) {
+      const double g_old = c->outlet[(size_t)k * ny + y];
+      const double f_last = src[(size_t)a * plane + (size_t)y * nx + (nx - 1)];
+      ghost[(size_t)a * ny + y] = (g_old + c->u_conv * f_last) / (1.0 + c->u_conv);
+    }
+  }
+  return 0;
 }
 
 int orc_init_equilibrium(const orc_config* c, double rho0, const double* u_init,
@@ -475,11 +500,13 @@ int orc_run(const orc_config* c, double* f, int64_t t0, int64_t n, double* fx,
   uint8_t* chi = (uint8_t*)malloc(plane);
   double* us = (double*)malloc(sizeof(double) * 2 * plane);
   double* row_sum = (double*)malloc(sizeof(double) * 3 * (size_t)ny);
-  if (!g || !chi || !us || !row_sum) {
+  double* ghost = (double*)calloc(9 * (size_t)ny, sizeof(double));
+  if (!g || !chi || !us || !row_sum || !ghost) {
     free(g);
     free(chi);
     free(us);
     free(row_sum);
+    free(ghost);
     return 2;
   }
   orc_model m;
@@ -487,16 +514,18 @@ int orc_run(const orc_config* c, double* f, int64_t t0, int64_t n, double* fx,
 
   double* src = f;
   double* dst = g;
+  int rc = 0;
   for (int64_t s = 0; s < n; ++s) {
     int64_t t = t0 + s;
     orc_mask(c, t, chi, us);
+    if ((rc = outlet_advance(c, src, ghost)) != 0) break;
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y) {
       double sfx = 0.0, sfy = 0.0, smass = 0.0;
       for (int x = 0; x < nx; ++x) {
         size_t i = (size_t)y * nx + x;
         double fl[9], fo[9], px, py;
-        for (int a = 0; a < 9; ++a) fl[a] = pull_one(&m, c, src, a, x, y);
+        for (int a = 0; a < 9; ++a) fl[a] = pull_one(&m, c, src, ghost, a, x, y);
         for (int a = 0; a < 9; ++a) smass += fl[a];
         collide(&m, c, fl, chi[i], us[i], us[plane + i], fo, &px, &py);
         if (chi[i]) { /* reaction on the body: minus the penalization force */
@@ -518,6 +547,10 @@ int orc_run(const orc_config* c, double* f, int64_t t0, int64_t n, double* fx,
     if (fx) fx[s] = tfx;
     if (fy) fy[s] = tfy;
     if (mass) mass[s] = tm;
+    if (c->bc_x == ORC_BC_INLET_CONVECTIVE) /* the state moves on to g^t */
+      for (int k = 0; k < 3; ++k)
+        for (int y = 0; y < ny; ++y)
+          c->outlet[(size_t)k * ny + y] = ghost[(size_t)OUTLET_DIRS[k] * ny + y];
     double* tmp = src;
     src = dst;
     dst = tmp;
@@ -527,7 +560,8 @@ int orc_run(const orc_config* c, double* f, int64_t t0, int64_t n, double* fx,
   free(chi);
   free(us);
   free(row_sum);
-  return 0;
+  free(ghost);
+  return rc;
 }
 
 int orc_moments(const orc_config* c, const double* f, int64_t t, double* rho,
@@ -536,25 +570,34 @@ int orc_moments(const orc_config* c, const double* f, int64_t t, double* rho,
   const size_t plane = (size_t)nx * (size_t)ny;
   uint8_t* chi = (uint8_t*)malloc(plane);
   double* us = (double*)malloc(sizeof(double) * 2 * plane);
-  if (!chi || !us) {
+  double* ghost = (double*)calloc(9 * (size_t)ny, sizeof(double));
+  if (!chi || !us || !ghost) {
     free(chi);
     free(us);
+    free(ghost);
     return 2;
   }
   orc_model m;
   model_init(c, &m);
   orc_mask(c, t, chi, us);
+  if (outlet_advance(c, f, ghost) != 0) { /* the state itself is not advanced */
+    free(chi);
+    free(us);
+    free(ghost);
+    return 1;
+  }
   for (int y = 0; y < ny; ++y) {
     for (int x = 0; x < nx; ++x) {
       size_t i = (size_t)y * nx + x;
       double fl[9], px, py;
-      for (int a = 0; a < 9; ++a) fl[a] = pull_one(&m, c, f, a, x, y);
+      for (int a = 0; a < 9; ++a) fl[a] = pull_one(&m, c, f, ghost, a, x, y);
       node_macros(&m, c, fl, chi[i], us[i], us[plane + i], &rho[i], &ux[i], &uy[i],
                   &px, &py);
     }
   }
   free(chi);
   free(us);
+  free(ghost);
   return 0;
 }
 

@@ -21,7 +21,8 @@ extern "C" {
 #endif
 
 enum { ORC_SRT = 0, ORC_MRT = 1 };
-enum { ORC_BC_PERIODIC = 0, ORC_BC_INLET_OUTLET = 1, ORC_BC_FREE_SLIP = 2 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_INLET_OUTLET = 1, ORC_BC_FREE_SLIP = 2,
+       ORC_BC_INLET_CONVECTIVE = 3 };
 
 /* Rigid circular body. Centre(t) = (cx, cy) + (amp_x, amp_y) sin(2 pi t / period)
  * (period <= 0: fixed). Solid velocity: translation d centre/dt plus rigid
@@ -38,7 +39,7 @@ typedef struct {
 typedef struct {
   int32_t nx, ny;
   int32_t collision;        /* ORC_SRT | ORC_MRT */
-  int32_t bc_x;             /* ORC_BC_PERIODIC | ORC_BC_INLET_OUTLET */
+  int32_t bc_x;             /* ORC_BC_PERIODIC | ORC_BC_INLET_OUTLET | ORC_BC_INLET_CONVECTIVE */
   int32_t bc_y;             /* ORC_BC_PERIODIC | ORC_BC_FREE_SLIP */
   int32_t use_rates;        /* 1: take the nine MRT rates from rates[] */
   double tau;               /* SRT relaxation time; MRT s_n = 1/tau */
@@ -52,6 +53,15 @@ typedef struct {
   const orc_body* bodies;   /* rigid bodies, may be NULL */
   int32_t n_bodies;
   int32_t pad_;
+  /* Convective outlet (bc_x = ORC_BC_INLET_CONVECTIVE, Section 3.3 after
+   * Yang): the ghost column x = nx of the three directions entering through
+   * it (alpha = 3, 6, 7) carries its own state g, advanced once per step by
+   * the implicit upwind form of dg/dt + U_c dg/dx = 0,
+   *   g^t = (g^{t-1} + U_c f*_alpha(nx - 1, y; t)) / (1 + U_c),
+   * before the last column pulls g^t. outlet holds g^{t-1} as [3][ny] (rows of
+   * alpha = 3, 6, 7; values of f) and orc_run leaves g^{t+n-1} in it. */
+  double u_conv;
+  double* outlet;
 } orc_config;
 
 /* D2Q9 constants as the oracle derives them (for the pin tests). */

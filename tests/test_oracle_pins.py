@@ -580,3 +580,90 @@ def test_momentum_exchange_single_node_closed_form():
     # links from y = -1 leave the grid: only directions with xi_y <= 0 remain
     ex = sum(xi[a] * (feq_u[a] + feq_0[opp[a]]) for a in range(1, 9) if xi[a][1] <= 0)
     np.testing.assert_allclose(O.momentum_exchange(slip, fs, 0), ex, rtol=0, atol=1e-15)
+
+
+# -----------------------------------------------------------------------------
+# Convective outlet (Section 3.3, after Yang): ghost state advanced by the
+# implicit upwind form of dg/dt + U_c dg/dx = 0 before the last column pulls it.
+# -----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("bc_y", [O.BC_FREE_SLIP, O.BC_PERIODIC])
+def test_convective_outlet_fast_limit_is_zero_gradient(bc_y):
+    """U_c -> infinity: the ghost takes the last column's value at once, which
+    is the zero-gradient outlet (pinned by the channel tests)."""
+    nx, ny = 30, 17
+    chi = I.random_mask(nx, ny, 41, 0.1)
+    base = dict(nx=nx, ny=ny, collision=O.MRT, tau=0.6, bc_y=bc_y, u_in=(0.04, 0.0), chi=chi,
+                bodies=[O.Body(20.0, 8.0, 4.0, omega=0.003)])
+    f0 = I.random_populations(nx, ny, 42, 0.05)
+    f_zg = f0.copy()
+    fx_zg, fy_zg, m_zg = O.run(O.Config(bc_x=O.BC_INLET_OUTLET, **base), f_zg, 6)
+    f_cv = f0.copy()
+    cfg = O.Config(bc_x=O.BC_INLET_CONVECTIVE, u_conv=1e15, outlet=O.outlet_from_store(f0), **base)
+    fx_cv, fy_cv, m_cv = O.run(cfg, f_cv, 6)
+    assert np.abs(f_cv - f_zg).max() < 1e-13
+    np.testing.assert_allclose(m_cv, m_zg, rtol=1e-14)
+    np.testing.assert_allclose(fx_cv, fx_zg, rtol=0, atol=1e-13)
+    # the state left behind is the last column of the store before the last step
+    assert cfg.outlet.shape == (3, ny)
+
+
+def test_convective_outlet_uniform_flow_is_steady():
+    """A uniform equilibrium flow at the inlet velocity stays exactly uniform,
+    and the outlet state stays at the equilibrium values."""
+    nx, ny, U = 24, 10, 0.05
+    u = np.zeros((2, ny, nx))
+    u[0] = U
+    cfg0 = O.Config(nx=nx, ny=ny, tau=0.8, bc_x=O.BC_INLET_CONVECTIVE, bc_y=O.BC_FREE_SLIP,
+                    u_in=(U, 0.0))
+    f = O.init_equilibrium(cfg0, 1.0, u)
+    f_start = f.copy()
+    cfg = O.Config(nx=nx, ny=ny, tau=0.8, bc_x=O.BC_INLET_CONVECTIVE, bc_y=O.BC_FREE_SLIP,
+                   u_in=(U, 0.0), u_conv=U, outlet=O.outlet_from_store(f))
+    O.run(cfg, f, 25)
+    assert np.abs(f - f_start).max() < 1e-15
+    feq = O.equilibrium(1.0, U, 0.0)
+    np.testing.assert_allclose(cfg.outlet, np.repeat(feq[list(O.OUTLET_DIRS)][:, None], ny, 1),
+                               rtol=0, atol=1e-16)
+
+
+@pytest.mark.parametrize("bc_y", [O.BC_FREE_SLIP, O.BC_PERIODIC])
+def test_convective_outlet_ghost_rows_and_weight(bc_y):
+    """A change delta in one entry of the outlet state reaches exactly one
+    node of the last column, with weight 1/(1 + U_c) on its density: the
+    entry of direction 3 at row y feeds (nx-1, y); of direction 6 at row y,
+    (nx-1, y+1); of direction 7, (nx-1, y-1); at the top and bottom rows the
+    free-slip mirror (6 <-> 7 in the same row) or the periodic wrap decides."""
+    nx, ny, uc, delta = 12, 7, 0.05, 1e-3
+    f = I.random_populations(nx, ny, 43, 0.05)
+    base = dict(nx=nx, ny=ny, tau=0.7, bc_x=O.BC_INLET_CONVECTIVE, bc_y=bc_y,
+                u_in=(0.04, 0.0), u_conv=uc)
+    state = O.outlet_from_store(f) + 0.01 * I.random_populations(1, ny, 44, 1.0)[:3, :, 0]
+    rho0, _, _ = O.moments(O.Config(outlet=state.copy(), **base), f)
+    for k, a in enumerate(O.OUTLET_DIRS):
+        for y in (0, 3, ny - 1):
+            st = state.copy()
+            st[k, y] += delta
+            rho, _, _ = O.moments(O.Config(outlet=st, **base), f)
+            d = rho - rho0
+            if a == 3:
+                yy = y
+            elif a == 6:
+                yy = y + 1 if y + 1 < ny else (0 if bc_y == O.BC_PERIODIC else y)
+            else:
+                yy = y - 1 if y >= 1 else (ny - 1 if bc_y == O.BC_PERIODIC else y)
+            expect = np.zeros_like(d)
+            expect[yy, nx - 1] = delta / (1.0 + uc)
+            np.testing.assert_allclose(d, expect, rtol=0, atol=1e-15)
+
+
+def test_convective_outlet_frozen_when_uc_zero():
+    """U_c = 0: the ghost keeps its initial state (a fixed-population outlet)."""
+    nx, ny = 16, 9
+    f = I.random_populations(nx, ny, 45, 0.05)
+    state = O.outlet_from_store(f) * 1.01
+    cfg = O.Config(nx=nx, ny=ny, tau=0.7, bc_x=O.BC_INLET_CONVECTIVE, bc_y=O.BC_FREE_SLIP,
+                   u_in=(0.04, 0.0), u_conv=0.0, outlet=state)
+    keep = state.copy()
+    O.run(cfg, f, 4)
+    assert np.array_equal(cfg.outlet, keep)
