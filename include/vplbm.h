@@ -70,10 +70,18 @@ enum { VPLBM_ROUND_NEAREST = 0, VPLBM_ROUND_STOCHASTIC = 1 };
 /* Boundary conditions, applied inside the pull (streaming) of each step.
  * x: PERIODIC, or INLET_OUTLET: a ghost column x = -1 held at f_eq(1, u_in)
  *    (uniform velocity inlet) and a ghost column x = nx that repeats column
- *    nx - 1 (zero-gradient outlet).
+ *    nx - 1 (zero-gradient outlet), or INLET_CONVECTIVE: the same inlet and
+ *    the convective outlet of Section 3.3 (after Yang): the ghost column
+ *    x = nx of the three entering directions (3, 6, 7) keeps a state g,
+ *    advanced each step by the implicit upwind step of dg/dt + U_c dg/dx = 0,
+ *    g^t = (g^{t-1} + U_c f*(nx - 1; t)) / (1 + U_c), with U_c = u_conv;
+ *    it starts as a copy of the last column whenever the populations are set
+ *    (initial velocity, perturbation, vplbm_set_populations) and is part of
+ *    the checkpoint.
  * y: PERIODIC, or FREE_SLIP: specular reflection off walls half-way beyond
  *    rows 0 and ny - 1 (the symmetry planes of Section 3.3). */
-enum { VPLBM_BC_PERIODIC = 0, VPLBM_BC_INLET_OUTLET = 1, VPLBM_BC_FREE_SLIP = 2 };
+enum { VPLBM_BC_PERIODIC = 0, VPLBM_BC_INLET_OUTLET = 1, VPLBM_BC_FREE_SLIP = 2,
+       VPLBM_BC_INLET_CONVECTIVE = 3 };
 
 /* Largest number of rigid bodies a solver tracks. */
 #define VPLBM_MAX_BODIES 8
@@ -101,7 +109,7 @@ typedef struct {
   double tau;              /* relaxation time > 1/2; nu = (tau - 1/2)/3; MRT s_n = 1/tau */
   double lambda;           /* MRT: s_q from Lambda = (1/s_n - 1/2)(1/s_q - 1/2) */
   double eta;              /* penalization parameter, > 0 (paper: 1e-7) */
-  double u_in[2];          /* inlet velocity (bc_x = INLET_OUTLET) */
+  double u_in[2];          /* inlet velocity (bc_x = INLET_OUTLET or INLET_CONVECTIVE) */
   double rho0;             /* initial density */
   double u0[2];            /* initial uniform velocity */
   double body_force[2];    /* uniform force per unit mass g (f_tot = f_pen + rho g) */
@@ -109,6 +117,7 @@ typedef struct {
   int32_t force_ring_len;  /* steps of (F_x, F_y, mass) kept on the device; >= 1 */
   int32_t rounding;        /* VPLBM_ROUND_NEAREST | VPLBM_ROUND_STOCHASTIC (16-bit stores) */
   void* stream;            /* cudaStream_t to run on, or NULL for a private stream */
+  double u_conv;           /* convective outlet velocity U_c >= 0 (bc_x = INLET_CONVECTIVE) */
 } vplbm_config;
 
 typedef struct vplbm_solver vplbm_solver;
@@ -212,6 +221,34 @@ vplbm_status vplbm_forces(vplbm_solver* s, double* fx, double* fy, double* mass,
  * valid once the stream has reached this point (an event or a sync). */
 vplbm_status vplbm_forces_async(vplbm_solver* s, double* records, int64_t cap, int64_t* count);
 
+/* Momentum-exchange force on the solids (the force measure of Section 3.3,
+ * after Ladd), a second measure beside the penalization-force records of
+ * vplbm_forces. Over every link from a fluid node x_f to a solid node
+ * x_s = x_f + xi_a (mask nonzero), the momentum xi_a [f*_a(x_f) + f*_abar(x_s)]
+ * of the post-collision store f*(t) crosses into the solid; the force is the
+ * sum over links, in lattice units, summed in FP64 in a fixed order (results
+ * are bitwise reproducible). Links that would start outside a non-periodic
+ * side of the grid are not counted. The reduction covers the bounding box of
+ * the bodies at t and of the static mask layer, so its cost scales with the
+ * solids, not with the grid.
+ *
+ * vplbm_momentum_exchange computes it once at the current state (step index
+ * vplbm_step_count, the mask of that step) and synchronizes; fx, fy receive
+ * the two components (either may be NULL).
+ *
+ * vplbm_enable_momentum_exchange(s, 1) makes every later vplbm_step record
+ * it for its own step index t (from f*(t), before the step), one extra launch
+ * per step, into a ring of force_ring_len records; 0 stops recording. Solvers
+ * that record are stepped one by one inside vplbm_group_step.
+ * vplbm_momentum_exchange_forces returns the records of the steps since the
+ * previous read (or since recording began, up to where it stopped) like
+ * vplbm_forces: at most cap entries, oldest first, count in *count;
+ * VPLBM_ERR_STATE if recording was never enabled. */
+vplbm_status vplbm_momentum_exchange(vplbm_solver* s, double* fx, double* fy);
+vplbm_status vplbm_enable_momentum_exchange(vplbm_solver* s, int32_t enable);
+vplbm_status vplbm_momentum_exchange_forces(vplbm_solver* s, double* fx, double* fy,
+                                            int64_t cap, int64_t* count);
+
 /* Advances n solvers by steps[i] steps each, batching them into grouped
  * launches (one launch per time step per storage/collision class covering
  * every solver still running). All solvers must share one stream. Results
@@ -268,8 +305,9 @@ vplbm_status vplbm_fused_timing(vplbm_solver* s, double* total_ms, int64_t* laun
  * before launching. All calls share the one array, so calls whose kernels
  * can overlap on the GPU (different streams without ordering) race and give
  * wrong results: order them on one stream. Asynchronous on cfg->stream;
- * returns VPLBM_ERR_INVALID for bad arguments and VPLBM_ERR_CUDA if a CUDA
- * call fails. Calls no allocating routine. */
+ * returns VPLBM_ERR_INVALID for bad arguments (including the convective
+ * outlet, whose state lives in a solver) and VPLBM_ERR_CUDA if a CUDA call
+ * fails. Calls no allocating routine. */
 vplbm_status vplbm_step_noalloc(const vplbm_config* cfg, const vplbm_body* bodies,
                                 int32_t n_bodies, const void* f_src, void* f_dst,
                                 const uint8_t* mask, const void* us, int32_t pitch,

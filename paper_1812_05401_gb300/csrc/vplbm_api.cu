@@ -10,6 +10,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdlib>
 #include <cmath>
 #include <cstdio>
@@ -67,6 +68,26 @@ __global__ void mask_update_kernel(uint8_t* mask, int pitch, int x0, int y0, int
 
 // Static mask import: chi != 0 -> 255; a node that was statically solid and is
 // no longer becomes fluid (body nodes are then rebuilt by mask_update_kernel).
+// Bounding box of the nonzero mask nodes, into box {x0, y0, x1, y1} (which
+// holds {INT_MAX, INT_MAX, -1, -1} on entry).
+__global__ void solid_box_kernel(const uint8_t* mask, int pitch, int nx, int ny, int* box) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const bool solid = x < nx && y < ny && mask[(long long)y * pitch + x] != 0;
+  const unsigned any = __ballot_sync(0xffffffffu, solid);
+  if (!any) return;
+  const int lo_x = __reduce_min_sync(0xffffffffu, solid ? x : INT_MAX);
+  const int lo_y = __reduce_min_sync(0xffffffffu, solid ? y : INT_MAX);
+  const int hi_x = __reduce_max_sync(0xffffffffu, solid ? x : -1);
+  const int hi_y = __reduce_max_sync(0xffffffffu, solid ? y : -1);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(box + 0, lo_x);
+    atomicMin(box + 1, lo_y);
+    atomicMax(box + 2, hi_x);
+    atomicMax(box + 3, hi_y);
+  }
+}
+
 __global__ void mask_import_kernel(uint8_t* mask, int pitch, int nx, int ny, const uint8_t* chi) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -156,6 +177,9 @@ dim3 grid2d(int w, int h, dim3 blk) {
   return dim3((w + blk.x - 1) / blk.x, (h + blk.y - 1) / blk.y);
 }
 
+// Element of the convective outlet state: the arithmetic type.
+size_t ghost_elem(int storage) { return storage == kF64 ? sizeof(double) : sizeof(float); }
+
 size_t element_size(int storage) {
   switch (storage) {
     case kF64: return 8;
@@ -188,6 +212,16 @@ struct vplbm_solver {
   unsigned* counters = nullptr;
   double* ring = nullptr;
   int* flag = nullptr;
+  int* static_box = nullptr;  // device box {x0, y0, x1, y1} of the static solid layer
+  void* ghost[2] = {nullptr, nullptr};  // convective outlet state of f[0], f[1] ([3][ny])
+
+  // Momentum-exchange force (Section 3.3): records per step when enabled.
+  bool me_on = false;
+  double* me_ring = nullptr;     // [force_ring_len][2]
+  double* me_scratch = nullptr;  // [kMeBlocks][2] partials, then one on-demand result
+  unsigned* me_counter = nullptr;
+  int64_t me_read = 0;  // first step not yet returned by vplbm_momentum_exchange_forces
+  int64_t me_stop = 0;  // step at which recording last stopped
 
   int tiles_x = 0, tiles_y = 0, n_tiles = 0, n_groups = 0;
   StepParams base{};  // constants; src/dst/t/bodies filled per step
@@ -314,6 +348,31 @@ vplbm_status ensure_mask(vplbm_solver* s, int64_t t) {
   return VPLBM_OK;
 }
 
+// Resets the static solid layer's box to empty and recomputes it from the
+// mask as it stands (a superset is harmless: the reduction checks each node).
+const int kEmptyBox[4] = {INT_MAX, INT_MAX, -1, -1};
+vplbm_status update_static_box(vplbm_solver* s) {
+  VP_CUDA(s, cudaMemcpyAsync(s->static_box, kEmptyBox, sizeof(kEmptyBox), cudaMemcpyHostToDevice,
+                             s->stream));
+  const dim3 blk(64, 4);
+  solid_box_kernel<<<grid2d(s->cfg.nx, s->cfg.ny, blk), blk, 0, s->stream>>>(
+      s->mask, s->pitch, s->cfg.nx, s->cfg.ny, s->static_box);
+  VP_CUDA(s, cudaGetLastError());
+  return VPLBM_OK;
+}
+
+vplbm_status ensure_me_buffers(vplbm_solver* s) {
+  if (s->me_scratch) return VPLBM_OK;
+  const size_t L = size_t(s->cfg.force_ring_len);
+  VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&s->me_ring), 2 * sizeof(double) * L, s->stream));
+  VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&s->me_scratch),
+                             2 * sizeof(double) * (kMeBlocks + 1), s->stream));
+  VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&s->me_counter), sizeof(unsigned), s->stream));
+  VP_CUDA(s, cudaMemsetAsync(s->me_ring, 0, 2 * sizeof(double) * L, s->stream));
+  VP_CUDA(s, cudaMemsetAsync(s->me_counter, 0, sizeof(unsigned), s->stream));
+  return VPLBM_OK;
+}
+
 void fill_bodies(const vplbm_solver* s, int64_t t, StepParams* p) {
   p->n_bodies = int(s->bodies.size());
   for (int b = 0; b < p->n_bodies; ++b) {
@@ -344,6 +403,8 @@ void round_consts(StepParams* p) {
   f.gx = float(d.gx);
   f.gy = float(d.gy);
   for (int a = 0; a < 9; ++a) f.heq_in[a] = float(d.heq_in[a]);
+  f.u_conv = float(d.u_conv);
+  f.conv_inv = float(d.conv_inv);
 }
 
 StepParams step_params(const vplbm_solver* s, int64_t t, int parity) {
@@ -351,6 +412,8 @@ StepParams step_params(const vplbm_solver* s, int64_t t, int parity) {
   const int c = s->cur ^ parity;
   p.src = s->f[c];
   p.dst = s->f[c ^ 1];
+  p.ghost_src = s->ghost[c];
+  p.ghost_dst = s->ghost[c ^ 1];
   if (p.use_tma) p.tmap = s->tmap[c];
   p.t = t;
   fill_bodies(s, t, &p);
@@ -377,6 +440,21 @@ cudaError_t launch_group(int storage, const StepParams* dp, const GroupTile* dt,
   }
 }
 
+// Momentum exchange at step index t from the store f*(t) (p.src) into out:
+// the candidate box is the bodies' boxes at t, united on the device with the
+// static layer's box.
+cudaError_t launch_momentum_exchange(const vplbm_solver* s, const StepParams& p, double* out) {
+  Box box{0, 0, -1, -1};
+  for (const auto& b : s->bodies) box = unite(box, body_box(s, b, p.t));
+  MeArgs m{box.x0, box.y0, box.x1, box.y1, s->static_box, s->me_scratch, s->me_counter, out};
+  switch (s->cfg.storage) {
+    case kF64: return launch_momentum_exchange_f64(p, m, s->stream);
+    case kF32: return launch_momentum_exchange_f32(p, m, s->stream);
+    case kF16: return launch_momentum_exchange_f16(p, m, s->stream);
+    default: return launch_momentum_exchange_bf16(p, m, s->stream);
+  }
+}
+
 cudaError_t launch_moments(const vplbm_solver* s, const StepParams& p, double* r, double* ux, double* uy) {
   switch (s->cfg.storage) {
     case kF64: return launch_moments_f64(p, r, ux, uy, s->stream);
@@ -393,6 +471,15 @@ cudaError_t launch_init(const vplbm_solver* s, const StepParams& p, void* dst, c
     case kF32: return launch_init_f32(p, dst, u, r0, ux, uy, s->stream);
     case kF16: return launch_init_f16(p, dst, u, r0, ux, uy, s->stream);
     default: return launch_init_bf16(p, dst, u, r0, ux, uy, s->stream);
+  }
+}
+
+cudaError_t launch_ghost_init(const vplbm_solver* s, const StepParams& p, const void* src, void* g) {
+  switch (s->cfg.storage) {
+    case kF64: return launch_ghost_init_f64(p, src, g, s->stream);
+    case kF32: return launch_ghost_init_f32(p, src, g, s->stream);
+    case kF16: return launch_ghost_init_f16(p, src, g, s->stream);
+    default: return launch_ghost_init_bf16(p, src, g, s->stream);
   }
 }
 
@@ -422,8 +509,11 @@ vplbm_status validate(const vplbm_config* c, std::string* why) {
     return *why = "unknown collision", VPLBM_ERR_INVALID;
   if (c->storage < VPLBM_F64 || c->storage > VPLBM_BF16_OFFSET)
     return *why = "unknown storage", VPLBM_ERR_INVALID;
-  if (c->bc_x != VPLBM_BC_PERIODIC && c->bc_x != VPLBM_BC_INLET_OUTLET)
-    return *why = "bc_x must be PERIODIC or INLET_OUTLET", VPLBM_ERR_INVALID;
+  if (c->bc_x != VPLBM_BC_PERIODIC && c->bc_x != VPLBM_BC_INLET_OUTLET &&
+      c->bc_x != VPLBM_BC_INLET_CONVECTIVE)
+    return *why = "bc_x must be PERIODIC, INLET_OUTLET or INLET_CONVECTIVE", VPLBM_ERR_INVALID;
+  if (c->bc_x == VPLBM_BC_INLET_CONVECTIVE && !(c->u_conv >= 0.0 && std::isfinite(c->u_conv)))
+    return *why = "u_conv must be finite and >= 0", VPLBM_ERR_INVALID;
   if (c->bc_y != VPLBM_BC_PERIODIC && c->bc_y != VPLBM_BC_FREE_SLIP)
     return *why = "bc_y must be PERIODIC or FREE_SLIP", VPLBM_ERR_INVALID;
   if (!(c->tau > 0.5) || !std::isfinite(c->tau)) return *why = "tau must be > 1/2", VPLBM_ERR_INVALID;
@@ -506,6 +596,7 @@ void vplbm_config_init(vplbm_config* c) {
   c->rho0 = 1.0;
   c->force_ring_len = 4096;
   c->rounding = VPLBM_ROUND_STOCHASTIC;
+  c->u_conv = 0.0;
 }
 
 double vplbm_tau_from_reynolds(double u_ref, double l_ref, double re) {
@@ -525,6 +616,7 @@ size_t vplbm_footprint_bytes(const vplbm_config* c) {
   b += 3 * sizeof(double) * (size_t(nt) + size_t(ng));   // reduction partials
   b += sizeof(unsigned) * (size_t(ng) + 1);
   b += 3 * sizeof(double) * size_t(c->force_ring_len);
+  if (c->bc_x == VPLBM_BC_INLET_CONVECTIVE) b += 2 * 3 * size_t(c->ny) * ghost_elem(c->storage);
   return b;
 }
 
@@ -570,16 +662,25 @@ vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
       (e = cudaMallocAsync(reinterpret_cast<void**>(&s->group_partials), 3 * sizeof(double) * s->n_groups, st0)) != cudaSuccess ||
       (e = cudaMallocAsync(reinterpret_cast<void**>(&s->counters), sizeof(unsigned) * (s->n_groups + 1), st0)) != cudaSuccess ||
       (e = cudaMallocAsync(reinterpret_cast<void**>(&s->ring), 3 * sizeof(double) * cfg->force_ring_len, st0)) != cudaSuccess ||
-      (e = cudaMallocAsync(reinterpret_cast<void**>(&s->flag), sizeof(int), st0)) != cudaSuccess) {
+      (e = cudaMallocAsync(reinterpret_cast<void**>(&s->flag), sizeof(int), st0)) != cudaSuccess ||
+      (e = cudaMallocAsync(reinterpret_cast<void**>(&s->static_box), sizeof(kEmptyBox), st0)) != cudaSuccess) {
     return bail(cuda_fail(s, e, "cudaMallocAsync"));
   }
   if ((e = cudaMemsetAsync(s->mask, 0, size_t(s->plane), s->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(s->counters, 0, sizeof(unsigned) * (s->n_groups + 1), s->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(s->ring, 0, 3 * sizeof(double) * cfg->force_ring_len, s->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(s->static_box, kEmptyBox, sizeof(kEmptyBox), cudaMemcpyHostToDevice,
+                           s->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(s->f[0], 0, pop, s->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(s->f[1], 0, pop, s->stream)) != cudaSuccess) {
     return bail(cuda_fail(s, e, "cudaMemsetAsync"));
+  }
+  if (cfg->bc_x == VPLBM_BC_INLET_CONVECTIVE) {
+    const size_t gb = 3 * size_t(cfg->ny) * ghost_elem(cfg->storage);
+    if ((e = cudaMallocAsync(&s->ghost[0], gb, st0)) != cudaSuccess ||
+        (e = cudaMallocAsync(&s->ghost[1], gb, st0)) != cudaSuccess)
+      return bail(cuda_fail(s, e, "cudaMallocAsync"));
   }
 
   StepParams& p = s->base;
@@ -621,6 +722,8 @@ vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
   cd.gx = cfg->body_force[0];
   cd.gy = cfg->body_force[1];
   heq_host(1.0, cfg->u_in[0], cfg->u_in[1], cd.heq_in);
+  cd.u_conv = cfg->u_conv;
+  cd.conv_inv = 1.0 / (1.0 + cfg->u_conv);
   round_consts(&p);
   p.partials = s->partials;
   p.group_partials = s->group_partials;
@@ -661,9 +764,12 @@ vplbm_status vplbm_set_initial_velocity(vplbm_solver* s, const double* u) {
   }
   s->cur = 0;
   VP_CUDA(s, launch_init(s, s->base, s->f[0], du));
+  if (s->ghost[0]) VP_CUDA(s, launch_ghost_init(s, s->base, s->f[0], s->ghost[0]));
   if (du) VP_CUDA(s, cudaFreeAsync(du, s->stream));
   s->t = 0;
   s->ring_read = 0;
+  s->me_read = 0;
+  s->me_stop = 0;
   VP_CUDA(s, cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream));
   VP_CUDA(s, cudaMemsetAsync(s->ring, 0, 3 * sizeof(double) * s->cfg.force_ring_len, s->stream));
   if (s->moving) s->mask_t = -1;
@@ -694,6 +800,7 @@ vplbm_status vplbm_set_mask_and_solid_velocity(vplbm_solver* s, const uint8_t* c
   const dim3 blk(64, 4);
   mask_import_kernel<<<grid2d(nx, ny, blk), blk, 0, s->stream>>>(s->mask, s->pitch, nx, ny, dchi);
   VP_CUDA(s, cudaGetLastError());
+  if ((st = update_static_box(s)) != VPLBM_OK) return st;
   if (dus) {
     const size_t vs = s->cfg.storage == kF64 ? sizeof(double2) : sizeof(float2);
     if (!s->us) VP_CUDA(s, cudaMallocAsync(&s->us, vs * size_t(s->plane), s->stream));
@@ -745,6 +852,10 @@ vplbm_status vplbm_step(vplbm_solver* s, int64_t n) {
   for (int64_t k = 0; k < n; ++k) {
     if ((st = ensure_mask(s, s->t)) != VPLBM_OK) return st;
     const StepParams p = step_params(s, s->t, 0);
+    if (s->me_on) {
+      VP_CUDA(s, launch_momentum_exchange(s, p, s->me_ring + 2 * (s->t % s->cfg.force_ring_len)));
+      s->launches++;
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (s->timing) {
       if ((st = get_event(s, &e0)) != VPLBM_OK) return st;
@@ -827,13 +938,15 @@ vplbm_status vplbm_set_populations(vplbm_solver* s, const double* f, int32_t on_
   const size_t n = size_t(s->cfg.nx) * s->cfg.ny;
   if (on_device) {
     VP_CUDA(s, launch_import(s, s->base, s->f[s->cur], f));
-    return VPLBM_OK;
+  } else {
+    double* d = nullptr;
+    VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&d), 9 * n * sizeof(double), s->stream));
+    VP_CUDA(s, cudaMemcpyAsync(d, f, 9 * n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    VP_CUDA(s, launch_import(s, s->base, s->f[s->cur], d));
+    VP_CUDA(s, cudaFreeAsync(d, s->stream));
   }
-  double* d = nullptr;
-  VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&d), 9 * n * sizeof(double), s->stream));
-  VP_CUDA(s, cudaMemcpyAsync(d, f, 9 * n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-  VP_CUDA(s, launch_import(s, s->base, s->f[s->cur], d));
-  VP_CUDA(s, cudaFreeAsync(d, s->stream));
+  // the convective outlet restarts from a zero-gradient copy of the new store
+  if (s->ghost[0]) VP_CUDA(s, launch_ghost_init(s, s->base, s->f[s->cur], s->ghost[s->cur]));
   return VPLBM_OK;
 }
 
@@ -894,18 +1007,24 @@ struct StateHeader {
   int32_t nx, ny, pitch, storage, collision, has_us;
   int64_t t;
   uint64_t pop_bytes, mask_bytes, us_bytes;
+  uint64_t ghost_bytes;  // convective outlet state, 0 for other outlets
 };
-constexpr uint64_t kStateMagic = 0x56504c424d535431ull;  // "VPLBMST1"
+constexpr uint64_t kStateMagic = 0x56504c424d535432ull;  // "VPLBMST2"
 
 size_t us_bytes(const vplbm_solver* s) {
   if (!s->us) return 0;
   return (s->cfg.storage == kF64 ? sizeof(double2) : sizeof(float2)) * size_t(s->plane);
 }
+
+size_t ghost_bytes(const vplbm_solver* s) {
+  return s->ghost[0] ? 3 * size_t(s->cfg.ny) * ghost_elem(s->cfg.storage) : 0;
+}
 }  // namespace
 
 size_t vplbm_state_bytes(const vplbm_solver* s) {
   if (!s) return 0;
-  return sizeof(StateHeader) + 9 * size_t(s->plane) * s->esize + size_t(s->plane) + us_bytes(s);
+  return sizeof(StateHeader) + 9 * size_t(s->plane) * s->esize + size_t(s->plane) + us_bytes(s) +
+         ghost_bytes(s);
 }
 
 vplbm_status vplbm_save_state(vplbm_solver* s, void* buf) {
@@ -925,6 +1044,7 @@ vplbm_status vplbm_save_state(vplbm_solver* s, void* buf) {
   h.pop_bytes = 9 * uint64_t(s->plane) * s->esize;
   h.mask_bytes = uint64_t(s->plane);
   h.us_bytes = us_bytes(s);
+  h.ghost_bytes = ghost_bytes(s);
   char* out = static_cast<char*>(buf);
   std::memcpy(out, &h, sizeof(h));
   out += sizeof(h);
@@ -934,6 +1054,10 @@ vplbm_status vplbm_save_state(vplbm_solver* s, void* buf) {
   out += h.mask_bytes;
   if (h.us_bytes)
     VP_CUDA(s, cudaMemcpyAsync(out, s->us, h.us_bytes, cudaMemcpyDeviceToHost, s->stream));
+  out += h.us_bytes;
+  if (h.ghost_bytes)
+    VP_CUDA(s, cudaMemcpyAsync(out, s->ghost[s->cur], h.ghost_bytes, cudaMemcpyDeviceToHost,
+                               s->stream));
   VP_CUDA(s, cudaStreamSynchronize(s->stream));
   return VPLBM_OK;
 }
@@ -946,7 +1070,7 @@ vplbm_status vplbm_load_state(vplbm_solver* s, const void* buf) {
   std::memcpy(&h, buf, sizeof(h));
   if (h.magic != kStateMagic || h.nx != s->cfg.nx || h.ny != s->cfg.ny || h.pitch != s->pitch ||
       h.storage != s->cfg.storage || h.pop_bytes != 9 * uint64_t(s->plane) * s->esize ||
-      h.mask_bytes != uint64_t(s->plane) || h.t < 0)
+      h.mask_bytes != uint64_t(s->plane) || h.t < 0 || h.ghost_bytes != ghost_bytes(s))
     return fail(s, VPLBM_ERR_INVALID, "state does not match this solver's grid and storage");
   const char* in = static_cast<const char*>(buf) + sizeof(h);
   VP_CUDA(s, cudaMemcpyAsync(s->f[s->cur], in, h.pop_bytes, cudaMemcpyHostToDevice, s->stream));
@@ -960,11 +1084,18 @@ vplbm_status vplbm_load_state(vplbm_solver* s, const void* buf) {
     if (!s->us) VP_CUDA(s, cudaMallocAsync(&s->us, h.us_bytes, s->stream));
     VP_CUDA(s, cudaMemcpyAsync(s->us, in, h.us_bytes, cudaMemcpyHostToDevice, s->stream));
     s->base.us = s->us;
+    in += h.us_bytes;
   }
+  if (h.ghost_bytes)
+    VP_CUDA(s, cudaMemcpyAsync(s->ghost[s->cur], in, h.ghost_bytes, cudaMemcpyHostToDevice,
+                               s->stream));
   // pageable host-to-device copies have been staged when they return
   s->t = h.t;
   s->ring_read = h.t;
+  s->me_read = h.t;
+  s->me_stop = h.t;
   s->mask_t = s->moving ? h.t : -1;
+  if ((st = update_static_box(s)) != VPLBM_OK) return st;
   return VPLBM_OK;
 }
 
@@ -989,6 +1120,63 @@ vplbm_status vplbm_forces_async(vplbm_solver* s, double* records, int64_t cap, i
   return VPLBM_OK;
 }
 
+vplbm_status vplbm_enable_momentum_exchange(vplbm_solver* s, int32_t enable) {
+  vplbm_status st = check_usable(s);
+  if (st != VPLBM_OK) return st;
+  if (enable && !s->me_on) {
+    if ((st = ensure_me_buffers(s)) != VPLBM_OK) return st;
+    s->me_read = s->t;
+  }
+  if (!enable && s->me_on) s->me_stop = s->t;
+  s->me_on = enable != 0;
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_momentum_exchange(vplbm_solver* s, double* fx, double* fy) {
+  vplbm_status st = check_usable(s);
+  if (st != VPLBM_OK) return st;
+  if ((st = ensure_me_buffers(s)) != VPLBM_OK) return st;
+  if ((st = ensure_mask(s, s->t)) != VPLBM_OK) return st;
+  double* out = s->me_scratch + 2 * kMeBlocks;
+  VP_CUDA(s, launch_momentum_exchange(s, step_params(s, s->t, 0), out));
+  double host[2];
+  VP_CUDA(s, cudaMemcpyAsync(host, out, sizeof(host), cudaMemcpyDeviceToHost, s->stream));
+  VP_CUDA(s, cudaStreamSynchronize(s->stream));
+  if (fx) *fx = host[0];
+  if (fy) *fy = host[1];
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_momentum_exchange_forces(vplbm_solver* s, double* fx, double* fy, int64_t cap,
+                                            int64_t* count) {
+  vplbm_status st = check_usable(s);
+  if (st != VPLBM_OK) return st;
+  if (count) *count = 0;
+  if (cap < 0) return fail(s, VPLBM_ERR_INVALID, "cap must be >= 0");
+  if (!s->me_ring) return fail(s, VPLBM_ERR_STATE, "momentum exchange was never enabled");
+  const int64_t L = s->cfg.force_ring_len;
+  const int64_t end = s->me_on ? s->t : std::max(s->me_stop, s->me_read);  // steps recorded
+  const int64_t k = std::min(std::min(end - s->me_read, L), cap);
+  std::vector<double> host(2 * size_t(std::max<int64_t>(k, 1)));
+  int64_t done = 0;
+  while (done < k) {
+    const int64_t step = end - k + done;
+    const int64_t slot = step % L;
+    const int64_t run = std::min(k - done, L - slot);
+    VP_CUDA(s, cudaMemcpyAsync(host.data() + 2 * done, s->me_ring + 2 * slot, 2 * sizeof(double) * run,
+                               cudaMemcpyDeviceToHost, s->stream));
+    done += run;
+  }
+  VP_CUDA(s, cudaStreamSynchronize(s->stream));
+  for (int64_t i = 0; i < k; ++i) {
+    if (fx) fx[i] = host[2 * i + 0];
+    if (fy) fy[i] = host[2 * i + 1];
+  }
+  if (count) *count = k;
+  s->me_read = end;
+  return VPLBM_OK;
+}
+
 vplbm_status vplbm_set_initial_perturbation(vplbm_solver* s, double u0x, double u0y, double amp,
                                             uint64_t seed) {
   vplbm_status st = check_usable(s);
@@ -1004,9 +1192,12 @@ vplbm_status vplbm_set_initial_perturbation(vplbm_solver* s, double u0x, double 
   VP_CUDA(s, cudaGetLastError());
   s->cur = 0;
   VP_CUDA(s, launch_init(s, s->base, s->f[0], du));
+  if (s->ghost[0]) VP_CUDA(s, launch_ghost_init(s, s->base, s->f[0], s->ghost[0]));
   VP_CUDA(s, cudaFreeAsync(du, s->stream));
   s->t = 0;
   s->ring_read = 0;
+  s->me_read = 0;
+  s->me_stop = 0;
   VP_CUDA(s, cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream));
   VP_CUDA(s, cudaMemsetAsync(s->ring, 0, 3 * sizeof(double) * s->cfg.force_ring_len, s->stream));
   if (s->moving) s->mask_t = -1;
@@ -1029,7 +1220,8 @@ vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int
     max_steps = std::max(max_steps, steps[i]);
   }
   vplbm_solver* s0 = solvers[0];
-  // Solvers with moving bodies need a mask update between steps: step them
+  // Solvers with moving bodies need a mask update between steps, and those
+  // recording the momentum exchange a reduction before each step: step them
   // alone, interleaved with the grouped launches of the others.
   struct Member {
     int idx;
@@ -1038,7 +1230,7 @@ vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int
   std::vector<Member> classes[4];  // one grouped launch per storage type and step
   std::vector<int> moving;
   for (int i = 0; i < n; ++i) {
-    if (solvers[i]->moving) {
+    if (solvers[i]->moving || solvers[i]->me_on) {
       moving.push_back(i);
       continue;
     }
@@ -1103,7 +1295,7 @@ vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int
   }
   for (int i = 0; i < n; ++i) {
     vplbm_solver* s = solvers[i];
-    if (s->moving) continue;
+    if (s->moving || s->me_on) continue;
     s->launches += steps[i];  // one grouped launch per step covers this solver
     s->cur ^= int(steps[i] & 1);
     s->t += steps[i];
@@ -1160,7 +1352,8 @@ void vplbm_destroy(vplbm_solver* s) {
   for (auto e : s->ev_pool) cudaEventDestroy(e);
   if (s->stream) {
     void* bufs[] = {s->f[0], s->f[1], s->mask, s->us, s->partials, s->group_partials,
-                    s->counters, s->ring, s->flag};
+                    s->counters, s->ring, s->flag, s->static_box, s->me_ring,
+                    s->me_scratch, s->me_counter, s->ghost[0], s->ghost[1]};
     for (void* b : bufs)
       if (b) cudaFreeAsync(b, s->stream);
     if (s->own_stream) cudaStreamDestroy(s->stream);
@@ -1226,6 +1419,11 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_config* cfg, const vplbm_
   }
   if (pitch < cfg->nx || pitch % 8 != 0) {
     std::fprintf(stderr, "vplbm_step_noalloc: pitch must be >= nx and a multiple of 8\n");
+    return VPLBM_ERR_INVALID;
+  }
+  if (cfg->bc_x == VPLBM_BC_INLET_CONVECTIVE) {
+    std::fprintf(stderr, "vplbm_step_noalloc: the convective outlet keeps state between steps "
+                         "(use vplbm_create / vplbm_step)\n");
     return VPLBM_ERR_INVALID;
   }
   int tx, ty, nt, ng;
@@ -1308,6 +1506,8 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_config* cfg, const vplbm_
   cd.gx = cfg->body_force[0];
   cd.gy = cfg->body_force[1];
   heq_host(1.0, cfg->u_in[0], cfg->u_in[1], cd.heq_in);
+  cd.u_conv = cfg->u_conv;
+  cd.conv_inv = 1.0 / (1.0 + cfg->u_conv);
   round_consts(&p);
   p.n_bodies = n_bodies;
   for (int b = 0; b < n_bodies; ++b) {

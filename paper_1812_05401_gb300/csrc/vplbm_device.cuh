@@ -33,6 +33,10 @@ __device__ __host__ constexpr int cy(int a) {
 __device__ __host__ constexpr int mirror_y(int a) {
   return a == 2 ? 4 : a == 4 ? 2 : a == 5 ? 8 : a == 8 ? 5 : a == 6 ? 7 : a == 7 ? 6 : a;
 }
+// Direction with the opposite velocity.
+__device__ __host__ constexpr int opposite(int a) {
+  return a == 0 ? 0 : (a <= 4 ? (a + 1) % 4 + 1 : (a - 3) % 4 + 5);
+}
 // Weights, Eq. anex_eq19.
 template <class T>
 __device__ __forceinline__ constexpr T wgt(int a) {
@@ -252,6 +256,24 @@ __device__ __forceinline__ unsigned round_bits(unsigned counter, unsigned key) {
 
 
 
+// Convective outlet (Section 3.3, after Yang): the ghost column x = nx of
+// direction as (3, 6 or 7), row ys, advanced by the implicit upwind step of
+// dg/dt + U_c dg/dx = 0 from the last column's f*(t):
+// g^t = (g^{t-1} + U_c f*(nx - 1)) / (1 + U_c), in offsets (the weights cancel).
+// The step's one reader of each entry writes g^t to ghost_dst (write = true).
+template <class S>
+__device__ __forceinline__ typename S::T outlet_ghost(const StepParams& p,
+                                                      const typename S::E* src, int as, int ys,
+                                                      bool write) {
+  using T = typename S::T;
+  const Consts<T>& c = consts<T>(p);
+  const long long gi = (long long)(as == 3 ? 0 : (as == 6 ? 1 : 2)) * p.ny + ys;
+  const T f_last = load_h<S>(src + (long long)as * p.plane + (long long)ys * p.pitch + (p.nx - 1), as);
+  const T g = (static_cast<const T*>(p.ghost_src)[gi] + c.u_conv * f_last) * c.conv_inv;
+  if (write) static_cast<T*>(p.ghost_dst)[gi] = g;
+  return g;
+}
+
 // ---------------------------------------------------------------------------
 // Pull with boundary conditions (streaming, left-hand side of Eq. LatticeBoltz)
 // ---------------------------------------------------------------------------
@@ -276,6 +298,8 @@ __device__ __forceinline__ typename S::T pull_bc(const StepParams& p, const type
     } else if (xs < 0) {  // inlet ghost column at f_eq(1, u_in)
       const Consts<T>& c = consts<T>(p);
       return as == A ? c.heq_in[A] : c.heq_in[mirror_y(A)];
+    } else if (p.bc_x == kBcInletConvective) {  // read only: the step writes the state
+      return outlet_ghost<S>(p, src, as, ys, false);
     } else {  // zero-gradient outlet ghost column
       xs = p.nx - 1;
     }
@@ -609,6 +633,10 @@ __device__ __forceinline__ typename S::T edge_pull(const StepParams& p, const ty
     } else if (xs < 0) {  // inlet ghost column at f_eq(1, u_in)
       const Consts<typename S::T>& c = consts<typename S::T>(p);
       return as == A ? c.heq_in[A] : c.heq_in[mirror_y(A)];
+    } else if (p.bc_x == kBcInletConvective) {
+      // xs == nx: the last column's own pull (the entry's one reader); beyond
+      // it, the unused edge value of a lane past the last column
+      return outlet_ghost<S>(p, src, as, ys, xs == p.nx);
     } else {  // zero-gradient outlet ghost column
       xs = p.nx - 1;
     }
@@ -1008,6 +1036,89 @@ __global__ void moments_kernel(const __grid_constant__ StepParams p, double* rho
   uy[o] = double(q.uy);
 }
 
+// ---------------------------------------------------------------------------
+// Momentum exchange (Section 3.3, after Ladd). Over every link from a fluid
+// node x_f to a solid node x_s = x_f + xi_a the momentum
+// xi_a [f*_a(x_f) + f*_abar(x_s)] of the store f*(t) crosses into the solid.
+// Threads take the solid nodes of the box and look back along each direction
+// for a fluid node; a link whose start lies outside a non-periodic side does
+// not exist. The grid is fixed (kMeBlocks) and each thread walks its nodes
+// grid-stride, so the share of each thread depends on the box alone; sums are
+// FP64 in fixed order (thread, warp, block, then the last block to finish
+// adds the block partials in block order).
+// ---------------------------------------------------------------------------
+template <int STORE>
+__global__ void __launch_bounds__(kThreads)
+    momentum_exchange_kernel(const __grid_constant__ StepParams p, const MeArgs m) {
+  using S = Store<STORE>;
+  using E = typename S::E;
+  __shared__ double sm[kThreads / 32][3];
+  __shared__ int s_last;
+  const E* src = static_cast<const E*>(p.src);
+  int x0 = m.x0, y0 = m.y0, x1 = m.x1, y1 = m.y1;
+  {
+    const int sx0 = m.static_box[0], sy0 = m.static_box[1];
+    const int sx1 = m.static_box[2], sy1 = m.static_box[3];
+    if (sx1 >= sx0 && sy1 >= sy0) {
+      if (x1 < x0 || y1 < y0) {
+        x0 = sx0, y0 = sy0, x1 = sx1, y1 = sy1;
+      } else {
+        x0 = min(x0, sx0), y0 = min(y0, sy0), x1 = max(x1, sx1), y1 = max(y1, sy1);
+      }
+    }
+  }
+  double fx = 0.0, fy = 0.0;
+  if (x1 >= x0 && y1 >= y0) {
+    const int w = x1 - x0 + 1;
+    const long long n = (long long)w * (y1 - y0 + 1);
+    for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n;
+         i += (long long)gridDim.x * kThreads) {
+      const int x = x0 + int(i % w), y = y0 + int(i / w);
+      if (p.mask[(long long)y * p.pitch + x] == 0) continue;
+#pragma unroll
+      for (int a = 1; a < 9; ++a) {
+        int xf = x - cx(a), yf = y - cy(a);
+        if (xf < 0 || xf >= p.nx) {
+          if (p.bc_x != kBcPeriodic) continue;
+          xf = xf < 0 ? xf + p.nx : xf - p.nx;
+        }
+        if (yf < 0 || yf >= p.ny) {
+          if (p.bc_y != kBcPeriodic) continue;
+          yf = yf < 0 ? yf + p.ny : yf - p.ny;
+        }
+        if (p.mask[(long long)yf * p.pitch + xf] != 0) continue;
+        const int o = opposite(a);
+        const double flow = S::to_f64(src + a * p.plane + (long long)yf * p.pitch + xf, a) +
+                            S::to_f64(src + o * p.plane + (long long)y * p.pitch + x, o);
+        fx += double(cx(a)) * flow;
+        fy += double(cy(a)) * flow;
+      }
+    }
+  }
+  double v[3] = {fx, fy, 0.0};
+  block_sum3(v, sm);
+  if (threadIdx.x == 0) {
+    __stcg(m.partials + 2 * blockIdx.x + 0, v[0]);
+    __stcg(m.partials + 2 * blockIdx.x + 1, v[1]);
+    __threadfence();
+    s_last = atomicAdd(m.counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double u[3] = {0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += kThreads) {
+    u[0] += __ldcg(m.partials + 2 * b + 0);
+    u[1] += __ldcg(m.partials + 2 * b + 1);
+  }
+  block_sum3(u, sm);
+  if (threadIdx.x == 0) {
+    m.out[0] = u[0];
+    m.out[1] = u[1];
+    *m.counter = 0u;
+  }
+}
+
 // f*(t) := f_eq(rho0, u(x)), u from a device [2][ny][nx] array or uniform.
 template <int STORE>
 __global__ void init_kernel(const __grid_constant__ StepParams p, void* dst, const double* u,
@@ -1030,6 +1141,20 @@ __global__ void init_kernel(const __grid_constant__ StepParams p, void* dst, con
     const T heq = wgt<T>(a) * (common + rho * xu * (T(3) + T(4.5) * xu));
     store_h<S>(d + (long long)a * p.plane + i, heq, a);
   }
+}
+
+// Convective outlet state g := the offsets of the last column of the store
+// (a zero-gradient start), [3][ny] rows alpha = 3, 6, 7.
+template <int STORE>
+__global__ void ghost_init_kernel(const __grid_constant__ StepParams p, const void* srcv, void* ghostv) {
+  using S = Store<STORE>;
+  using T = typename S::T;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * p.ny) return;
+  const int k = i / p.ny, y = i - k * p.ny;
+  const int a = k == 0 ? 3 : (k == 1 ? 6 : 7);
+  const typename S::E* src = static_cast<const typename S::E*>(srcv);
+  static_cast<T*>(ghostv)[i] = load_h<S>(src + (long long)a * p.plane + (long long)y * p.pitch + (p.nx - 1), a);
 }
 
 // Store <-> dense FP64 [9][ny][nx].

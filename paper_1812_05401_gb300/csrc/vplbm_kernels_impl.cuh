@@ -56,9 +56,20 @@ cudaError_t VPLBM_FN(launch_moments_)(const StepParams& p, double* rho, double* 
   return cudaGetLastError();
 }
 
+cudaError_t VPLBM_FN(launch_momentum_exchange_)(const StepParams& p, const MeArgs& m, cudaStream_t st) {
+  momentum_exchange_kernel<VPLBM_STORE><<<kMeBlocks, kThreads, 0, st>>>(p, m);
+  return cudaGetLastError();
+}
+
 cudaError_t VPLBM_FN(launch_init_)(const StepParams& p, void* dst, const double* u, double rho0,
                                    double u0x, double u0y, cudaStream_t st) {
   init_kernel<VPLBM_STORE><<<node_grid(p), dim3(kBlockX, kBlockY), 0, st>>>(p, dst, u, rho0, u0x, u0y);
+  return cudaGetLastError();
+}
+
+cudaError_t VPLBM_FN(launch_ghost_init_)(const StepParams& p, const void* src, void* ghost,
+                                         cudaStream_t st) {
+  ghost_init_kernel<VPLBM_STORE><<<(3 * p.ny + 255) / 256, 256, 0, st>>>(p, src, ghost);
   return cudaGetLastError();
 }
 

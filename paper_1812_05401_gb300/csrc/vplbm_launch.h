@@ -14,8 +14,12 @@ namespace vplbm {
                                     cudaStream_t st);                                           \
   cudaError_t launch_moments_##SUFFIX(const StepParams& p, double* rho, double* ux, double* uy, \
                                       cudaStream_t st);                                         \
+  cudaError_t launch_momentum_exchange_##SUFFIX(const StepParams& p, const MeArgs& m,            \
+                                                cudaStream_t st);                               \
   cudaError_t launch_init_##SUFFIX(const StepParams& p, void* dst, const double* u, double rho0, \
                                    double u0x, double u0y, cudaStream_t st);                    \
+  cudaError_t launch_ghost_init_##SUFFIX(const StepParams& p, const void* src, void* ghost,     \
+                                        cudaStream_t st);                                       \
   cudaError_t launch_export_##SUFFIX(const StepParams& p, const void* src, double* f,           \
                                      cudaStream_t st);                                          \
   cudaError_t launch_import_##SUFFIX(const StepParams& p, void* dst, const double* f,           \

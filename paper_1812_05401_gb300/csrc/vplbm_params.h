@@ -9,7 +9,7 @@ namespace vplbm {
 
 enum { kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
 enum { kSrt = 0, kMrt = 1 };
-enum { kBcPeriodic = 0, kBcInletOutlet = 1, kBcFreeSlip = 2 };
+enum { kBcPeriodic = 0, kBcInletOutlet = 1, kBcFreeSlip = 2, kBcInletConvective = 3 };
 
 constexpr int kMaxBodies = 8;
 // Fused-step tiles: a block is 8 warps; each warp covers one row segment of
@@ -37,6 +37,7 @@ __host__ __device__ constexpr int tile_x(int storage) { return kLanes * npt(stor
 constexpr int kBlockX = 64;
 constexpr int kBlockY = 4;
 constexpr int kGroup = 256;             // tiles per first-level reduction group
+constexpr int kMeBlocks = 304;          // fixed grid of the momentum-exchange reduction (2 per SM)
 constexpr uint8_t kStaticSolid = 255;   // mask value of a node solid through the static mask
 
 // State of one rigid body at the time of a step.
@@ -54,6 +55,7 @@ struct Consts {
   T a_s, kappa_s;                         // 1/(2 eta) and (1/eta)/(1 + 1/(2 eta))
   T gx, gy;                               // body force per unit mass
   T heq_in[9];                            // inlet ghost f_eq(1, u_in) - w
+  T u_conv, conv_inv;                     // convective outlet: U_c and 1/(1 + U_c)
   T body[kMaxBodies][5];                  // cx, cy, vx, vy, omega of each body
 };
 
@@ -64,6 +66,8 @@ struct StepParams {
   void* dst;                // f*(t+1)
   const uint8_t* mask;      // [ny][pitch]: 0 fluid, 1..kMaxBodies body, 255 static solid
   const void* us;           // static solid velocity, float2/double2 [ny][pitch], or null
+  const void* ghost_src;    // convective outlet state g^{t-1}: [3][ny] of the arithmetic
+  void* ghost_dst;          // type (offsets, rows alpha = 3, 6, 7); g^t goes to ghost_dst
   int nx, ny, pitch;
   int bc_x, bc_y;
   int tiles_x, n_tiles;
@@ -111,6 +115,17 @@ template <> __host__ __device__ inline const Consts<float>& consts<float>(const 
 struct GroupTile {
   int solver;
   int tile;
+};
+
+// Arguments of the momentum-exchange reduction: a box of candidate solid
+// nodes (inclusive bounds; empty when x1 < x0), united on the device with the
+// box of the static solid layer, and the reduction's scratch and output.
+struct MeArgs {
+  int x0, y0, x1, y1;
+  const int* static_box;  // device {x0, y0, x1, y1} of the static layer
+  double* partials;       // [kMeBlocks][2]
+  unsigned* counter;      // zero on entry, left zero
+  double* out;            // F_x, F_y
 };
 
 }  // namespace vplbm

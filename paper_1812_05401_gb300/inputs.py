@@ -108,6 +108,7 @@ class Workload:
     bodies: list = field(default_factory=list)
     perturbation: float = 0.0
     seed: int = 1
+    outlet: str = "zero-gradient"  # channel outlet: "zero-gradient" | "convective"
 
     def initial_velocity(self) -> np.ndarray:
         u0 = (self.u_ref, 0.0) if self.bc == "channel" else (0.0, 0.0)
@@ -128,15 +129,16 @@ def circular_couette(n: int = 128, r1: float = 24.0, r2: float = 56.0, wall_spee
 
 def cylinder_channel(nx: int, ny: int, diameter: float, u_in: float, re: float, steps: int,
                      xc: float | None = None, collision: str = "mrt", storage: str = "f32",
-                     perturbation: float = 1e-4, seed: int = 1, lam: float = 3.0 / 16.0) -> Workload:
-    """Fixed cylinder in a channel: uniform inlet at x = 0, outlet at x = nx - 1,
-    free-slip walls at y = 0 and y = ny - 1."""
+                     perturbation: float = 1e-4, seed: int = 1, lam: float = 3.0 / 16.0,
+                     outlet: str = "zero-gradient") -> Workload:
+    """Fixed cylinder in a channel: uniform inlet at x = 0, outlet at x = nx - 1
+    (zero-gradient or convective), free-slip walls at y = 0 and y = ny - 1."""
     xc = nx / 4.0 if xc is None else xc
     return Workload(
         name=f"cylinder-channel-{nx}x{ny}-D{diameter:g}-Re{re:g}", nx=nx, ny=ny,
         collision=collision, storage=storage, bc="channel", steps=steps, u_ref=u_in,
         l_ref=diameter, re=re, lam=lam, bodies=[BodySpec(xc, (ny - 1) / 2.0, diameter / 2.0)],
-        perturbation=perturbation, seed=seed)
+        perturbation=perturbation, seed=seed, outlet=outlet)
 
 
 def moving_cylinder_channel(nx: int = 16384, ny: int = 4096, diameter: float = 256.0,

@@ -24,7 +24,7 @@ VPLBM_OK, VPLBM_ERR_INVALID, VPLBM_ERR_NOMEM, VPLBM_ERR_CUDA = 0, 1, 2, 3
 VPLBM_ERR_DIVERGED, VPLBM_ERR_TIMEOUT, VPLBM_ERR_STATE = 4, 5, 6
 VPLBM_SRT, VPLBM_MRT = 0, 1
 VPLBM_F64, VPLBM_F32, VPLBM_F16_OFFSET, VPLBM_BF16_OFFSET = 0, 1, 2, 3
-VPLBM_BC_PERIODIC, VPLBM_BC_INLET_OUTLET, VPLBM_BC_FREE_SLIP = 0, 1, 2
+VPLBM_BC_PERIODIC, VPLBM_BC_INLET_OUTLET, VPLBM_BC_FREE_SLIP, VPLBM_BC_INLET_CONVECTIVE = 0, 1, 2, 3
 VPLBM_MAX_BODIES = 8
 VPLBM_ROUND_NEAREST, VPLBM_ROUND_STOCHASTIC = 0, 1
 
@@ -46,7 +46,8 @@ class vplbm_config(C.Structure):
                 ("tau", C.c_double), ("lam", C.c_double), ("eta", C.c_double),
                 ("u_in", C.c_double * 2), ("rho0", C.c_double), ("u0", C.c_double * 2),
                 ("body_force", C.c_double * 2), ("rates", C.c_double * 9),
-                ("force_ring_len", C.c_int32), ("rounding", C.c_int32), ("stream", C.c_void_p)]
+                ("force_ring_len", C.c_int32), ("rounding", C.c_int32), ("stream", C.c_void_p),
+                ("u_conv", C.c_double)]
 
 
 class VplbmError(RuntimeError):
@@ -96,6 +97,9 @@ def lib() -> C.CDLL:
         L.vplbm_set_populations.argtypes = [P, P, C.c_int32]
         L.vplbm_mask.argtypes = [P, P]
         L.vplbm_forces.argtypes = [P, dp, dp, dp, C.c_int64, C.POINTER(C.c_int64)]
+        L.vplbm_momentum_exchange.argtypes = [P, dp, dp]
+        L.vplbm_enable_momentum_exchange.argtypes = [P, C.c_int32]
+        L.vplbm_momentum_exchange_forces.argtypes = [P, dp, dp, C.c_int64, C.POINTER(C.c_int64)]
         L.vplbm_group_step.argtypes = [C.POINTER(P), C.c_int32, C.POINTER(C.c_int64)]
         L.vplbm_launch_count.argtypes = [P]
         L.vplbm_launch_count.restype = C.c_int64
@@ -112,7 +116,9 @@ def lib() -> C.CDLL:
                      "vplbm_set_mask_and_solid_velocity",
                      "vplbm_set_bodies", "vplbm_step", "vplbm_synchronize", "vplbm_moments",
                      "vplbm_populations", "vplbm_set_populations", "vplbm_mask", "vplbm_forces",
-                     "vplbm_group_step", "vplbm_enable_timing", "vplbm_fused_timing"):
+                     "vplbm_group_step", "vplbm_enable_timing", "vplbm_fused_timing",
+                     "vplbm_momentum_exchange", "vplbm_enable_momentum_exchange",
+                     "vplbm_momentum_exchange_forces"):
             getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -257,6 +263,28 @@ def vplbm_forces(h, cap: int):
     return fx[:k], fy[:k], ms[:k]
 
 
+def vplbm_momentum_exchange(h):
+    fx, fy = C.c_double(), C.c_double()
+    _check(h, lib().vplbm_momentum_exchange(h, C.byref(fx), C.byref(fy)), "vplbm_momentum_exchange")
+    return fx.value, fy.value
+
+
+def vplbm_enable_momentum_exchange(h, enable: bool = True):
+    _check(h, lib().vplbm_enable_momentum_exchange(h, 1 if enable else 0),
+           "vplbm_enable_momentum_exchange")
+
+
+def vplbm_momentum_exchange_forces(h, cap: int):
+    fx, fy = np.zeros(cap), np.zeros(cap)
+    cnt = C.c_int64()
+    dp = C.POINTER(C.c_double)
+    _check(h, lib().vplbm_momentum_exchange_forces(h, fx.ctypes.data_as(dp), fy.ctypes.data_as(dp),
+                                                   cap, C.byref(cnt)),
+           "vplbm_momentum_exchange_forces")
+    k = cnt.value
+    return fx[:k], fy[:k]
+
+
 def vplbm_group_step(handles, steps):
     n = len(handles)
     arr = (C.c_void_p * max(1, n))(*handles)
@@ -294,7 +322,10 @@ def vplbm_destroy(h):
 def make_config(nx, ny, collision="srt", storage="f32", tau=0.8, lam=3.0 / 16.0, eta=1e-7,
                 bc="periodic", u_in=(0.0, 0.0), u0=(0.0, 0.0), rho0=1.0, body_force=(0.0, 0.0),
                 rates=None, reduce_mass=True, ring_len=4096, stream=None,
-                rounding="stochastic") -> vplbm_config:
+                rounding="stochastic", u_conv=None) -> vplbm_config:
+    """bc: "periodic", "channel" (inlet, zero-gradient outlet, free-slip walls),
+    "channel-convective" (the same with the convective outlet; U_c = u_conv,
+    by default the inlet speed), or a (bc_x, bc_y) pair."""
     c = vplbm_config_init()
     c.nx, c.ny = int(nx), int(ny)
     c.collision = COLLISION[collision] if isinstance(collision, str) else int(collision)
@@ -303,8 +334,11 @@ def make_config(nx, ny, collision="srt", storage="f32", tau=0.8, lam=3.0 / 16.0,
         c.bc_x, c.bc_y = VPLBM_BC_PERIODIC, VPLBM_BC_PERIODIC
     elif bc == "channel":
         c.bc_x, c.bc_y = VPLBM_BC_INLET_OUTLET, VPLBM_BC_FREE_SLIP
+    elif bc == "channel-convective":
+        c.bc_x, c.bc_y = VPLBM_BC_INLET_CONVECTIVE, VPLBM_BC_FREE_SLIP
     else:
         c.bc_x, c.bc_y = bc
+    c.u_conv = float(u_in[0] if u_conv is None else u_conv)
     c.tau, c.lam, c.eta = tau, lam, eta
     c.u_in[0], c.u_in[1] = u_in
     c.u0[0], c.u0[1] = u0
@@ -329,7 +363,8 @@ def config_from_workload(w, ring_len: int = 4096, stream=None, reduce_mass: bool
     Reynolds number when it gives one)."""
     tau = w.tau if w.tau is not None else vplbm_tau_from_reynolds(w.u_ref, w.l_ref, w.re)
     u_in = (w.u_ref, 0.0) if w.bc == "channel" else (0.0, 0.0)
-    cfg = make_config(w.nx, w.ny, w.collision, w.storage, tau, w.lam, bc=w.bc, u_in=u_in,
+    bc = "channel-convective" if w.bc == "channel" and w.outlet == "convective" else w.bc
+    cfg = make_config(w.nx, w.ny, w.collision, w.storage, tau, w.lam, bc=bc, u_in=u_in,
                       ring_len=ring_len, stream=stream, reduce_mass=reduce_mass, rounding=rounding)
     return cfg, list(w.bodies)
 
@@ -424,6 +459,16 @@ class Solver:
 
     def forces(self, cap: int | None = None):
         return vplbm_forces(self.h, cap or self.cfg.force_ring_len)
+
+    def momentum_exchange(self):
+        """Momentum-exchange force on the solids at the current state."""
+        return vplbm_momentum_exchange(self.h)
+
+    def record_momentum_exchange(self, enable: bool = True):
+        vplbm_enable_momentum_exchange(self.h, enable)
+
+    def momentum_exchange_forces(self, cap: int | None = None):
+        return vplbm_momentum_exchange_forces(self.h, cap or self.cfg.force_ring_len)
 
     @property
     def launches(self) -> int:

@@ -7,9 +7,9 @@ top and bottom, constant-velocity inlet, cylinder 25D from the outlet.
 Table 2 (VP-LBM column): C_Dave = 1.45, C_Lrms = 0.84, St = 0.22.
 
 Readings: cylinder centre 5D from the inlet (x = 1005) and on the centre line
-(y = 1007.5); zero-gradient outlet in place of the paper's convective one;
-the force is the penalization volume integral (the paper uses momentum
-exchange); statistics over steps 200,000-400,000 (~11 shedding periods; the
+(y = 1007.5); the outlet is run both as the paper's convective condition
+(U_c = the inlet speed) and as a zero-gradient copy; the force is measured both ways -- the penalization volume integral and the
+paper's momentum exchange over the mask's fluid-to-solid links; statistics over steps 200,000-400,000 (~11 shedding periods; the
 force record shows the shedding saturated by step 200,000), St from the lift
 spectrum.
 
@@ -17,9 +17,12 @@ Measured (FP32, 500,000-step run, window 250k-500k): C_Dave = 1.544 (+6.5%),
 C_Lrms = 0.98 (+17%), St = 0.2345 (+6.6%). Drag and Strouhal number are both
 a few percent above the paper's, as the 10% blockage of the free-slip walls
 at +-5D would produce; the paper's values sit on the unconfined experiments.
-The other differences above (force definition, outlet) are candidates too.
+The outlet is a candidate too. The two force measures differ by the rate of
+change of the solid region's momentum (a one-step balance the oracle pins),
+whose mean vanishes in a periodic state: their C_Dave agree closely.
 Bounds: 8% on C_Dave and St, 20% on C_Lrms (the RMS lift is the most
-sensitive to the outlet and force definitions).
+sensitive to the outlet and force definitions), for both measures; 1% between
+the two measures' C_Dave and St.
 """
 import json
 import os
@@ -34,7 +37,8 @@ PAPER = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
 pytestmark = pytest.mark.gpu
 
 
-def test_table2_cylinder_re500():
+@pytest.mark.parametrize("outlet", ["convective", "zero-gradient"])
+def test_table2_cylinder_re500(outlet):
     import torch
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
@@ -44,15 +48,22 @@ def test_table2_cylinder_re500():
     from paper_1812_05401_gb300 import vplbm as V
     D, U, steps = float(PAPER["D"]), PAPER["U"], 400_000
     w = I.cylinder_channel(PAPER["nx"], PAPER["ny"], D, U, 500.0, steps, xc=5 * D, collision="srt",
-                           storage="f32", perturbation=1e-4, seed=1)
+                           storage="f32", perturbation=1e-4, seed=1, outlet=outlet)
     cfg, bodies = V.config_from_workload(w, ring_len=steps, reduce_mass=False)
     cfg.tau = PAPER["tau"]  # as printed
     with V.Solver(cfg, bodies, w.initial_velocity()) as s:
+        s.record_momentum_exchange(True)
         s.step(steps)
         s.synchronize()
         fx, fy, _ = s.forces()
+        mx, my = s.momentum_exchange_forces()
     st = diag.wake_statistics(fx, fy, U, D, discard=0.5)
-    print("Table 2 reproduction:", st)
-    assert st["C_D_ave"] == pytest.approx(PAPER["C_D_ave"], rel=0.08)
-    assert st["St"] == pytest.approx(PAPER["St"], rel=0.08)
-    assert st["C_L_rms"] == pytest.approx(PAPER["C_L_rms"], rel=0.20)
+    me = diag.wake_statistics(mx, my, U, D, discard=0.5)
+    print(f"Table 2 reproduction ({outlet} outlet), penalization integral:", st)
+    print(f"Table 2 reproduction ({outlet} outlet), momentum exchange:", me)
+    for r in (st, me):
+        assert r["C_D_ave"] == pytest.approx(PAPER["C_D_ave"], rel=0.08)
+        assert r["St"] == pytest.approx(PAPER["St"], rel=0.08)
+        assert r["C_L_rms"] == pytest.approx(PAPER["C_L_rms"], rel=0.20)
+    assert me["C_D_ave"] == pytest.approx(st["C_D_ave"], rel=0.01)
+    assert me["St"] == pytest.approx(st["St"], rel=0.01)
