@@ -63,13 +63,13 @@ def hbm_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def traffic_per_launch(workload: str, storage: str):
+def traffic_per_launch(workload: str, storage: str, streaming: str = "ab"):
     """DRAM bytes per fused launch from the committed ncu summary, if it was
     taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "fused_step_traffic.json")
     try:
         d = json.load(open(p))
-        e = d.get(f"{workload}:{storage}")
+        e = d.get(f"{workload}:{storage}" + ("" if streaming == "ab" else f":{streaming}"))
         if e and e.get("kernel_hash") == kernel_hash():
             return float(e["dram_bytes_per_launch"])
     except Exception:
@@ -232,7 +232,8 @@ def run_gpu(args):
 
     w = make_workload(args.workload, args.storage)
     nodes = w.nx * w.ny
-    s = V.Solver.from_workload(w, stream=stream, ring_len=max(4096, args.steps + 16))
+    s = V.Solver.from_workload(w, stream=stream, ring_len=max(4096, args.steps + 16),
+                               streaming=args.streaming)
     try:
         # warm-up
         s.step(args.warmup)
@@ -284,37 +285,45 @@ def run_gpu(args):
     finally:
         s.close()
 
-    # ---- same workload, FP16-offset storage (FP32 vs FP16-store comparison)
-    extra = {}
-    if args.compare_f16 and args.storage == "f32":
-        w16 = make_workload(args.workload, "f16")
-        s16 = V.Solver.from_workload(w16, stream=stream, ring_len=4096)
+    # ---- the same workload in another storage or streaming scheme (side
+    # measurements: FP16-offset store, in-place AA streaming)
+    def side_run(storage, streaming):
+        ws = make_workload(args.workload, storage)
+        s2 = V.Solver.from_workload(ws, stream=stream, ring_len=4096, streaming=streaming)
         try:
-            s16.step(args.warmup)
-            s16.synchronize()
-            V.vplbm_enable_timing(s16.h, True)
-            V.vplbm_fused_timing(s16.h)
+            s2.step(args.warmup)
+            s2.synchronize()
+            V.vplbm_enable_timing(s2.h, True)
+            V.vplbm_fused_timing(s2.h)
             a0 = torch.cuda.Event(enable_timing=True)
             a1 = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             with torch.cuda.stream(stream):
                 a0.record(stream)
-            s16.step(args.steps)
+            s2.step(args.steps)
             with torch.cuda.stream(stream):
                 a1.record(stream)
             torch.cuda.synchronize()
-            s16.synchronize()
-            ms16 = max_over_ranks(a0.elapsed_time(a1))
-            k16, n16 = V.vplbm_fused_timing(s16.h)
+            s2.synchronize()
+            ms2 = max_over_ranks(a0.elapsed_time(a1))
+            k2, n2 = V.vplbm_fused_timing(s2.h)
+            cfg2, _ = V.config_from_workload(ws, streaming=streaming)
+            foot = V.vplbm_footprint_bytes(cfg2)
         finally:
-            s16.close()
-        peak, src = hbm_peak()
-        kms = k16 / max(n16, 1)
-        ach = ALGO_BYTES["f16"] * nodes / (kms / 1e3) / 1e9
-        extra["f16_offset_store"] = {"value": round(world * nodes * args.steps / (ms16 / 1e3) / 1e6, 1),
-                                     "unit": "MLUPS", "fused_kernel_ms": round(kms, 4),
-                                     "achieved_gbs": round(ach, 1), "frac": round(ach / peak, 4),
-                                     "algo_bytes_per_node": ALGO_BYTES["f16"]}
+            s2.close()
+        peak, _ = hbm_peak()
+        kms2 = k2 / max(n2, 1)
+        ach = ALGO_BYTES[storage] * nodes / (kms2 / 1e3) / 1e9
+        return {"value": round(world * nodes * args.steps / (ms2 / 1e3) / 1e6, 1),
+                "unit": "MLUPS", "fused_kernel_ms": round(kms2, 4),
+                "achieved_gbs": round(ach, 1), "frac": round(ach / peak, 4),
+                "algo_bytes_per_node": ALGO_BYTES[storage], "footprint_gb": round(foot / 1e9, 3)}
+
+    extra = {}
+    if args.compare_f16 and args.storage == "f32":
+        extra["f16_offset_store"] = side_run("f16", args.streaming)
+    if args.compare_aa and args.storage == "f32" and args.streaming == "ab":
+        extra["aa_inplace"] = side_run("f32", "aa")
 
     if args.serve_in_bench:
         rep = run_serving(args, n_requests=args.serve_requests, rate=args.serve_rate_bench,
@@ -324,7 +333,7 @@ def run_gpu(args):
     peak, peak_src = hbm_peak()
     kms = fused_ms / max(fused_n, 1)
     achieved = ALGO_BYTES[args.storage] * nodes / (kms / 1e3) / 1e9
-    traffic = traffic_per_launch(args.workload, args.storage)
+    traffic = traffic_per_launch(args.workload, args.storage, args.streaming)
     result = {
         "metric": "VP-LBM MLUPS (node updates per second / 1e6)",
         "value": round(value, 1),
@@ -342,8 +351,11 @@ def run_gpu(args):
                    "nx": w.nx, "ny": w.ny, "nodes": nodes, "storage": args.storage,
                    "collision": w.collision, "re": w.re, "u_in": w.u_ref,
                    "step": "mask update of the moving body + fused pull/penalize/collide/reduce kernel",
-                   "l2": "inputs larger than L2 (two population buffers of %.2f GB)" % (
-                       2 * 9 * nodes * {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}[args.storage] / 1e9),
+                   "streaming": args.streaming,
+                   "l2": "inputs larger than L2 (%s population buffer%s of %.2f GB)" % (
+                       "two" if args.streaming == "ab" else "one in-place",
+                       "s" if args.streaming == "ab" else "",
+                       9 * nodes * {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}[args.storage] / 1e9),
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": round(e2e, 1), "unit": "MLUPS", "h2d_bytes_per_step": 704,
                 "d2h_bytes_per_step": 24,
@@ -351,7 +363,8 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_source": f"{peak_src} copy bandwidth",
-                     "kernel": "fused_step_kernel<F32,MRT>" if args.storage == "f32" else f"fused_step_kernel<{args.storage},MRT>",
+                     "kernel": f"fused_step_kernel<{args.storage.upper()},MRT>" + (
+                         "" if args.streaming == "ab" else " (in place: push and local steps)"),
                      "kernel_ms": round(kms, 4), "algo_bytes_per_node": ALGO_BYTES[args.storage],
                      "algo_bytes_per_launch": ALGO_BYTES[args.storage] * nodes},
         "gpu_launches": launches,
@@ -479,6 +492,10 @@ def main():
                     choices=["moving-cylinder", "cylinder-re1000", "cylinder-re100"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f64"])
     ap.add_argument("--no-compare-f16", dest="compare_f16", action="store_false")
+    ap.add_argument("--no-compare-aa", dest="compare_aa", action="store_false",
+                    help="skip the in-place (AA) streaming side measurement")
+    ap.add_argument("--streaming", default="ab", choices=["ab", "aa"],
+                    help="streaming scheme of the headline run (A/B buffers or in place)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-budget", type=float, default=90.0,

@@ -83,6 +83,17 @@ enum { VPLBM_ROUND_NEAREST = 0, VPLBM_ROUND_STOCHASTIC = 1 };
 enum { VPLBM_BC_PERIODIC = 0, VPLBM_BC_INLET_OUTLET = 1, VPLBM_BC_FREE_SLIP = 2,
        VPLBM_BC_INLET_CONVECTIVE = 3 };
 
+/* Streaming scheme. AB: two population buffers, each step pulls from one and
+ * writes the other. AA: in-place streaming on one buffer (the AA pattern),
+ * half the population memory with the same bytes moved per node update; steps
+ * alternate between a push step (each node pulls from the opposite slots of
+ * its neighbours and writes to their own slots) and a local step (each node
+ * reads its own slots and writes its opposite slots). The stored values are
+ * rounded with the same bits as in AB, so the two schemes give bitwise the
+ * same populations, forces and moments; all entry points behave alike, except
+ * vplbm_step_noalloc, which takes AB buffers only. */
+enum { VPLBM_STREAM_AB = 0, VPLBM_STREAM_AA = 1 };
+
 /* Largest number of rigid bodies a solver tracks. */
 #define VPLBM_MAX_BODIES 8
 
@@ -118,6 +129,8 @@ typedef struct {
   int32_t rounding;        /* VPLBM_ROUND_NEAREST | VPLBM_ROUND_STOCHASTIC (16-bit stores) */
   void* stream;            /* cudaStream_t to run on, or NULL for a private stream */
   double u_conv;           /* convective outlet velocity U_c >= 0 (bc_x = INLET_CONVECTIVE) */
+  int32_t streaming;       /* VPLBM_STREAM_AB (default) | VPLBM_STREAM_AA */
+  int32_t reserved;        /* 0 */
 } vplbm_config;
 
 typedef struct vplbm_solver vplbm_solver;
@@ -306,8 +319,8 @@ vplbm_status vplbm_fused_timing(vplbm_solver* s, double* total_ms, int64_t* laun
  * can overlap on the GPU (different streams without ordering) race and give
  * wrong results: order them on one stream. Asynchronous on cfg->stream;
  * returns VPLBM_ERR_INVALID for bad arguments (including the convective
- * outlet, whose state lives in a solver) and VPLBM_ERR_CUDA if a CUDA call
- * fails. Calls no allocating routine. */
+ * outlet, whose state lives in a solver, and AA streaming) and VPLBM_ERR_CUDA
+ * if a CUDA call fails. Calls no allocating routine. */
 vplbm_status vplbm_step_noalloc(const vplbm_config* cfg, const vplbm_body* bodies,
                                 int32_t n_bodies, const void* f_src, void* f_dst,
                                 const uint8_t* mask, const void* us, int32_t pitch,

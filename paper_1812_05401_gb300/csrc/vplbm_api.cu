@@ -214,6 +214,11 @@ struct vplbm_solver {
   int* flag = nullptr;
   int* static_box = nullptr;  // device box {x0, y0, x1, y1} of the static solid layer
   void* ghost[2] = {nullptr, nullptr};  // convective outlet state of f[0], f[1] ([3][ny])
+  // In-place (AA) streaming: one population buffer (f[1] aliases f[0]) and cur
+  // is the phase (0: the next step is a push step, 1: a local step).
+  bool aa = false;
+  void* z = nullptr;     // AA, open outlet: stored f*(nx - 1) of alpha = 3, 6, 7
+  void* lost = nullptr;  // AA, open x sides: values pushed out of the grid
 
   // Momentum-exchange force (Section 3.3): records per step when enabled.
   bool me_on = false;
@@ -414,6 +419,7 @@ StepParams step_params(const vplbm_solver* s, int64_t t, int parity) {
   p.dst = s->f[c ^ 1];
   p.ghost_src = s->ghost[c];
   p.ghost_dst = s->ghost[c ^ 1];
+  p.mode = s->aa ? (c == 0 ? kModeAAPush : kModeAALocal) : kModeAB;
   if (p.use_tma) p.tmap = s->tmap[c];
   p.t = t;
   fill_bodies(s, t, &p);
@@ -431,12 +437,12 @@ cudaError_t launch_fused(const vplbm_solver* s, const StepParams& p) {
 }
 
 cudaError_t launch_group(int storage, const StepParams* dp, const GroupTile* dt, int nb, long long k,
-                         cudaStream_t st) {
+                         int mode, cudaStream_t st) {
   switch (storage) {
-    case kF64: return launch_group_f64(dp, dt, nb, k, st);
-    case kF32: return launch_group_f32(dp, dt, nb, k, st);
-    case kF16: return launch_group_f16(dp, dt, nb, k, st);
-    default: return launch_group_bf16(dp, dt, nb, k, st);
+    case kF64: return launch_group_f64(dp, dt, nb, k, mode, st);
+    case kF32: return launch_group_f32(dp, dt, nb, k, mode, st);
+    case kF16: return launch_group_f16(dp, dt, nb, k, mode, st);
+    default: return launch_group_bf16(dp, dt, nb, k, mode, st);
   }
 }
 
@@ -474,13 +480,23 @@ cudaError_t launch_init(const vplbm_solver* s, const StepParams& p, void* dst, c
   }
 }
 
-cudaError_t launch_ghost_init(const vplbm_solver* s, const StepParams& p, const void* src, void* g) {
+cudaError_t launch_ghost_init(const vplbm_solver* s, const StepParams& p, const void* src, void* g,
+                              void* z) {
   switch (s->cfg.storage) {
-    case kF64: return launch_ghost_init_f64(p, src, g, s->stream);
-    case kF32: return launch_ghost_init_f32(p, src, g, s->stream);
-    case kF16: return launch_ghost_init_f16(p, src, g, s->stream);
-    default: return launch_ghost_init_bf16(p, src, g, s->stream);
+    case kF64: return launch_ghost_init_f64(p, src, g, z, s->stream);
+    case kF32: return launch_ghost_init_f32(p, src, g, z, s->stream);
+    case kF16: return launch_ghost_init_f16(p, src, g, z, s->stream);
+    default: return launch_ghost_init_bf16(p, src, g, z, s->stream);
   }
+}
+
+// Outlet state once the populations were set (cur: the new store's buffer,
+// or phase in place): the convective state and, in place, the side copy of
+// the last column start as copies of the store's last column.
+vplbm_status init_outlet_state(vplbm_solver* s) {
+  if (!s->ghost[0] && !s->z) return VPLBM_OK;
+  VP_CUDA(s, launch_ghost_init(s, step_params(s, s->t, 0), s->f[s->cur], s->ghost[s->cur], s->z));
+  return VPLBM_OK;
 }
 
 cudaError_t launch_export(const vplbm_solver* s, const StepParams& p, const void* src, double* f) {
@@ -514,6 +530,8 @@ vplbm_status validate(const vplbm_config* c, std::string* why) {
     return *why = "bc_x must be PERIODIC, INLET_OUTLET or INLET_CONVECTIVE", VPLBM_ERR_INVALID;
   if (c->bc_x == VPLBM_BC_INLET_CONVECTIVE && !(c->u_conv >= 0.0 && std::isfinite(c->u_conv)))
     return *why = "u_conv must be finite and >= 0", VPLBM_ERR_INVALID;
+  if (c->streaming != VPLBM_STREAM_AB && c->streaming != VPLBM_STREAM_AA)
+    return *why = "streaming must be AB or AA", VPLBM_ERR_INVALID;
   if (c->bc_y != VPLBM_BC_PERIODIC && c->bc_y != VPLBM_BC_FREE_SLIP)
     return *why = "bc_y must be PERIODIC or FREE_SLIP", VPLBM_ERR_INVALID;
   if (!(c->tau > 0.5) || !std::isfinite(c->tau)) return *why = "tau must be > 1/2", VPLBM_ERR_INVALID;
@@ -611,7 +629,9 @@ size_t vplbm_footprint_bytes(const vplbm_config* c) {
   tiles_of(c, &tx, &ty, &nt, &ng);
   const size_t pitch = size_t(row_pitch(c->nx, c->storage));
   const size_t plane = pitch * size_t(c->ny);
-  size_t b = 2 * 9 * plane * element_size(c->storage);  // A/B populations
+  const bool aa = c->streaming == VPLBM_STREAM_AA;
+  size_t b = (aa ? 1 : 2) * 9 * plane * element_size(c->storage);  // A/B or in-place populations
+  if (aa && c->bc_x != VPLBM_BC_PERIODIC) b += 9 * size_t(c->ny) * element_size(c->storage);
   b += plane;                                            // mask
   b += 3 * sizeof(double) * (size_t(nt) + size_t(ng));   // reduction partials
   b += sizeof(unsigned) * (size_t(ng) + 1);
@@ -655,8 +675,9 @@ vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
   // Stream-ordered allocations: neither allocation nor release synchronizes
   // the device, so solvers can come and go while others run (serving).
   cudaStream_t st0 = s->stream;
+  s->aa = cfg->streaming == VPLBM_STREAM_AA;
   if ((e = cudaMallocAsync(&s->f[0], pop, st0)) != cudaSuccess ||
-      (e = cudaMallocAsync(&s->f[1], pop, st0)) != cudaSuccess ||
+      (!s->aa && (e = cudaMallocAsync(&s->f[1], pop, st0)) != cudaSuccess) ||
       (e = cudaMallocAsync(reinterpret_cast<void**>(&s->mask), size_t(s->plane), st0)) != cudaSuccess ||
       (e = cudaMallocAsync(reinterpret_cast<void**>(&s->partials), 3 * sizeof(double) * s->n_tiles, st0)) != cudaSuccess ||
       (e = cudaMallocAsync(reinterpret_cast<void**>(&s->group_partials), 3 * sizeof(double) * s->n_groups, st0)) != cudaSuccess ||
@@ -673,8 +694,18 @@ vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
       (e = cudaMemcpyAsync(s->static_box, kEmptyBox, sizeof(kEmptyBox), cudaMemcpyHostToDevice,
                            s->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(s->f[0], 0, pop, s->stream)) != cudaSuccess ||
-      (e = cudaMemsetAsync(s->f[1], 0, pop, s->stream)) != cudaSuccess) {
+      (!s->aa && (e = cudaMemsetAsync(s->f[1], 0, pop, s->stream)) != cudaSuccess)) {
     return bail(cuda_fail(s, e, "cudaMemsetAsync"));
+  }
+  if (s->aa) {
+    s->f[1] = s->f[0];
+    if (cfg->bc_x != VPLBM_BC_PERIODIC) {
+      if ((e = cudaMallocAsync(&s->z, 3 * size_t(cfg->ny) * s->esize, st0)) != cudaSuccess ||
+          (e = cudaMallocAsync(&s->lost, 6 * size_t(cfg->ny) * s->esize, st0)) != cudaSuccess)
+        return bail(cuda_fail(s, e, "cudaMallocAsync"));
+      if ((e = cudaMemsetAsync(s->lost, 0, 6 * size_t(cfg->ny) * s->esize, st0)) != cudaSuccess)
+        return bail(cuda_fail(s, e, "cudaMemsetAsync"));
+    }
   }
   if (cfg->bc_x == VPLBM_BC_INLET_CONVECTIVE) {
     const size_t gb = 3 * size_t(cfg->ny) * ghost_elem(cfg->storage);
@@ -695,6 +726,9 @@ vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
   p.bc_y = cfg->bc_y;
   p.tiles_x = s->tiles_x;
   p.n_tiles = s->n_tiles;
+  p.mode = s->aa ? kModeAAPush : kModeAB;
+  p.z = s->z;
+  p.lost = s->lost;
   Consts<double>& cd = p.cd;
   cd.omega = 1.0 / cfg->tau;
   cd.srt_pre = 1.0 - 1.0 / (2.0 * cfg->tau);
@@ -741,7 +775,7 @@ vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
   // leave room for only two blocks per SM.
   {
     const char* env = std::getenv("VPLBM_TMA");
-    const bool want = env && env[0] == '1';
+    const bool want = env && env[0] == '1' && !s->aa;
     p.use_tma = want && make_tensor_map(&s->tmap[0], s->f[0], cfg->storage, s->pitch, cfg->ny) &&
                         make_tensor_map(&s->tmap[1], s->f[1], cfg->storage, s->pitch, cfg->ny)
                     ? 1
@@ -764,7 +798,7 @@ vplbm_status vplbm_set_initial_velocity(vplbm_solver* s, const double* u) {
   }
   s->cur = 0;
   VP_CUDA(s, launch_init(s, s->base, s->f[0], du));
-  if (s->ghost[0]) VP_CUDA(s, launch_ghost_init(s, s->base, s->f[0], s->ghost[0]));
+  if ((st = init_outlet_state(s)) != VPLBM_OK) return st;
   if (du) VP_CUDA(s, cudaFreeAsync(du, s->stream));
   s->t = 0;
   s->ring_read = 0;
@@ -919,12 +953,12 @@ vplbm_status vplbm_populations(vplbm_solver* s, double* f, int32_t on_device) {
   if (!f) return fail(s, VPLBM_ERR_INVALID, "output pointer is NULL");
   const size_t n = size_t(s->cfg.nx) * s->cfg.ny;
   if (on_device) {
-    VP_CUDA(s, launch_export(s, s->base, s->f[s->cur], f));
+    VP_CUDA(s, launch_export(s, step_params(s, s->t, 0), s->f[s->cur], f));
     return VPLBM_OK;
   }
   double* d = nullptr;
   VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&d), 9 * n * sizeof(double), s->stream));
-  VP_CUDA(s, launch_export(s, s->base, s->f[s->cur], d));
+  VP_CUDA(s, launch_export(s, step_params(s, s->t, 0), s->f[s->cur], d));
   VP_CUDA(s, cudaMemcpyAsync(f, d, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   VP_CUDA(s, cudaFreeAsync(d, s->stream));
   VP_CUDA(s, cudaStreamSynchronize(s->stream));
@@ -936,6 +970,7 @@ vplbm_status vplbm_set_populations(vplbm_solver* s, const double* f, int32_t on_
   if (st != VPLBM_OK) return st;
   if (!f) return fail(s, VPLBM_ERR_INVALID, "input pointer is NULL");
   const size_t n = size_t(s->cfg.nx) * s->cfg.ny;
+  if (s->aa) s->cur = 0;  // in place: the store restarts before a push step
   if (on_device) {
     VP_CUDA(s, launch_import(s, s->base, s->f[s->cur], f));
   } else {
@@ -946,8 +981,7 @@ vplbm_status vplbm_set_populations(vplbm_solver* s, const double* f, int32_t on_
     VP_CUDA(s, cudaFreeAsync(d, s->stream));
   }
   // the convective outlet restarts from a zero-gradient copy of the new store
-  if (s->ghost[0]) VP_CUDA(s, launch_ghost_init(s, s->base, s->f[s->cur], s->ghost[s->cur]));
-  return VPLBM_OK;
+  return init_outlet_state(s);
 }
 
 vplbm_status vplbm_mask(vplbm_solver* s, uint8_t* chi) {
@@ -1008,8 +1042,10 @@ struct StateHeader {
   int64_t t;
   uint64_t pop_bytes, mask_bytes, us_bytes;
   uint64_t ghost_bytes;  // convective outlet state, 0 for other outlets
+  int32_t aa, phase;     // in-place streaming and its phase
+  uint64_t side_bytes;   // in place, open x sides: the side copy z and the lost values
 };
-constexpr uint64_t kStateMagic = 0x56504c424d535432ull;  // "VPLBMST2"
+constexpr uint64_t kStateMagic = 0x56504c424d535433ull;  // "VPLBMST3"
 
 size_t us_bytes(const vplbm_solver* s) {
   if (!s->us) return 0;
@@ -1019,12 +1055,14 @@ size_t us_bytes(const vplbm_solver* s) {
 size_t ghost_bytes(const vplbm_solver* s) {
   return s->ghost[0] ? 3 * size_t(s->cfg.ny) * ghost_elem(s->cfg.storage) : 0;
 }
+
+size_t side_bytes(const vplbm_solver* s) { return s->z ? 9 * size_t(s->cfg.ny) * s->esize : 0; }
 }  // namespace
 
 size_t vplbm_state_bytes(const vplbm_solver* s) {
   if (!s) return 0;
   return sizeof(StateHeader) + 9 * size_t(s->plane) * s->esize + size_t(s->plane) + us_bytes(s) +
-         ghost_bytes(s);
+         ghost_bytes(s) + side_bytes(s);
 }
 
 vplbm_status vplbm_save_state(vplbm_solver* s, void* buf) {
@@ -1045,6 +1083,9 @@ vplbm_status vplbm_save_state(vplbm_solver* s, void* buf) {
   h.mask_bytes = uint64_t(s->plane);
   h.us_bytes = us_bytes(s);
   h.ghost_bytes = ghost_bytes(s);
+  h.aa = s->aa ? 1 : 0;
+  h.phase = s->aa ? s->cur : 0;
+  h.side_bytes = side_bytes(s);
   char* out = static_cast<char*>(buf);
   std::memcpy(out, &h, sizeof(h));
   out += sizeof(h);
@@ -1058,6 +1099,12 @@ vplbm_status vplbm_save_state(vplbm_solver* s, void* buf) {
   if (h.ghost_bytes)
     VP_CUDA(s, cudaMemcpyAsync(out, s->ghost[s->cur], h.ghost_bytes, cudaMemcpyDeviceToHost,
                                s->stream));
+  out += h.ghost_bytes;
+  if (h.side_bytes) {
+    const size_t zb = 3 * size_t(s->cfg.ny) * s->esize;
+    VP_CUDA(s, cudaMemcpyAsync(out, s->z, zb, cudaMemcpyDeviceToHost, s->stream));
+    VP_CUDA(s, cudaMemcpyAsync(out + zb, s->lost, h.side_bytes - zb, cudaMemcpyDeviceToHost, s->stream));
+  }
   VP_CUDA(s, cudaStreamSynchronize(s->stream));
   return VPLBM_OK;
 }
@@ -1070,7 +1117,8 @@ vplbm_status vplbm_load_state(vplbm_solver* s, const void* buf) {
   std::memcpy(&h, buf, sizeof(h));
   if (h.magic != kStateMagic || h.nx != s->cfg.nx || h.ny != s->cfg.ny || h.pitch != s->pitch ||
       h.storage != s->cfg.storage || h.pop_bytes != 9 * uint64_t(s->plane) * s->esize ||
-      h.mask_bytes != uint64_t(s->plane) || h.t < 0 || h.ghost_bytes != ghost_bytes(s))
+      h.mask_bytes != uint64_t(s->plane) || h.t < 0 || h.ghost_bytes != ghost_bytes(s) ||
+      h.aa != (s->aa ? 1 : 0) || h.side_bytes != side_bytes(s) || h.phase < 0 || h.phase > 1)
     return fail(s, VPLBM_ERR_INVALID, "state does not match this solver's grid and storage");
   const char* in = static_cast<const char*>(buf) + sizeof(h);
   VP_CUDA(s, cudaMemcpyAsync(s->f[s->cur], in, h.pop_bytes, cudaMemcpyHostToDevice, s->stream));
@@ -1086,9 +1134,16 @@ vplbm_status vplbm_load_state(vplbm_solver* s, const void* buf) {
     s->base.us = s->us;
     in += h.us_bytes;
   }
+  if (s->aa) s->cur = h.phase;  // before the state is placed: the ghost index is the phase
   if (h.ghost_bytes)
     VP_CUDA(s, cudaMemcpyAsync(s->ghost[s->cur], in, h.ghost_bytes, cudaMemcpyHostToDevice,
                                s->stream));
+  in += h.ghost_bytes;
+  if (h.side_bytes) {
+    const size_t zb = 3 * size_t(s->cfg.ny) * s->esize;
+    VP_CUDA(s, cudaMemcpyAsync(s->z, in, zb, cudaMemcpyHostToDevice, s->stream));
+    VP_CUDA(s, cudaMemcpyAsync(s->lost, in + zb, h.side_bytes - zb, cudaMemcpyHostToDevice, s->stream));
+  }
   // pageable host-to-device copies have been staged when they return
   s->t = h.t;
   s->ring_read = h.t;
@@ -1192,7 +1247,7 @@ vplbm_status vplbm_set_initial_perturbation(vplbm_solver* s, double u0x, double 
   VP_CUDA(s, cudaGetLastError());
   s->cur = 0;
   VP_CUDA(s, launch_init(s, s->base, s->f[0], du));
-  if (s->ghost[0]) VP_CUDA(s, launch_ghost_init(s, s->base, s->f[0], s->ghost[0]));
+  if ((st = init_outlet_state(s)) != VPLBM_OK) return st;
   VP_CUDA(s, cudaFreeAsync(du, s->stream));
   s->t = 0;
   s->ring_read = 0;
@@ -1227,17 +1282,22 @@ vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int
     int idx;
     int64_t steps;
   };
-  std::vector<Member> classes[4];  // one grouped launch per storage type and step
+  // One grouped launch per step for each storage type and scheme class: A/B
+  // (class 0), and in place by phase at the group's first step (classes 1, 2:
+  // phase 0 or 1), whose launches alternate between push and local steps.
+  std::vector<Member> classes[4][3];
   std::vector<int> moving;
   for (int i = 0; i < n; ++i) {
     if (solvers[i]->moving || solvers[i]->me_on) {
       moving.push_back(i);
       continue;
     }
-    classes[solvers[i]->cfg.storage].push_back({i, steps[i]});
+    const vplbm_solver* s = solvers[i];
+    classes[s->cfg.storage][s->aa ? 1 + s->cur : 0].push_back({i, steps[i]});
   }
   struct Plan {
     int storage;
+    int cls;
     StepParams* d_params;
     GroupTile* d_table;
     std::vector<int64_t> prefix_steps;  // steps of the j-th member (descending)
@@ -1245,8 +1305,8 @@ vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int
   };
   std::vector<Plan> plans;
   for (int sg = 0; sg < 4; ++sg) {
-    {
-      auto& mem = classes[sg];
+    for (int cls = 0; cls < 3; ++cls) {
+      auto& mem = classes[sg][cls];
       if (mem.empty()) continue;
       std::stable_sort(mem.begin(), mem.end(),
                        [](const Member& a, const Member& b) { return a.steps > b.steps; });
@@ -1254,6 +1314,7 @@ vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int
       std::vector<GroupTile> ht;
       Plan pl;
       pl.storage = sg;
+      pl.cls = cls;
       for (size_t j = 0; j < mem.size(); ++j) {
         vplbm_solver* s = solvers[mem[j].idx];
         hp.push_back(step_params(s, s->t, 0));
@@ -1280,7 +1341,9 @@ vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int
       while (active < int(pl.prefix_steps.size()) && pl.prefix_steps[active] > k) ++active;
       if (active == 0) continue;
       const int nb = pl.prefix_tiles[active - 1];
-      VP_CUDA(s0, launch_group(pl.storage, pl.d_params, pl.d_table, nb, k, stream));
+      const int mode = pl.cls == 0 ? kModeAB
+                                   : (((pl.cls - 1) ^ int(k & 1)) == 0 ? kModeAAPush : kModeAALocal);
+      VP_CUDA(s0, launch_group(pl.storage, pl.d_params, pl.d_table, nb, k, mode, stream));
     }
     for (int i : moving) {
       if (steps[i] > k) {
@@ -1351,9 +1414,9 @@ void vplbm_destroy(vplbm_solver* s) {
   }
   for (auto e : s->ev_pool) cudaEventDestroy(e);
   if (s->stream) {
-    void* bufs[] = {s->f[0], s->f[1], s->mask, s->us, s->partials, s->group_partials,
+    void* bufs[] = {s->f[0], s->aa ? nullptr : s->f[1], s->mask, s->us, s->partials, s->group_partials,
                     s->counters, s->ring, s->flag, s->static_box, s->me_ring,
-                    s->me_scratch, s->me_counter, s->ghost[0], s->ghost[1]};
+                    s->me_scratch, s->me_counter, s->ghost[0], s->ghost[1], s->z, s->lost};
     for (void* b : bufs)
       if (b) cudaFreeAsync(b, s->stream);
     if (s->own_stream) cudaStreamDestroy(s->stream);
@@ -1421,9 +1484,9 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_config* cfg, const vplbm_
     std::fprintf(stderr, "vplbm_step_noalloc: pitch must be >= nx and a multiple of 8\n");
     return VPLBM_ERR_INVALID;
   }
-  if (cfg->bc_x == VPLBM_BC_INLET_CONVECTIVE) {
-    std::fprintf(stderr, "vplbm_step_noalloc: the convective outlet keeps state between steps "
-                         "(use vplbm_create / vplbm_step)\n");
+  if (cfg->bc_x == VPLBM_BC_INLET_CONVECTIVE || cfg->streaming != VPLBM_STREAM_AB) {
+    std::fprintf(stderr, "vplbm_step_noalloc: the convective outlet and in-place streaming keep "
+                         "state between steps (use vplbm_create / vplbm_step)\n");
     return VPLBM_ERR_INVALID;
   }
   int tx, ty, nt, ng;

@@ -69,6 +69,11 @@ template <> struct Store<kF64> {
   static __device__ __forceinline__ void store_h(E* p, const T h[2], int a, const unsigned*, bool) {
     *reinterpret_cast<double2*>(p) = make_double2(h[0] + wgt<T>(a), h[1] + wgt<T>(a));
   }
+  // one element's raw bits, rounded as store_h rounds it (r: the node's word)
+  using R = unsigned long long;
+  static __device__ __forceinline__ R round_e(T h, int a, unsigned, bool) {
+    return static_cast<R>(__double_as_longlong(h + wgt<T>(a)));
+  }
 };
 template <> struct Store<kF32> {
   // FP32 elements hold the offsets h = f - w as well: the same bytes as f,
@@ -102,6 +107,8 @@ template <> struct Store<kF32> {
   static __device__ __forceinline__ void store_h(E* p, const T h[4], int, const unsigned*, bool) {
     *reinterpret_cast<float4*>(p) = make_float4(h[0], h[1], h[2], h[3]);
   }
+  using R = unsigned;
+  static __device__ __forceinline__ R round_e(T h, int, unsigned, bool) { return __float_as_uint(h); }
 };
 // 16-bit offset forms: npt = 4 elements as one 8-byte access.
 // Multipliers deriving each direction's rounding bits from the node's word
@@ -185,6 +192,11 @@ template <> struct Store<kF16> : Store16<__half> {
   }
   static __device__ __forceinline__ T in(E e, int) { return __half2float(e); }
   static __device__ __forceinline__ E out(T h, int) { return __float2half_rn(h); }
+  // one element as store_h rounds it (the packed conversions round each half alike)
+  using R = unsigned short;
+  static __device__ __forceinline__ R round_e(T h, int a, unsigned r, bool sr) {
+    return __half_as_ushort(sr ? __float2half_rz(dither<13>(h, r * round_mul(a))) : __float2half_rn(h));
+  }
   static __device__ __forceinline__ double to_f64(const E* p, int a) {
     return wgt<double>(a) + double(__half2float(*p));
   }
@@ -221,6 +233,11 @@ template <> struct Store<kBF16> : Store16<__nv_bfloat16> {
   }
   static __device__ __forceinline__ T in(E e, int) { return __bfloat162float(e); }
   static __device__ __forceinline__ E out(T h, int) { return __float2bfloat16_rn(h); }
+  using R = unsigned short;
+  static __device__ __forceinline__ R round_e(T h, int a, unsigned r, bool sr) {
+    return __bfloat16_as_ushort(sr ? __float2bfloat16_rz(dither<16>(h, r * round_mul(a)))
+                                   : __float2bfloat16_rn(h));
+  }
   static __device__ __forceinline__ double to_f64(const E* p, int a) {
     return wgt<double>(a) + double(__bfloat162float(*p));
   }
@@ -271,6 +288,22 @@ __device__ __forceinline__ typename S::T outlet_ghost(const StepParams& p,
   const T f_last = load_h<S>(src + (long long)as * p.plane + (long long)ys * p.pitch + (p.nx - 1), as);
   const T g = (static_cast<const T*>(p.ghost_src)[gi] + c.u_conv * f_last) * c.conv_inv;
   if (write) static_cast<T*>(p.ghost_dst)[gi] = g;
+  return g;
+}
+
+// The same ghost value in the in-place (AA) push step, whose store no longer
+// holds the last column intact (the neighbours' pushes overwrite it): the
+// stored f*(nx - 1) comes from the side copy z that the local step wrote.
+template <class S>
+__device__ __forceinline__ typename S::T outlet_ghost_aa(const StepParams& p, int as, int ys,
+                                                         bool write) {
+  using T = typename S::T;
+  const long long gi = (long long)(as == 3 ? 0 : (as == 6 ? 1 : 2)) * p.ny + ys;
+  const T f_last = S::in(static_cast<const typename S::E*>(p.z)[gi], as);
+  if (p.bc_x != kBcInletConvective) return f_last;  // zero gradient
+  const Consts<T>& c = consts<T>(p);
+  const T g = (static_cast<const T*>(p.ghost_src)[gi] + c.u_conv * f_last) * c.conv_inv;
+  if (write && p.ghost_dst) static_cast<T*>(p.ghost_dst)[gi] = g;
   return g;
 }
 
@@ -623,7 +656,10 @@ __device__ __forceinline__ void finish_reduction(const StepParams& p, int tile, 
 // entering the domain's last column; lanes past the last column load and
 // store nothing. The arithmetic per node is the same on both paths.
 // ---------------------------------------------------------------------------
-template <class S, int A>
+// AA: the push step reads f*_as(xs, ys) from the opposite slot of the source
+// node (where the local step put it), with plain (coherent) loads, since the
+// kernel also writes this buffer.
+template <class S, int A, bool AA = false>
 __device__ __forceinline__ typename S::T edge_pull(const StepParams& p, const typename S::E* src,
                                                    int as, int ys, int xs) {
   if (xs < 0 || xs >= p.nx) {
@@ -633,6 +669,8 @@ __device__ __forceinline__ typename S::T edge_pull(const StepParams& p, const ty
     } else if (xs < 0) {  // inlet ghost column at f_eq(1, u_in)
       const Consts<typename S::T>& c = consts<typename S::T>(p);
       return as == A ? c.heq_in[A] : c.heq_in[mirror_y(A)];
+    } else if (AA) {
+      return outlet_ghost_aa<S>(p, as, ys, xs == p.nx);
     } else if (p.bc_x == kBcInletConvective) {
       // xs == nx: the last column's own pull (the entry's one reader); beyond
       // it, the unused edge value of a lane past the last column
@@ -641,10 +679,11 @@ __device__ __forceinline__ typename S::T edge_pull(const StepParams& p, const ty
       xs = p.nx - 1;
     }
   }
+  if (AA) return S::in(src[(long long)opposite(as) * p.plane + (long long)ys * p.pitch + xs], A);
   return load_h<S>(src + (long long)as * p.plane + (long long)ys * p.pitch + xs, A);
 }
 
-template <class S, int N, int A, bool GEN>
+template <class S, int N, int A, bool GEN, bool AA = false>
 __device__ __forceinline__ void pull_dir_vec(const StepParams& p, const typename S::E* src, int xb,
                                              int y, int lane, bool lane_active,
                                              typename S::T (&h)[N][9]) {
@@ -660,10 +699,13 @@ __device__ __forceinline__ void pull_dir_vec(const StepParams& p, const typename
       ys = y;
     }
   }
-  const E* row = src + (long long)as * p.plane + (long long)ys * p.pitch;
+  const E* row = src + (long long)(AA ? opposite(as) : as) * p.plane + (long long)ys * p.pitch;
   T v[N];
   if (!GEN || lane_active) {
-    S::load_h(row + xb, v, A);
+    if (AA)
+      S::load_h_shared(row + xb, v, A);  // a plain generic load
+    else
+      S::load_h(row + xb, v, A);
   } else {
 #pragma unroll
     for (int k = 0; k < N; ++k) v[k] = T(0);
@@ -673,14 +715,17 @@ __device__ __forceinline__ void pull_dir_vec(const StepParams& p, const typename
     for (int k = 0; k < N; ++k) h[k][A] = v[k];
   } else if (cx(A) == 1) {  // node k pulls from x - 1
     T left = __shfl_up_sync(0xffffffffu, v[N - 1], 1);
-    if (lane == 0) left = GEN ? edge_pull<S, A>(p, src, as, ys, xb - 1) : load_h<S>(row + xb - 1, A);
+    if (lane == 0)
+      left = GEN ? edge_pull<S, A, AA>(p, src, as, ys, xb - 1)
+                 : (AA ? S::in(row[xb - 1], A) : load_h<S>(row + xb - 1, A));
     h[0][A] = left;
 #pragma unroll
     for (int k = 1; k < N; ++k) h[k][A] = v[k - 1];
   } else {  // node k pulls from x + 1
     T right = __shfl_down_sync(0xffffffffu, v[0], 1);
     if (lane == kLanes - 1)
-      right = GEN ? edge_pull<S, A>(p, src, as, ys, xb + N) : load_h<S>(row + xb + N, A);
+      right = GEN ? edge_pull<S, A, AA>(p, src, as, ys, xb + N)
+                  : (AA ? S::in(row[xb + N], A) : load_h<S>(row + xb + N, A));
 #pragma unroll
     for (int k = 0; k < N - 1; ++k) h[k][A] = v[k + 1];
     h[N - 1][A] = right;
@@ -688,9 +733,198 @@ __device__ __forceinline__ void pull_dir_vec(const StepParams& p, const typename
       // the domain's last column pulls from beyond it, through the x boundary
 #pragma unroll
       for (int k = 0; k < N; ++k)
-        if (xb + k == p.nx - 1) h[k][A] = edge_pull<S, A>(p, src, as, ys, p.nx);
+        if (xb + k == p.nx - 1) h[k][A] = edge_pull<S, A, AA>(p, src, as, ys, p.nx);
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// In-place (AA-pattern) streaming on one buffer. A push step reads each
+// population from the opposite slot of its source node (where the previous
+// local step put it), collides, and writes f*_a to slot a of the node it
+// streams to; a local step reads a node's own slots, collides, and writes f*_a
+// to the node's opposite slot. Every location a push step reads is written by
+// the same node, after its read: in the vector layout both happen in the lane
+// that owns the location's aligned vector (or the edge lane's extra element),
+// so the buffer can be updated in place. Each value is rounded with the bits
+// of its node, direction and step, as the A/B scheme rounds it, so the two
+// schemes give bitwise the same populations.
+// ---------------------------------------------------------------------------
+template <class S>
+__device__ __forceinline__ void store_raw(typename S::E* p, typename S::R w) {
+  *reinterpret_cast<typename S::R*>(p) = w;
+}
+// N raw elements to an aligned vector (16 bytes, or 8 for 16-bit storage)
+template <class S, int N>
+__device__ __forceinline__ void store_raw_vec(typename S::E* p, const typename S::R (&w)[N]) {
+  if constexpr (sizeof(typename S::E) == 2) {
+    uint2 v;
+    v.x = unsigned(w[0]) | (unsigned(w[1 % N]) << 16);
+    v.y = unsigned(w[2 % N]) | (unsigned(w[3 % N]) << 16);
+    *reinterpret_cast<uint2*>(p) = v;
+  } else if constexpr (sizeof(typename S::E) == 4) {
+    *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1 % N], w[2 % N], w[3 % N]);
+  } else {
+    *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(w[0], w[1 % N]);
+  }
+}
+template <class R>
+__device__ __forceinline__ R shfl_up_raw(R v) {
+  if constexpr (sizeof(R) == 8)
+    return __shfl_up_sync(0xffffffffu, v, 1);
+  else
+    return R(__shfl_up_sync(0xffffffffu, unsigned(v), 1));
+}
+template <class R>
+__device__ __forceinline__ R shfl_down_raw(R v) {
+  if constexpr (sizeof(R) == 8)
+    return __shfl_down_sync(0xffffffffu, v, 1);
+  else
+    return R(__shfl_down_sync(0xffffffffu, unsigned(v), 1));
+}
+
+// Slot of the value that a push step sends out through an open x side:
+// lost[side][k][y], side 0 = x = nx - 1 (alpha = 1, 5, 8), 1 = x = 0 (alpha = 3, 6, 7).
+__device__ __forceinline__ long long lost_index(const StepParams& p, int a, int y, bool left) {
+  const int k = left ? (a == 3 ? 0 : (a == 6 ? 1 : 2)) : (a == 1 ? 0 : (a == 5 ? 1 : 2));
+  return (long long)((left ? 3 : 0) + k) * p.ny + y;
+}
+
+// Where a push step puts f*_a of node (x, y): the pull's boundary rules read
+// backwards (periodic wrap; a free-slip wall returns it as mirror_y(a) in the
+// same row at x + cx(a)). Returns false when it leaves through an open x side.
+__device__ __forceinline__ bool push_target(const StepParams& p, int a, int x, int y, int* ap,
+                                            int* xt, int* yt) {
+  *ap = a;
+  *xt = x + cx(a);
+  *yt = y + cy(a);
+  if (*yt < 0 || *yt >= p.ny) {
+    if (p.bc_y == kBcPeriodic) {
+      *yt = *yt < 0 ? *yt + p.ny : *yt - p.ny;
+    } else {
+      *ap = mirror_y(a);
+      *yt = y;
+    }
+  }
+  if (*xt < 0 || *xt >= p.nx) {
+    if (p.bc_x != kBcPeriodic) return false;
+    *xt = *xt < 0 ? *xt + p.nx : *xt - p.nx;
+  }
+  return true;
+}
+
+template <class S>
+__device__ __forceinline__ void push_one(const StepParams& p, typename S::E* buf, int a, int x, int y,
+                                         typename S::R e) {
+  int ap, xt, yt;
+  if (push_target(p, a, x, y, &ap, &xt, &yt))
+    store_raw<S>(buf + (long long)ap * p.plane + (long long)yt * p.pitch + xt, e);
+  else
+    store_raw<S>(static_cast<typename S::E*>(p.lost) + lost_index(p, a, y, x + cx(a) < 0), e);
+}
+
+// The outlet's ghost column (a copy of the last column) streams its
+// populations alpha = 3, 6, 7 into the last column: the push step writes them
+// where the next local step reads them (that step turns them into the
+// zero-gradient or convective ghost values).
+template <class S>
+__device__ __forceinline__ void push_outlet_copy(const StepParams& p, typename S::E* buf, int as,
+                                                 int y, typename S::R e) {
+  int ap = as, yt = y + cy(as);
+  if (yt < 0 || yt >= p.ny) {
+    if (p.bc_y == kBcPeriodic) {
+      yt = yt < 0 ? yt + p.ny : yt - p.ny;
+    } else {
+      ap = mirror_y(as);
+      yt = y;
+    }
+  }
+  store_raw<S>(buf + (long long)ap * p.plane + (long long)yt * p.pitch + (p.nx - 1), e);
+}
+
+// Interior tiles: the push of direction a as one aligned vector store per
+// lane (the x-shifted element from the neighbouring lane); the edge lanes
+// write the element that crosses into the next tile, and leave the one the
+// neighbouring tile writes.
+template <class S, int N>
+__device__ __forceinline__ void push_dir_vec(const StepParams& p, typename S::E* buf, int a, int xb,
+                                             int y, int lane, const typename S::R (&e)[N]) {
+  using R = typename S::R;
+  typename S::E* row = buf + (long long)a * p.plane + (long long)(y + cy(a)) * p.pitch;
+  if (cx(a) == 0) {
+    store_raw_vec<S, N>(row + xb, e);
+  } else if (cx(a) == 1) {  // element j of this lane's vector receives node xb + j - 1
+    R w[N];
+    w[0] = shfl_up_raw(e[N - 1]);
+#pragma unroll
+    for (int j = 1; j < N; ++j) w[j] = e[j - 1];
+    if (lane == 0) {
+#pragma unroll
+      for (int j = 1; j < N; ++j) store_raw<S>(row + xb + j, w[j]);
+    } else {
+      store_raw_vec<S, N>(row + xb, w);
+    }
+    if (lane == kLanes - 1) store_raw<S>(row + xb + N, e[N - 1]);
+  } else {  // element j receives node xb + j + 1
+    R w[N];
+#pragma unroll
+    for (int j = 0; j < N - 1; ++j) w[j] = e[j + 1];
+    w[N - 1] = shfl_down_raw(e[0]);
+    if (lane == kLanes - 1) {
+#pragma unroll
+      for (int j = 0; j < N - 1; ++j) store_raw<S>(row + xb + j, w[j]);
+    } else {
+      store_raw_vec<S, N>(row + xb, w);
+    }
+    if (lane == 0) store_raw<S>(row + xb - 1, e[0]);
+  }
+}
+
+// Local step at the open x sides: the values the A/B pull would take from the
+// ghost columns. Inlet: f_eq(1, u_in) for the directions entering at x = 0.
+// Outlet: h holds the ghost column's copy of f*(nx - 1) (pushed there by the
+// previous push step); the convective outlet advances its state from it.
+template <class S>
+__device__ __forceinline__ void aa_local_boundary(const StepParams& p, typename S::T h[9], int x,
+                                                  int y, bool write) {
+  using T = typename S::T;
+  if (p.bc_x == kBcPeriodic) return;
+  const Consts<T>& c = consts<T>(p);
+#pragma unroll
+  for (int a = 1; a < 9; ++a) {
+    if (!((cx(a) == 1 && x == 0) || (cx(a) == -1 && x == p.nx - 1))) continue;
+    int as = a, ys = y - cy(a);
+    if (ys < 0 || ys >= p.ny) {
+      if (p.bc_y == kBcPeriodic) {
+        ys = ys < 0 ? ys + p.ny : ys - p.ny;
+      } else {
+        as = mirror_y(a);
+        ys = y;
+      }
+    }
+    if (cx(a) == 1) {
+      h[a] = c.heq_in[as];
+    } else if (p.bc_x == kBcInletConvective) {
+      const long long gi = (long long)(as == 3 ? 0 : (as == 6 ? 1 : 2)) * p.ny + ys;
+      const T g = (static_cast<const T*>(p.ghost_src)[gi] + c.u_conv * h[a]) * c.conv_inv;
+      if (write) static_cast<T*>(p.ghost_dst)[gi] = g;
+      h[a] = g;
+    }
+  }
+}
+
+// f*_a(x, y) as stored, whatever the scheme and phase (for the diagnostics:
+// export, momentum exchange, outlet state).
+template <class S>
+__device__ __forceinline__ typename S::E fstar_e(const StepParams& p, const typename S::E* buf, int a,
+                                                 int x, int y) {
+  if (p.mode == kModeAB) return buf[(long long)a * p.plane + (long long)y * p.pitch + x];
+  if (p.mode == kModeAAPush)  // after a local step: the node's opposite slot
+    return buf[(long long)opposite(a) * p.plane + (long long)y * p.pitch + x];
+  int ap, xt, yt;  // after a push step: where it was pushed
+  if (push_target(p, a, x, y, &ap, &xt, &yt))
+    return buf[(long long)ap * p.plane + (long long)yt * p.pitch + xt];
+  return static_cast<const typename S::E*>(p.lost)[lost_index(p, a, y, x + cx(a) < 0)];
 }
 
 // ---------------------------------------------------------------------------
@@ -773,7 +1007,9 @@ __device__ __forceinline__ void pull_dir_smem(const typename S::E* row, int lane
 // TMA: interior tiles are staged through shared memory (tma_smem, the
 // kernel's dynamic shared memory of tma_smem_bytes(STORE)); a separate kernel
 // instantiation, so the direct-pull kernel carries none of its code.
-template <int STORE, int COLL, bool TMA = false>
+// MODE: kModeAB (pull from p.src, store to p.dst), or one of the two in-place
+// AA steps on the one buffer p.dst (== p.src).
+template <int STORE, int COLL, bool TMA = false, int MODE = kModeAB>
 __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long long t,
                                           unsigned char* tma_smem) {
   using S = Store<STORE>;
@@ -793,6 +1029,8 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
   const bool interior = x0 >= 1 && x0 + TX <= p.nx - 1 && y0 >= 1 && y0 + kTileY <= p.ny - 1;
   const E* __restrict__ src = static_cast<const E*>(p.src);
   E* __restrict__ dst = static_cast<E*>(p.dst);
+  E* buf = static_cast<E*>(p.dst);  // the in-place modes' one buffer (not restrict: read and written)
+  static_assert(MODE == kModeAB || !TMA, "TMA staging is for the A/B scheme");
 
   T dm = T(0);           // sum of drho over this thread's nodes
   T tfx = T(0), tfy = T(0);  // force on this thread's solid nodes (<= 16, arithmetic type)
@@ -840,12 +1078,56 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
         collide_mrt<T>(p, h[k], q);
       finish_node(q, m[k]);
     }
+    if constexpr (MODE == kModeAB) {
 #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-      T o[N];
+      for (int a = 0; a < 9; ++a) {
+        T o[N];
 #pragma unroll
-      for (int k = 0; k < N; ++k) o[k] = h[k][a];
-      S::store_h(dst + (long long)a * p.plane + i, o, a, nb, sr);
+        for (int k = 0; k < N; ++k) o[k] = h[k][a];
+        S::store_h(dst + (long long)a * p.plane + i, o, a, nb, sr);
+      }
+    } else if constexpr (MODE == kModeAALocal) {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        T o[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) o[k] = h[k][a];
+        S::store_h(buf + (long long)opposite(a) * p.plane + i, o, a, nb, sr);
+      }
+      if (GEN && p.bc_x != kBcPeriodic) {
+        // the outlet column's stored f* of alpha = 3, 6, 7, for the next push step
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          if (xb + k != p.nx - 1) continue;
+          typename S::R* z = static_cast<typename S::R*>(p.z);
+          z[0 * p.ny + y] = S::round_e(h[k][3], 3, nb[k], sr);
+          z[1 * p.ny + y] = S::round_e(h[k][6], 6, nb[k], sr);
+          z[2 * p.ny + y] = S::round_e(h[k][7], 7, nb[k], sr);
+        }
+      }
+    } else {  // push step
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        typename S::R e[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) e[k] = S::round_e(h[k][a], a, nb[k], sr);
+        if (!GEN) {
+          push_dir_vec<S, N>(p, buf, a, xb, y, lane, e);
+        } else {
+#pragma unroll
+          for (int k = 0; k < N; ++k)
+            if (xb + k < p.nx) push_one<S>(p, buf, a, xb + k, y, e[k]);
+        }
+      }
+      if (GEN && p.bc_x != kBcPeriodic) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          if (xb + k != p.nx - 1) continue;
+          push_outlet_copy<S>(p, buf, 3, y, S::round_e(h[k][3], 3, nb[k], sr));
+          push_outlet_copy<S>(p, buf, 6, y, S::round_e(h[k][6], 6, nb[k], sr));
+          push_outlet_copy<S>(p, buf, 7, y, S::round_e(h[k][7], 7, nb[k], sr));
+        }
+      }
     }
   };
 
@@ -853,16 +1135,35 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
     constexpr bool GEN = decltype(gen)::value;
     const bool lane_active = !GEN || xb < p.nx;
     T h[N][9];
-    pull_dir_vec<S, N, 0, GEN>(p, src, xb, y, lane, lane_active, h);
-    pull_dir_vec<S, N, 1, GEN>(p, src, xb, y, lane, lane_active, h);
-    pull_dir_vec<S, N, 2, GEN>(p, src, xb, y, lane, lane_active, h);
-    pull_dir_vec<S, N, 3, GEN>(p, src, xb, y, lane, lane_active, h);
-    pull_dir_vec<S, N, 4, GEN>(p, src, xb, y, lane, lane_active, h);
-    pull_dir_vec<S, N, 5, GEN>(p, src, xb, y, lane, lane_active, h);
-    pull_dir_vec<S, N, 6, GEN>(p, src, xb, y, lane, lane_active, h);
-    pull_dir_vec<S, N, 7, GEN>(p, src, xb, y, lane, lane_active, h);
-    pull_dir_vec<S, N, 8, GEN>(p, src, xb, y, lane, lane_active, h);
-    if (!lane_active) return;
+    if constexpr (MODE == kModeAALocal) {
+      if (!lane_active) return;
+      const long long i = (long long)y * p.pitch + xb;
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        T v[N];
+        S::load_h_shared(buf + (long long)a * p.plane + i, v, a);  // a plain generic load
+#pragma unroll
+        for (int k = 0; k < N; ++k) h[k][a] = v[k];
+      }
+      if (GEN) {
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+          if (xb + k < p.nx) aa_local_boundary<S>(p, h[k], xb + k, y, true);
+      }
+    } else {
+      constexpr bool AA = MODE == kModeAAPush;
+      const E* from = AA ? buf : src;
+      pull_dir_vec<S, N, 0, GEN, AA>(p, from, xb, y, lane, lane_active, h);
+      pull_dir_vec<S, N, 1, GEN, AA>(p, from, xb, y, lane, lane_active, h);
+      pull_dir_vec<S, N, 2, GEN, AA>(p, from, xb, y, lane, lane_active, h);
+      pull_dir_vec<S, N, 3, GEN, AA>(p, from, xb, y, lane, lane_active, h);
+      pull_dir_vec<S, N, 4, GEN, AA>(p, from, xb, y, lane, lane_active, h);
+      pull_dir_vec<S, N, 5, GEN, AA>(p, from, xb, y, lane, lane_active, h);
+      pull_dir_vec<S, N, 6, GEN, AA>(p, from, xb, y, lane, lane_active, h);
+      pull_dir_vec<S, N, 7, GEN, AA>(p, from, xb, y, lane, lane_active, h);
+      pull_dir_vec<S, N, 8, GEN, AA>(p, from, xb, y, lane, lane_active, h);
+      if (!lane_active) return;
+    }
     process_row(y, h, gen);
   };
 
@@ -980,10 +1281,10 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
   finish_reduction(p, tile, t, ts, sm);
 }
 
-template <int STORE, int COLL, bool TMA>
+template <int STORE, int COLL, bool TMA, int MODE = kModeAB>
 __global__ void __launch_bounds__(kThreads, min_blocks_per_sm(STORE)) fused_step_kernel(const __grid_constant__ StepParams p) {
   extern __shared__ __align__(128) unsigned char dyn_smem[];
-  step_tile<STORE, COLL, TMA>(p, blockIdx.x, p.t, dyn_smem);
+  step_tile<STORE, COLL, TMA, MODE>(p, blockIdx.x, p.t, dyn_smem);
 }
 
 // Grouped launch for serving: block b runs tile table[b].tile of solver
@@ -992,8 +1293,9 @@ __global__ void __launch_bounds__(kThreads, min_blocks_per_sm(STORE)) fused_step
 // buffers swapped); params[].t is the solver's step index at k = 0. The block
 // copies its solver's parameters to shared memory first (they are read many
 // times per node), and takes the collision operator from them, so one launch
-// covers SRT and MRT solvers of one storage type.
-template <int STORE>
+// covers SRT and MRT solvers of one storage type. MODE: the streaming step of
+// every solver in the launch (in-place solvers are grouped by phase).
+template <int STORE, int MODE = kModeAB>
 __global__ void __launch_bounds__(kThreads, min_blocks_per_sm(STORE))
     fused_group_kernel(const StepParams* __restrict__ params, const GroupTile* __restrict__ table,
                        long long k) {
@@ -1010,14 +1312,52 @@ __global__ void __launch_bounds__(kThreads, min_blocks_per_sm(STORE))
   __syncthreads();
   // grouped launches pull directly (use_tma is off in their parameters)
   if (sp.collision == kSrt)
-    step_tile<STORE, kSrt>(sp, gt.tile, sp.t + k, nullptr);
+    step_tile<STORE, kSrt, false, MODE>(sp, gt.tile, sp.t + k, nullptr);
   else
-    step_tile<STORE, kMrt>(sp, gt.tile, sp.t + k, nullptr);
+    step_tile<STORE, kMrt, false, MODE>(sp, gt.tile, sp.t + k, nullptr);
 }
 
 // ---------------------------------------------------------------------------
 // Moments: the density and implicit velocity the next step computes.
 // ---------------------------------------------------------------------------
+// The populations the next step pulls, in any scheme and phase (read only:
+// the caller's parameters carry no ghost_dst).
+template <class S, int A>
+__device__ __forceinline__ typename S::T pull_aa(const StepParams& p, const typename S::E* buf, int x,
+                                                 int y) {
+  int as = A, ys = y - cy(A);
+  if (ys < 0 || ys >= p.ny) {
+    if (p.bc_y == kBcPeriodic) {
+      ys = ys < 0 ? ys + p.ny : ys - p.ny;
+    } else {
+      as = mirror_y(A);
+      ys = y;
+    }
+  }
+  return edge_pull<S, A, true>(p, buf, as, ys, x - cx(A));
+}
+template <class S>
+__device__ __forceinline__ void pull_node_any(const StepParams& p, int x, int y, typename S::T h[9]) {
+  const typename S::E* buf = static_cast<const typename S::E*>(p.src);
+  if (p.mode == kModeAB) {
+    pull_node<S>(p, buf, false, x, y, h);
+  } else if (p.mode == kModeAALocal) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) h[a] = S::in(buf[(long long)a * p.plane + (long long)y * p.pitch + x], a);
+    aa_local_boundary<S>(p, h, x, y, false);
+  } else {
+    h[0] = pull_aa<S, 0>(p, buf, x, y);
+    h[1] = pull_aa<S, 1>(p, buf, x, y);
+    h[2] = pull_aa<S, 2>(p, buf, x, y);
+    h[3] = pull_aa<S, 3>(p, buf, x, y);
+    h[4] = pull_aa<S, 4>(p, buf, x, y);
+    h[5] = pull_aa<S, 5>(p, buf, x, y);
+    h[6] = pull_aa<S, 6>(p, buf, x, y);
+    h[7] = pull_aa<S, 7>(p, buf, x, y);
+    h[8] = pull_aa<S, 8>(p, buf, x, y);
+  }
+}
+
 template <int STORE>
 __global__ void moments_kernel(const __grid_constant__ StepParams p, double* rho, double* ux,
                                double* uy) {
@@ -1027,7 +1367,7 @@ __global__ void moments_kernel(const __grid_constant__ StepParams p, double* rho
   const int y = blockIdx.y * kBlockY + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
   T h[9];
-  pull_node<S>(p, static_cast<const typename S::E*>(p.src), false, x, y, h);
+  pull_node_any<S>(p, x, y, h);
   const uint8_t m = p.mask[(long long)y * p.pitch + x];
   const Macro<T> q = macros<T>(p, h, m, x, y);
   const long long o = (long long)y * p.nx + x;
@@ -1088,8 +1428,8 @@ __global__ void __launch_bounds__(kThreads)
         }
         if (p.mask[(long long)yf * p.pitch + xf] != 0) continue;
         const int o = opposite(a);
-        const double flow = S::to_f64(src + a * p.plane + (long long)yf * p.pitch + xf, a) +
-                            S::to_f64(src + o * p.plane + (long long)y * p.pitch + x, o);
+        const E ef = fstar_e<S>(p, src, a, xf, yf), es = fstar_e<S>(p, src, o, x, y);
+        const double flow = S::to_f64(&ef, a) + S::to_f64(&es, o);
         fx += double(cx(a)) * flow;
         fy += double(cy(a)) * flow;
       }
@@ -1139,22 +1479,28 @@ __global__ void init_kernel(const __grid_constant__ StepParams p, void* dst, con
   for (int a = 0; a < 9; ++a) {
     const T xu = T(cx(a)) * ux + T(cy(a)) * uy;
     const T heq = wgt<T>(a) * (common + rho * xu * (T(3) + T(4.5) * xu));
-    store_h<S>(d + (long long)a * p.plane + i, heq, a);
+    // in place (AA), a state before a push step keeps f*_a in the opposite slot
+    const int slot = p.mode == kModeAB ? a : opposite(a);
+    store_h<S>(d + (long long)slot * p.plane + i, heq, a);
   }
 }
 
 // Convective outlet state g := the offsets of the last column of the store
 // (a zero-gradient start), [3][ny] rows alpha = 3, 6, 7.
+// In place (AA), also the side copy z of those stored values (either output
+// may be null).
 template <int STORE>
-__global__ void ghost_init_kernel(const __grid_constant__ StepParams p, const void* srcv, void* ghostv) {
+__global__ void ghost_init_kernel(const __grid_constant__ StepParams p, const void* srcv, void* ghostv,
+                                  void* zv) {
   using S = Store<STORE>;
   using T = typename S::T;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 3 * p.ny) return;
   const int k = i / p.ny, y = i - k * p.ny;
   const int a = k == 0 ? 3 : (k == 1 ? 6 : 7);
-  const typename S::E* src = static_cast<const typename S::E*>(srcv);
-  static_cast<T*>(ghostv)[i] = load_h<S>(src + (long long)a * p.plane + (long long)y * p.pitch + (p.nx - 1), a);
+  const typename S::E e = fstar_e<S>(p, static_cast<const typename S::E*>(srcv), a, p.nx - 1, y);
+  if (ghostv) static_cast<T*>(ghostv)[i] = S::in(e, a);
+  if (zv) static_cast<typename S::E*>(zv)[i] = e;
 }
 
 // Store <-> dense FP64 [9][ny][nx].
@@ -1169,7 +1515,11 @@ __global__ void export_kernel(const __grid_constant__ StepParams p, const void* 
   const long long o = (long long)y * p.nx + x;
   const long long nn = (long long)p.nx * p.ny;
 #pragma unroll
-  for (int a = 0; a < 9; ++a) f[a * nn + o] = S::to_f64(src + a * p.plane + i, a);
+  for (int a = 0; a < 9; ++a) {
+    const typename S::E e = fstar_e<S>(p, src, a, x, y);
+    f[a * nn + o] = S::to_f64(&e, a);
+  }
+  (void)i;
 }
 
 template <int STORE>
@@ -1183,7 +1533,10 @@ __global__ void import_kernel(const __grid_constant__ StepParams p, void* dstv, 
   const long long o = (long long)y * p.nx + x;
   const long long nn = (long long)p.nx * p.ny;
 #pragma unroll
-  for (int a = 0; a < 9; ++a) S::from_f64(dst + a * p.plane + i, f[a * nn + o], a);
+  for (int a = 0; a < 9; ++a) {
+    const int slot = p.mode == kModeAB ? a : opposite(a);  // in place: before a push step
+    S::from_f64(dst + slot * p.plane + i, f[a * nn + o], a);
+  }
 }
 
 }  // namespace vplbm

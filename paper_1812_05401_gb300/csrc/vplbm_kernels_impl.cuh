@@ -28,7 +28,11 @@ static cudaError_t allow_tma_smem() {
 
 template <int COLL>
 static cudaError_t launch_fused_coll(const StepParams& p, cudaStream_t st) {
-  if (p.use_tma) {
+  if (p.mode == kModeAAPush) {
+    fused_step_kernel<VPLBM_STORE, COLL, false, kModeAAPush><<<p.n_tiles, dim3(kLanes, kWarps), 0, st>>>(p);
+  } else if (p.mode == kModeAALocal) {
+    fused_step_kernel<VPLBM_STORE, COLL, false, kModeAALocal><<<p.n_tiles, dim3(kLanes, kWarps), 0, st>>>(p);
+  } else if (p.use_tma) {
     const cudaError_t e = allow_tma_smem<COLL>();
     if (e != cudaSuccess) return e;
     fused_step_kernel<VPLBM_STORE, COLL, true>
@@ -44,15 +48,23 @@ cudaError_t VPLBM_FN(launch_fused_)(int coll, const StepParams& p, cudaStream_t 
 }
 
 cudaError_t VPLBM_FN(launch_group_)(const StepParams* d_params, const GroupTile* d_table,
-                                    int n_blocks, long long k, cudaStream_t st) {
+                                    int n_blocks, long long k, int mode, cudaStream_t st) {
   if (n_blocks <= 0) return cudaSuccess;
-  fused_group_kernel<VPLBM_STORE><<<n_blocks, dim3(kLanes, kWarps), 0, st>>>(d_params, d_table, k);
+  const dim3 blk(kLanes, kWarps);
+  if (mode == kModeAAPush)
+    fused_group_kernel<VPLBM_STORE, kModeAAPush><<<n_blocks, blk, 0, st>>>(d_params, d_table, k);
+  else if (mode == kModeAALocal)
+    fused_group_kernel<VPLBM_STORE, kModeAALocal><<<n_blocks, blk, 0, st>>>(d_params, d_table, k);
+  else
+    fused_group_kernel<VPLBM_STORE, kModeAB><<<n_blocks, blk, 0, st>>>(d_params, d_table, k);
   return cudaGetLastError();
 }
 
 cudaError_t VPLBM_FN(launch_moments_)(const StepParams& p, double* rho, double* ux, double* uy,
                                       cudaStream_t st) {
-  moments_kernel<VPLBM_STORE><<<node_grid(p), dim3(kBlockX, kBlockY), 0, st>>>(p, rho, ux, uy);
+  StepParams q = p;
+  q.ghost_dst = nullptr;  // read only: the outlet state is not advanced
+  moments_kernel<VPLBM_STORE><<<node_grid(q), dim3(kBlockX, kBlockY), 0, st>>>(q, rho, ux, uy);
   return cudaGetLastError();
 }
 
@@ -67,9 +79,9 @@ cudaError_t VPLBM_FN(launch_init_)(const StepParams& p, void* dst, const double*
   return cudaGetLastError();
 }
 
-cudaError_t VPLBM_FN(launch_ghost_init_)(const StepParams& p, const void* src, void* ghost,
+cudaError_t VPLBM_FN(launch_ghost_init_)(const StepParams& p, const void* src, void* ghost, void* z,
                                          cudaStream_t st) {
-  ghost_init_kernel<VPLBM_STORE><<<(3 * p.ny + 255) / 256, 256, 0, st>>>(p, src, ghost);
+  ghost_init_kernel<VPLBM_STORE><<<(3 * p.ny + 255) / 256, 256, 0, st>>>(p, src, ghost, z);
   return cudaGetLastError();
 }
 

@@ -11,7 +11,7 @@ namespace vplbm {
   cudaError_t launch_fused_##SUFFIX(int coll, const StepParams& p, cudaStream_t st);            \
   cudaError_t launch_group_##SUFFIX(const StepParams* d_params,                                 \
                                     const GroupTile* d_table, int n_blocks, long long k,         \
-                                    cudaStream_t st);                                           \
+                                    int mode, cudaStream_t st);                                 \
   cudaError_t launch_moments_##SUFFIX(const StepParams& p, double* rho, double* ux, double* uy, \
                                       cudaStream_t st);                                         \
   cudaError_t launch_momentum_exchange_##SUFFIX(const StepParams& p, const MeArgs& m,            \
@@ -19,7 +19,7 @@ namespace vplbm {
   cudaError_t launch_init_##SUFFIX(const StepParams& p, void* dst, const double* u, double rho0, \
                                    double u0x, double u0y, cudaStream_t st);                    \
   cudaError_t launch_ghost_init_##SUFFIX(const StepParams& p, const void* src, void* ghost,     \
-                                        cudaStream_t st);                                       \
+                                        void* z, cudaStream_t st);                              \
   cudaError_t launch_export_##SUFFIX(const StepParams& p, const void* src, double* f,           \
                                      cudaStream_t st);                                          \
   cudaError_t launch_import_##SUFFIX(const StepParams& p, void* dst, const double* f,           \

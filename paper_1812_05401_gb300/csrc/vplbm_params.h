@@ -10,6 +10,12 @@ namespace vplbm {
 enum { kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
 enum { kSrt = 0, kMrt = 1 };
 enum { kBcPeriodic = 0, kBcInletOutlet = 1, kBcFreeSlip = 2, kBcInletConvective = 3 };
+// Streaming schemes of the fused step: A/B buffers (pull from src, write dst),
+// or in-place AA-pattern streaming on one buffer, whose steps alternate
+// between a push step (pull from the opposite slots of the neighbours, push
+// to their own slots) and a local step (read own slots, write the opposite
+// slots of the same node).
+enum { kModeAB = 0, kModeAAPush = 1, kModeAALocal = 2 };
 
 constexpr int kMaxBodies = 8;
 // Fused-step tiles: a block is 8 warps; each warp covers one row segment of
@@ -68,6 +74,10 @@ struct StepParams {
   const void* us;           // static solid velocity, float2/double2 [ny][pitch], or null
   const void* ghost_src;    // convective outlet state g^{t-1}: [3][ny] of the arithmetic
   void* ghost_dst;          // type (offsets, rows alpha = 3, 6, 7); g^t goes to ghost_dst
+  int mode;                 // kModeAB | kModeAAPush | kModeAALocal
+  void* z;                  // AA, open outlet: stored f*(nx-1) of alpha = 3, 6, 7 ([3][ny])
+  void* lost;               // AA, open x sides: values a push step sends out of the grid,
+                            // [2][3][ny]: x = nx-1 alpha = 1, 5, 8; x = 0 alpha = 3, 6, 7
   int nx, ny, pitch;
   int bc_x, bc_y;
   int tiles_x, n_tiles;

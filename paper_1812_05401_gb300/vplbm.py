@@ -25,6 +25,7 @@ VPLBM_ERR_DIVERGED, VPLBM_ERR_TIMEOUT, VPLBM_ERR_STATE = 4, 5, 6
 VPLBM_SRT, VPLBM_MRT = 0, 1
 VPLBM_F64, VPLBM_F32, VPLBM_F16_OFFSET, VPLBM_BF16_OFFSET = 0, 1, 2, 3
 VPLBM_BC_PERIODIC, VPLBM_BC_INLET_OUTLET, VPLBM_BC_FREE_SLIP, VPLBM_BC_INLET_CONVECTIVE = 0, 1, 2, 3
+VPLBM_STREAM_AB, VPLBM_STREAM_AA = 0, 1
 VPLBM_MAX_BODIES = 8
 VPLBM_ROUND_NEAREST, VPLBM_ROUND_STOCHASTIC = 0, 1
 
@@ -47,7 +48,7 @@ class vplbm_config(C.Structure):
                 ("u_in", C.c_double * 2), ("rho0", C.c_double), ("u0", C.c_double * 2),
                 ("body_force", C.c_double * 2), ("rates", C.c_double * 9),
                 ("force_ring_len", C.c_int32), ("rounding", C.c_int32), ("stream", C.c_void_p),
-                ("u_conv", C.c_double)]
+                ("u_conv", C.c_double), ("streaming", C.c_int32), ("reserved", C.c_int32)]
 
 
 class VplbmError(RuntimeError):
@@ -322,7 +323,7 @@ def vplbm_destroy(h):
 def make_config(nx, ny, collision="srt", storage="f32", tau=0.8, lam=3.0 / 16.0, eta=1e-7,
                 bc="periodic", u_in=(0.0, 0.0), u0=(0.0, 0.0), rho0=1.0, body_force=(0.0, 0.0),
                 rates=None, reduce_mass=True, ring_len=4096, stream=None,
-                rounding="stochastic", u_conv=None) -> vplbm_config:
+                rounding="stochastic", u_conv=None, streaming="ab") -> vplbm_config:
     """bc: "periodic", "channel" (inlet, zero-gradient outlet, free-slip walls),
     "channel-convective" (the same with the convective outlet; U_c = u_conv,
     by default the inlet speed), or a (bc_x, bc_y) pair."""
@@ -339,6 +340,8 @@ def make_config(nx, ny, collision="srt", storage="f32", tau=0.8, lam=3.0 / 16.0,
     else:
         c.bc_x, c.bc_y = bc
     c.u_conv = float(u_in[0] if u_conv is None else u_conv)
+    c.streaming = {"ab": VPLBM_STREAM_AB, "aa": VPLBM_STREAM_AA}[streaming] \
+        if isinstance(streaming, str) else int(streaming)
     c.tau, c.lam, c.eta = tau, lam, eta
     c.u_in[0], c.u_in[1] = u_in
     c.u0[0], c.u0[1] = u0
@@ -358,14 +361,15 @@ def make_config(nx, ny, collision="srt", storage="f32", tau=0.8, lam=3.0 / 16.0,
 
 
 def config_from_workload(w, ring_len: int = 4096, stream=None, reduce_mass: bool = True,
-                         rounding: str = "stochastic"):
+                         rounding: str = "stochastic", streaming: str = "ab"):
     """vplbm_config and body list for an inputs.Workload (tau from its
     Reynolds number when it gives one)."""
     tau = w.tau if w.tau is not None else vplbm_tau_from_reynolds(w.u_ref, w.l_ref, w.re)
     u_in = (w.u_ref, 0.0) if w.bc == "channel" else (0.0, 0.0)
     bc = "channel-convective" if w.bc == "channel" and w.outlet == "convective" else w.bc
     cfg = make_config(w.nx, w.ny, w.collision, w.storage, tau, w.lam, bc=bc, u_in=u_in,
-                      ring_len=ring_len, stream=stream, reduce_mass=reduce_mass, rounding=rounding)
+                      ring_len=ring_len, stream=stream, reduce_mass=reduce_mass, rounding=rounding,
+                      streaming=streaming)
     return cfg, list(w.bodies)
 
 
@@ -392,10 +396,10 @@ class Solver:
     @classmethod
     def from_workload(cls, w, stream=None, ring_len: int = 4096, reduce_mass: bool = True,
                       with_initial_velocity: bool = True, rounding: str = "stochastic",
-                      device_init: bool = False):
+                      device_init: bool = False, streaming: str = "ab"):
         """device_init: generate the workload's seeded initial field on the
         device (bit-identical to w.initial_velocity())."""
-        cfg, bodies = config_from_workload(w, ring_len, stream, reduce_mass, rounding)
+        cfg, bodies = config_from_workload(w, ring_len, stream, reduce_mass, rounding, streaming)
         if not with_initial_velocity:
             return cls(cfg, bodies)
         if device_init:

@@ -50,13 +50,22 @@ def test_host_helpers(lib):
     assert V.vplbm_footprint_bytes(c16) < 0.55 * fp
     bad = V.make_config(0, 10)
     assert V.vplbm_footprint_bytes(bad) == 0
+    # in-place streaming keeps one population buffer (plus 9 values per row
+    # of side state at open x sides)
+    ab = V.make_config(16384, 4096, "mrt", "f32", 0.6, bc="channel")
+    aa = V.make_config(16384, 4096, "mrt", "f32", 0.6, bc="channel", streaming="aa")
+    fab, faa = V.vplbm_footprint_bytes(ab), V.vplbm_footprint_bytes(aa)
+    assert fab - faa == 9 * 16384 * 4096 * 4 - 9 * 4096 * 4
+    assert faa < 0.55 * fab
     assert V.lib().vplbm_status_string(4) == b"diverged"
 
 
 def test_invalid_configs_rejected_without_gpu(lib):
     from paper_1812_05401_gb300 import vplbm as V
     for kw in (dict(nx=0, ny=4), dict(nx=4, ny=4, tau=0.5), dict(nx=4, ny=4, eta=0.0),
-               dict(nx=4, ny=4, storage=7), dict(nx=4, ny=4, ring_len=0)):
+               dict(nx=4, ny=4, storage=7), dict(nx=4, ny=4, ring_len=0),
+               dict(nx=4, ny=4, streaming=2), dict(nx=4, ny=4, bc=(3, 2), u_in=(0.05, 0.0),
+                                                   u_conv=-1.0)):
         nx, ny = kw.pop("nx"), kw.pop("ny")
         c = V.make_config(nx, ny, **kw)
         with pytest.raises(V.VplbmError) as e:
