@@ -169,6 +169,43 @@ def make_workload(name: str, storage: str):
 # CPU baseline: the FP64 oracle on a bounded sample of the workload
 # -----------------------------------------------------------------------------
 
+def oracle_rates(budget_s: float = 8.0):
+    """The FP64 oracle's rate on the host cores for each configuration at its
+    full grid size (C1 Couette, C2 and C3 cylinders, C5 moving cylinder), with
+    one thread and with every core: a timed sample of up to budget_s seconds
+    per measurement (after one untimed step). Prints one JSON line."""
+    import oracle as O
+    from paper_1812_05401_gb300 import inputs as I
+    out = {"kind": "oracle", "nproc": os.cpu_count(), "budget_s_per_rate": budget_s, "configs": {}}
+    for name, w in (("C1", I.c1_circular_couette()), ("C2", I.c2_cylinder_re100()),
+                    ("C3", I.c3_cylinder_re1000("f32")), ("C5", I.c5_moving_cylinder("f32"))):
+        tau = O.tau_from_reynolds(w.u_ref, w.l_ref, w.re) if w.re else w.tau
+        chan = w.bc == "channel"
+        cfg = O.Config(nx=w.nx, ny=w.ny, collision=O.MRT if w.collision == "mrt" else O.SRT,
+                       tau=tau, lam=w.lam, bc_x=O.BC_INLET_OUTLET if chan else O.BC_PERIODIC,
+                       bc_y=O.BC_FREE_SLIP if chan else O.BC_PERIODIC,
+                       u_in=(w.u_ref, 0.0) if chan else (0.0, 0.0),
+                       bodies=[O.Body(b.cx, b.cy, b.radius, b.amp_x, b.amp_y, b.period, b.omega,
+                                      b.outside) for b in w.bodies])
+        f = O.init_equilibrium(cfg, 1.0, None)
+        rates = {}
+        for threads in (1, 0):
+            O.set_num_threads(threads)
+            O.run(cfg, f, 1)
+            steps, t0 = 0, time.perf_counter()
+            while time.perf_counter() - t0 < budget_s:
+                O.run(cfg, f, 1, t0=steps + 1)
+                steps += 1
+            dt = time.perf_counter() - t0
+            rates["1_thread" if threads == 1 else f"{O.num_threads()}_threads"] = {
+                "mlups": round(w.nx * w.ny * steps / dt / 1e6, 3), "steps": steps,
+                "seconds": round(dt, 2)}
+        O.set_num_threads(0)
+        out["configs"][name] = {"workload": w.name, "nodes": w.nx * w.ny, **rates}
+        del f
+    print(json.dumps(out), flush=True)
+
+
 def oracle_sample(w, budget_s: float = 12.0, max_steps: int = 50):
     """Runs the FP64 oracle on a window of the workload's grid: rows around the
     body (at most 1024) and the first half of the columns (at most 8192), same
@@ -501,6 +538,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=90.0,
                     help="reference arm: seconds of oracle work for the warm-up and timed steps")
     ap.add_argument("--serving", action="store_true", help="run only the serving mix")
+    ap.add_argument("--oracle-rates", action="store_true",
+                    help="time the FP64 oracle (CPU baseline) on every configuration, 1 thread and all cores")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-rate", type=float, default=0.0)
     ap.add_argument("--serve-slots", type=int, default=256)
@@ -513,7 +552,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.oracle_rates:
+        oracle_rates()
+    elif args.impl == "reference":
         run_reference(args)
     else:
         from paper_1812_05401_gb300 import build as B

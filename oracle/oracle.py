@@ -85,6 +85,8 @@ def lib():
             L.orc_run.argtypes = [cp, dp, C.c_int64, C.c_int64, dp, dp, dp]
             L.orc_moments.argtypes = [cp, dp, C.c_int64, dp, dp, dp]
             L.orc_num_threads.restype = C.c_int
+            L.orc_set_num_threads.argtypes = [C.c_int]
+            L.orc_set_num_threads.restype = None
             L.orc_momentum_exchange.argtypes = [cp, dp, C.c_int64, dp, dp]
             L.orc_momentum_exchange.restype = C.c_int
             for name in ("orc_mask", "orc_init_equilibrium", "orc_run", "orc_moments"):
@@ -306,6 +308,11 @@ def outlet_from_store(f: np.ndarray) -> np.ndarray:
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's row loop; n <= 0 restores all processors."""
+    lib().orc_set_num_threads(int(n))
 
 
 def tau_from_reynolds(u_ref: float, l_ref: float, re: float) -> float:

@@ -641,6 +641,14 @@ int orc_momentum_exchange(const orc_config* c, const double* f, int64_t t, doubl
   return 0;
 }
 
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+  (void)n;
+#endif
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -118,6 +118,8 @@ int orc_moments(const orc_config* c, const double* f, int64_t t,
  * counted. */
 int orc_momentum_exchange(const orc_config* c, const double* f, int64_t t, double* fx, double* fy);
 
+/* Host threads of the row loop (OpenMP builds); n <= 0: all processors. */
+void orc_set_num_threads(int n);
 int orc_num_threads(void);
 
 #ifdef __cplusplus
