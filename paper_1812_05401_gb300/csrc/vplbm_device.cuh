@@ -1106,12 +1106,16 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
         }
       }
     } else {  // push step
+      // vector pushes wherever every target of the row lies in the grid: all
+      // of an interior tile, and the rows of a boundary tile that touches
+      // neither x side nor the first or last row (warp-uniform)
+      const bool vec = !GEN || (x0 >= 1 && x0 + TX <= p.nx - 1 && y >= 1 && y <= p.ny - 2);
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
         typename S::R e[N];
 #pragma unroll
         for (int k = 0; k < N; ++k) e[k] = S::round_e(h[k][a], a, nb[k], sr);
-        if (!GEN) {
+        if (vec) {
           push_dir_vec<S, N>(p, buf, a, xb, y, lane, e);
         } else {
 #pragma unroll
