@@ -65,7 +65,9 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = build()
+            # VPLBM_ORACLE_LIB: load another build of this source instead (the
+            # mutation test points it at deliberately broken copies)
+            path = os.environ.get("VPLBM_ORACLE_LIB") or build()
             L = C.CDLL(path)
             dp = C.POINTER(C.c_double)
             cp = C.POINTER(OrcConfig)
