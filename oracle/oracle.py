@@ -90,6 +90,10 @@ def lib():
             L.orc_set_num_threads.argtypes = [C.c_int]
             L.orc_set_num_threads.restype = None
             L.orc_momentum_exchange.argtypes = [cp, dp, C.c_int64, dp, dp]
+            ip = C.POINTER(C.c_int32)
+            L.orc_step_nodes.argtypes = [cp, dp, C.c_int64, C.c_int64, ip, ip, dp, dp, dp,
+                                         C.POINTER(C.c_uint8)]
+            L.orc_step_nodes.restype = C.c_int
             L.orc_momentum_exchange.restype = C.c_int
             for name in ("orc_mask", "orc_init_equilibrium", "orc_run", "orc_moments"):
                 getattr(L, name).restype = C.c_int
@@ -300,6 +304,23 @@ def momentum_exchange(cfg: Config, f: np.ndarray, t: int = 0):
     rc = lib().orc_momentum_exchange(C.byref(s), _dp(f), t, C.byref(fx), C.byref(fy))
     assert rc == 0
     return fx.value, fy.value
+
+
+def step_nodes(cfg: Config, f: np.ndarray, t: int, xs, ys):
+    """One step (index t) of the listed nodes from the store f*(t):
+    (f*(t+1) [n][9], fpx [n], fpy [n], chi [n])."""
+    s, keep = cfg.c_struct()
+    assert f.dtype == np.float64 and f.flags.c_contiguous and f.shape == (9, cfg.ny, cfg.nx)
+    xs = np.ascontiguousarray(xs, dtype=np.int32)
+    ys = np.ascontiguousarray(ys, dtype=np.int32)
+    n = xs.size
+    fout = np.zeros((n, 9))
+    fpx, fpy, chi = np.zeros(n), np.zeros(n), np.zeros(n, np.uint8)
+    ip = C.POINTER(C.c_int32)
+    rc = lib().orc_step_nodes(C.byref(s), _dp(f), t, n, xs.ctypes.data_as(ip), ys.ctypes.data_as(ip),
+                              _dp(fout), _dp(fpx), _dp(fpy), chi.ctypes.data_as(C.POINTER(C.c_uint8)))
+    assert rc == 0, rc
+    return fout, fpx, fpy, chi
 
 
 def outlet_from_store(f: np.ndarray) -> np.ndarray:

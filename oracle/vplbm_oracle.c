@@ -367,43 +367,63 @@ static void body_state(const orc_body* b, int64_t t, double* cx, double* cy,
   }
 }
 
-int orc_mask(const orc_config* c, int64_t t, uint8_t* chi, double* us) {
-  const int nx = c->nx, ny = c->ny;
-  const size_t plane = (size_t)nx * (size_t)ny;
+/* Mask and solid velocity of node (x, y), given the body states st (centre
+ * x, y and velocity x, y of each body at the time of the step): the static
+ * mask first, then the first body whose shape holds the node. */
+static int node_mask(const orc_config* c, const double* st, int x, int y, double* usx,
+                     double* usy) {
+  const size_t plane = (size_t)c->nx * (size_t)c->ny;
+  size_t i = (size_t)y * c->nx + x;
+  int solid = 0;
+  double sx = 0.0, sy = 0.0;
+  if (c->chi && c->chi[i]) {
+    solid = 1;
+    if (c->us) {
+      sx = c->us[i];
+      sy = c->us[plane + i];
+    }
+  } else {
+    for (int b = 0; b < c->n_bodies; ++b) {
+      const orc_body* bd = &c->bodies[b];
+      double dx = (double)x - st[4 * b];
+      double dy = (double)y - st[4 * b + 1];
+      double r2 = dx * dx + dy * dy;
+      double R2 = bd->radius * bd->radius;
+      int in = bd->outside ? (r2 >= R2) : (r2 <= R2);
+      if (in) {
+        solid = 1;
+        sx = st[4 * b + 2] - bd->omega * dy;
+        sy = st[4 * b + 3] + bd->omega * dx;
+        break;
+      }
+    }
+  }
+  *usx = sx;
+  *usy = sy;
+  return solid;
+}
+
+/* Body states at step index t: [n_bodies][4] (centre x, y, velocity x, y). */
+static double* body_states(const orc_config* c, int64_t t) {
   int nb = c->n_bodies;
   double* st = (double*)malloc(sizeof(double) * 4 * (size_t)(nb > 0 ? nb : 1));
-  if (!st) return 2;
+  if (!st) return NULL;
   for (int b = 0; b < nb; ++b)
     body_state(&c->bodies[b], t, &st[4 * b], &st[4 * b + 1], &st[4 * b + 2],
                &st[4 * b + 3]);
+  return st;
+}
+
+int orc_mask(const orc_config* c, int64_t t, uint8_t* chi, double* us) {
+  const int nx = c->nx, ny = c->ny;
+  const size_t plane = (size_t)nx * (size_t)ny;
+  double* st = body_states(c, t);
+  if (!st) return 2;
   for (int y = 0; y < ny; ++y) {
     for (int x = 0; x < nx; ++x) {
       size_t i = (size_t)y * nx + x;
-      int solid = 0;
-      double sx = 0.0, sy = 0.0;
-      if (c->chi && c->chi[i]) {
-        solid = 1;
-        if (c->us) {
-          sx = c->us[i];
-          sy = c->us[plane + i];
-        }
-      } else {
-        for (int b = 0; b < nb; ++b) {
-          const orc_body* bd = &c->bodies[b];
-          double dx = (double)x - st[4 * b];
-          double dy = (double)y - st[4 * b + 1];
-          double r2 = dx * dx + dy * dy;
-          double R2 = bd->radius * bd->radius;
-          int in = bd->outside ? (r2 >= R2) : (r2 <= R2);
-          if (in) {
-            solid = 1;
-            sx = st[4 * b + 2] - bd->omega * dy;
-            sy = st[4 * b + 3] + bd->omega * dx;
-            break;
-          }
-        }
-      }
-      chi[i] = (uint8_t)solid;
+      double sx, sy;
+      chi[i] = (uint8_t)node_mask(c, st, x, y, &sx, &sy);
       if (us) {
         us[i] = sx;
         us[plane + i] = sy;
@@ -597,6 +617,44 @@ int orc_moments(const orc_config* c, const double* f, int64_t t, double* rho,
   }
   free(chi);
   free(us);
+  free(ghost);
+  return 0;
+}
+
+int orc_step_nodes(const orc_config* c, const double* f, int64_t t, int64_t n,
+                   const int32_t* xs, const int32_t* ys, double* fout, double* fpx, double* fpy,
+                   uint8_t* chi) {
+  const int ny = c->ny;
+  double* st = body_states(c, t);
+  double* ghost = (double*)calloc(9 * (size_t)ny, sizeof(double));
+  if (!st || !ghost) {
+    free(st);
+    free(ghost);
+    return 2;
+  }
+  orc_model m;
+  model_init(c, &m);
+  if (outlet_advance(c, f, ghost) != 0) { /* the state itself is not advanced */
+    free(st);
+    free(ghost);
+    return 1;
+  }
+  for (int64_t k = 0; k < n; ++k) {
+    const int x = xs[k], y = ys[k];
+    if (x < 0 || x >= c->nx || y < 0 || y >= ny) {
+      free(st);
+      free(ghost);
+      return 1;
+    }
+    double usx, usy, fl[9], px, py;
+    const int solid = node_mask(c, st, x, y, &usx, &usy);
+    for (int a = 0; a < 9; ++a) fl[a] = pull_one(&m, c, f, ghost, a, x, y);
+    collide(&m, c, fl, solid, usx, usy, fout + 9 * (size_t)k, &px, &py);
+    if (fpx) fpx[k] = px;
+    if (fpy) fpy[k] = py;
+    if (chi) chi[k] = (uint8_t)solid;
+  }
+  free(st);
   free(ghost);
   return 0;
 }

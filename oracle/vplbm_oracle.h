@@ -110,6 +110,16 @@ int orc_run(const orc_config* c, double* f, int64_t t0, int64_t n,
 int orc_moments(const orc_config* c, const double* f, int64_t t,
                 double* rho, double* ux, double* uy);
 
+/* One step (index t) of the listed nodes only, from the store f*(t): the pull
+ * with the boundary rules of orc_run (convective state read, not advanced),
+ * the mask of step t and the collision. fout [n][9] receives f*(t+1) of each
+ * node, fpx/fpy its penalization force and chi its mask (any may be NULL
+ * except fout). The same arithmetic as orc_run, node by node, so that a step
+ * of a grid too large for the oracle can be checked at sampled nodes. */
+int orc_step_nodes(const orc_config* c, const double* f, int64_t t, int64_t n,
+                   const int32_t* xs, const int32_t* ys, double* fout, double* fpx, double* fpy,
+                   uint8_t* chi);
+
 /* Momentum-exchange force on the solids at step index t (the force measure of
  * Section 3.3, after Ladd): over every link from a fluid node x_f to a solid
  * node x_s = x_f + xi_alpha, the momentum xi_alpha [f*_alpha(x_f) +

@@ -667,3 +667,35 @@ def test_convective_outlet_frozen_when_uc_zero():
     keep = state.copy()
     O.run(cfg, f, 4)
     assert np.array_equal(cfg.outlet, keep)
+
+
+@pytest.mark.parametrize("bcs", [(O.BC_PERIODIC, O.BC_PERIODIC), (O.BC_INLET_OUTLET, O.BC_FREE_SLIP),
+                                 (O.BC_INLET_CONVECTIVE, O.BC_PERIODIC)])
+def test_step_nodes_equals_a_grid_step(bcs):
+    """The node-by-node step (for sampled checks of grids too large for the
+    oracle) gives, at every node, bitwise the populations and penalization
+    force of a whole-grid step: mask, bodies, boundaries and outlet state
+    included."""
+    nx, ny = 23, 17
+    chi = I.random_mask(nx, ny, 71, 0.1)
+    us = I.random_solid_velocity(nx, ny, 72, 0.03)
+    cfg = O.Config(nx=nx, ny=ny, collision=O.MRT, tau=0.6, bc_x=bcs[0], bc_y=bcs[1],
+                   u_in=(0.04, 0.0), g=(1e-6, 2e-6), chi=chi, us=us, u_conv=0.05,
+                   bodies=[O.Body(12.0, 8.5, 4.0, amp_y=2.0, period=50.0, omega=0.01)])
+    f = I.random_populations(nx, ny, 73, 0.05)
+    if bcs[0] == O.BC_INLET_CONVECTIVE:
+        cfg.outlet = O.outlet_from_store(f) * 1.01
+    t = 7
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    keep = None if cfg.outlet is None else cfg.outlet.copy()
+    fout, fpx, fpy, mk = O.step_nodes(cfg, f, t, xx.ravel(), yy.ravel())
+    if keep is not None:
+        assert np.array_equal(cfg.outlet, keep)  # read, not advanced
+    ref = f.copy()
+    fx, fy, _ = O.run(cfg, ref, 1, t0=t)
+    assert np.array_equal(fout.T.reshape(9, ny, nx), ref)
+    chi_t, _ = O.mask(cfg, t)
+    assert np.array_equal(mk.reshape(ny, nx), chi_t)
+    solid = mk.astype(bool)
+    np.testing.assert_allclose(-fpx[solid].sum(), fx[0], rtol=1e-13, atol=1e-16)
+    np.testing.assert_allclose(-fpy[solid].sum(), fy[0], rtol=1e-13, atol=1e-16)
