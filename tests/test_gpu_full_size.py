@@ -1,0 +1,143 @@
+"""Parity at the benchmark's full size, in the configuration the benchmark
+times: the 16384 x 4096 moving-cylinder channel (67.1M nodes, MRT), built and
+stepped exactly as bench.py builds and steps it.
+
+The oracle cannot run this grid, so it checks sampled outputs node by node
+(orc_step_nodes: the oracle's pull with every boundary rule, mask and
+collision for the listed nodes, from the GPU's own stored f*(t)): random
+nodes, every kind of boundary node, tile-border nodes, the ring around the
+moving body, and every solid node for the force record of the step.
+Tolerances: FP32 storage 4e-7 on one step's populations (FP32 arithmetic on
+values <= 0.5); FP16 offsets (stochastically rounded) one rounding step of
+each offset's own binade plus FP32 arithmetic; the force within 2e-5 relative
+(FP32 node forces summed in FP64).
+The in-place scheme is bitwise the A/B scheme at this size as well.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1812_05401_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+V = None
+WARMUP = 5  # bench.py's default warm-up steps: the checked step is step index 5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    global V
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1812_05401_gb300 import build as B
+    B.build()
+    from paper_1812_05401_gb300 import vplbm
+    V = vplbm
+    yield
+
+
+def _oracle_config(w, cfg):
+    return O.Config(nx=w.nx, ny=w.ny, collision=O.MRT if w.collision == "mrt" else O.SRT,
+                    tau=cfg.tau, lam=cfg.lam, eta=cfg.eta, bc_x=O.BC_INLET_OUTLET,
+                    bc_y=O.BC_FREE_SLIP, u_in=(cfg.u_in[0], cfg.u_in[1]),
+                    bodies=[O.Body(b.cx, b.cy, b.radius, b.amp_x, b.amp_y, b.period, b.omega,
+                                   b.outside) for b in w.bodies])
+
+
+def _export(torch, s, nx, ny):
+    f = torch.empty((9, ny, nx), dtype=torch.float64, device="cuda")
+    V.vplbm_populations(s.h, f, on_device=True)
+    s.synchronize()
+    return f
+
+
+def _sample(w, t):
+    """Sampled nodes: random, boundary, tile borders, ring around the body."""
+    nx, ny = w.nx, w.ny
+    rng = np.random.default_rng(20240)
+    xs = [rng.integers(0, nx, 4096)]
+    ys = [rng.integers(0, ny, 4096)]
+    edge = rng.integers(0, max(nx, ny), 512)
+    xs += [np.zeros(256, int), np.full(256, nx - 1), edge[:256] % nx, edge[256:] % nx]
+    ys += [edge[:256] % ny, edge[256:] % ny, np.zeros(256, int), np.full(256, ny - 1)]
+    xs.append(np.array([0, 0, nx - 1, nx - 1]))
+    ys.append(np.array([0, ny - 1, 0, ny - 1]))
+    tb = rng.integers(1, nx // 128, 512) * 128 + rng.integers(-1, 1, 512)  # tile borders
+    xs.append(tb)
+    ys.append(rng.integers(0, ny, 512))
+    b = w.bodies[0]
+    cy = b.cy + b.amp_y * np.sin(2 * np.pi * t / b.period)
+    th = np.linspace(0.0, 2 * np.pi, 2400, endpoint=False)
+    for dr in (-1.5, -0.5, 0.5, 1.5):
+        xs.append(np.rint(b.cx + (b.radius + dr) * np.cos(th)).astype(int))
+        ys.append(np.rint(cy + (b.radius + dr) * np.sin(th)).astype(int))
+    x, y = np.concatenate(xs), np.concatenate(ys)
+    ok = (x >= 0) & (x < nx) & (y >= 0) & (y < ny)
+    return x[ok], y[ok]
+
+
+def _solid_nodes(w, t):
+    b = w.bodies[0]
+    cy = b.cy + b.amp_y * np.sin(2 * np.pi * t / b.period)
+    r = int(np.ceil(b.radius)) + 2
+    yy, xx = np.mgrid[int(cy) - r:int(cy) + r + 2, int(b.cx) - r:int(b.cx) + r + 2]
+    return xx.ravel(), yy.ravel()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_bench_workload_sampled_against_oracle(storage):
+    import torch
+    w = I.c5_moving_cylinder(storage)
+    nx, ny = w.nx, w.ny
+    with V.Solver.from_workload(w, ring_len=4096) as s:
+        cfg, _ = V.config_from_workload(w)
+        s.step(WARMUP)
+        f_t = _export(torch, s, nx, ny)
+        s.step(1)
+        fx, fy, _ = s.forces()
+        f_t1 = _export(torch, s, nx, ny)
+    t = WARMUP
+    ocfg = _oracle_config(w, cfg)
+    f_host = f_t.cpu().numpy()
+    del f_t
+    x, y = _sample(w, t)
+    ref, _, _, _ = O.step_nodes(ocfg, f_host, t, x, y)
+    xi = torch.as_tensor(x, device="cuda")
+    yi = torch.as_tensor(y, device="cuda")
+    got = f_t1[:, yi, xi].T.cpu().numpy()
+    err = np.abs(got - ref)
+    if storage == "f32":
+        assert err.max() < 4e-7, err.max()
+    else:
+        # stochastic FP16 rounding of the offset h = f - w: less than one
+        # rounding step of the binade of h (10 stored bits), plus FP32 arithmetic
+        h = np.abs(ref - O.weights()[None, :])
+        step = 2.0 ** (np.floor(np.log2(np.maximum(h, 2.0 ** -14))) - 10)
+        assert (err < step + 2e-6).all(), (err.max(), (err - step).max())
+        assert h.max() < 0.5
+    # the step's force record against the oracle's node forces over every solid node
+    sx, sy = _solid_nodes(w, t)
+    _, fpx, fpy, chi = O.step_nodes(ocfg, f_host, t, sx, sy)
+    solid = chi.astype(bool)
+    assert solid.sum() > 50_000
+    ex, ey = -fpx[solid].sum(), -fpy[solid].sum()
+    assert fx[-1] == pytest.approx(ex, rel=2e-5)
+    assert fy[-1] == pytest.approx(ey, rel=2e-5, abs=2e-5 * abs(ex))
+
+
+def test_bench_workload_in_place_bitwise():
+    """The in-place side measurement's solver against the A/B one after an
+    odd and an even number of steps (a push step and a local step last)."""
+    import torch
+    w = I.c5_moving_cylinder("f32")
+    with V.Solver.from_workload(w, ring_len=64) as a, \
+            V.Solver.from_workload(w, ring_len=64, streaming="aa") as b:
+        for n in (WARMUP, 1):
+            a.step(n)
+            b.step(n)
+            assert torch.equal(_export(torch, a, w.nx, w.ny), _export(torch, b, w.nx, w.ny))
+            fa, fb = a.forces(), b.forces()
+            for u, v in zip(fa, fb):
+                assert np.array_equal(u, v)
