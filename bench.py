@@ -421,18 +421,58 @@ def run_gpu(args):
 def run_serving_passes(args):
     """Closed-loop capacity, then Poisson arrivals at 0.8 x capacity, for the
     mixed storage and for all-FP32 and all-FP16 requests."""
-    out = {}
+    out, served = {}, {}
     for st in (None, "f32", "f16"):
-        cap = run_serving(args, rate=0.0, storage=st, quiet=True)
+        cap, res = run_serving(args, rate=0.0, storage=st, quiet=True, want_results=True)
+        served[st] = res
         rate = round(0.8 * cap["solves_per_s"], 2)
         rep = run_serving(args, rate=rate, storage=st, quiet=True)
         out[st or "mixed"] = {"capacity_solves_per_s": cap["solves_per_s"], "capacity_mlups": cap["mlups"],
                               "at_0.8_capacity": rep}
+    out["fp16_vs_fp32_drag"] = drag_agreement(args, served["f32"], served["f16"])
     print(json.dumps({"metric": "served solves/s and p50/p99 latency (VP-LBM serving mix)",
                       "serving": out}), flush=True)
 
 
-def run_serving(args, n_requests=None, rate=None, storage=None, quiet=False):
+def drag_agreement(args, res32, res16):
+    """Mean drag coefficient (second half of each run) of every cylinder
+    request served with FP16-offset storage against the same request served
+    with FP32 storage; requests that diverged in either pass are left out.
+    Reported for all cylinder requests and for those below the onset of
+    vortex shedding (Re < 47), which reach a steady drag: a short run above
+    it averages over a wake whose shedding onset any perturbation -- rounding
+    noise of either storage included -- moves."""
+    import numpy as np
+
+    from paper_1812_05401_gb300 import diag
+    from paper_1812_05401_gb300 import inputs as I
+    reqs = {r.rid: r.workload for r in I.serving_mix(args.serve_requests, rate=1.0, seed=1234)}
+    a = {r.rid: r for r in res32 if not r.error}
+    b = {r.rid: r for r in res16 if not r.error}
+    rel, steady = [], []
+    for rid in sorted(set(a) & set(b)):
+        w = reqs[rid]
+        if "cylinder" not in w.name:
+            continue
+        cd = []
+        for r in (a[rid], b[rid]):
+            c, _ = diag.coefficients(r.fx, r.fy, w.u_ref, w.l_ref)
+            cd.append(float(np.mean(c[len(c) // 2:])))
+        d = abs(cd[1] - cd[0]) / abs(cd[0])
+        rel.append(d)
+        if w.re < 47.0:
+            steady.append(d)
+
+    def summary(x):
+        x = np.array(x)
+        if x.size == 0:
+            return {"requests": 0}
+        return {"requests": int(x.size), "cd_rel_diff_median": float(np.median(x)),
+                "cd_rel_diff_max": float(x.max()), "within_1e-3": int((x <= 1e-3).sum())}
+    return {"steady_re_below_47": summary(steady), "all_cylinder_requests": summary(rel)}
+
+
+def run_serving(args, n_requests=None, rate=None, storage=None, quiet=False, want_results=False):
     """The serving mix (Poisson arrivals; Couette or cylinder channel 50/50;
     side log-uniform in 64..1024; Re in 20..500; SRT/MRT 50/50; 2000..20000
     steps; FP32 or FP16-offset storage) through the continuous-batching
@@ -458,7 +498,7 @@ def run_serving(args, n_requests=None, rate=None, storage=None, quiet=False):
                 "rejected": len(srv.rejected)})
     if not quiet:
         print(json.dumps({"metric": "served solves/s (VP-LBM serving mix)", "serving": rep}), flush=True)
-    return rep
+    return (rep, results) if want_results else rep
 
 
 def run_reference(args):

@@ -187,8 +187,11 @@ def serving_mix(n_requests: int = 256, rate: float = 4.0, seed: int = 1234,
     Couette or cylinder channel 50/50; square side log-uniform in
     [side_min, side_max] (channels are 4 side x side); Re uniform in [20, 500];
     SRT or MRT 50/50; steps uniform in [steps_min, steps_max]; storage f32 or
-    f16 50/50 unless fixed. The reference speed is kept at or below
-    Re nu_min / L so that the relaxation time stays away from 1/2."""
+    f16 50/50 unless fixed. Each request runs at the largest lattice speed
+    (0.01 for Couette, 0.05 for channels) with its relaxation time from Re, and
+    never below tau_min = 1/2 + 3 nu_min: a grid too coarse for the requested
+    Re at tau_min runs at the highest Re it resolves (U L / nu_min), which is
+    recorded in the workload."""
     r = uniform01(seed, 8 * n_requests).reshape(n_requests, 8)
     reqs = []
     t = 0.0
@@ -202,13 +205,15 @@ def serving_mix(n_requests: int = 256, rate: float = 4.0, seed: int = 1234,
         if r[i, 6] < 0.5:
             r1, r2 = 0.1875 * side, 0.4375 * side
             lref = r2 - r1
-            u = min(0.01, re * nu_min / lref)
+            u = 0.01
+            re = min(re, u * lref / nu_min)
             w = circular_couette(side, r1, r2, u, 0.8, steps, coll, st)
             w.tau = None
             w.re = re
         else:
             d = max(4.0, round(40.0 * side / 256.0))
-            u = min(0.05, re * nu_min / d)
+            u = 0.05
+            re = min(re, u * d / nu_min)
             w = cylinder_channel(4 * side, side, d, u, re, steps, collision=coll, storage=st,
                                  perturbation=1e-4, seed=seed + i)
         w.name = f"req{i}-" + w.name
