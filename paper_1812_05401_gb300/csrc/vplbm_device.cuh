@@ -715,21 +715,23 @@ __device__ __forceinline__ void pull_dir_vec(const StepParams& p, const typename
     for (int k = 0; k < N; ++k) h[k][A] = v[k];
   } else if (cx(A) == 1) {  // node k pulls from x - 1
     T left = __shfl_up_sync(0xffffffffu, v[N - 1], 1);
+    // the edge lanes' extra value: through the x boundary rules only where
+    // it lies outside the grid (the source row already carries the y rules)
     if (lane == 0)
-      left = GEN ? edge_pull<S, A, AA>(p, src, as, ys, xb - 1)
-                 : (AA ? S::in(row[xb - 1], A) : load_h<S>(row + xb - 1, A));
+      left = GEN && xb - 1 < 0 ? edge_pull<S, A, AA>(p, src, as, ys, xb - 1)
+                               : (AA ? S::in(row[xb - 1], A) : load_h<S>(row + xb - 1, A));
     h[0][A] = left;
 #pragma unroll
     for (int k = 1; k < N; ++k) h[k][A] = v[k - 1];
   } else {  // node k pulls from x + 1
     T right = __shfl_down_sync(0xffffffffu, v[0], 1);
     if (lane == kLanes - 1)
-      right = GEN ? edge_pull<S, A, AA>(p, src, as, ys, xb + N)
-                  : (AA ? S::in(row[xb + N], A) : load_h<S>(row + xb + N, A));
+      right = GEN && xb + N >= p.nx ? edge_pull<S, A, AA>(p, src, as, ys, xb + N)
+                                    : (AA ? S::in(row[xb + N], A) : load_h<S>(row + xb + N, A));
 #pragma unroll
     for (int k = 0; k < N - 1; ++k) h[k][A] = v[k + 1];
     h[N - 1][A] = right;
-    if (GEN) {
+    if (GEN && xb <= p.nx - 1 && xb + N > p.nx - 1) {
       // the domain's last column pulls from beyond it, through the x boundary
 #pragma unroll
       for (int k = 0; k < N; ++k)
