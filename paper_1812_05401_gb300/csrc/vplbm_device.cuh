@@ -55,8 +55,11 @@ template <> struct Store<kF64> {
   static __device__ __forceinline__ E out(T h, int a) { return h + wgt<T>(a); }
   static __device__ __forceinline__ double to_f64(const E* p, int) { return *p; }
   static __device__ __forceinline__ void from_f64(E* p, double f, int) { *p = f; }
-  // npt = 2 consecutive elements as one 16-byte access, as offsets h = f - w
-  static __device__ __forceinline__ void load_h_shared(const E* p, T h[2], int a) {
+  // npt = 2 consecutive elements as one 16-byte access, as offsets h = f - w.
+  // load_h_plain: a plain generic load, for shared memory (the TMA stages) and
+  // for a buffer the kernel also writes (the in-place steps); load_h takes the
+  // read-only data path.
+  static __device__ __forceinline__ void load_h_plain(const E* p, T h[2], int a) {
     const double2 v = *reinterpret_cast<const double2*>(p);
     h[0] = v.x - wgt<T>(a);
     h[1] = v.y - wgt<T>(a);
@@ -90,7 +93,7 @@ template <> struct Store<kF32> {
     *p = float(f - wgt<double>(a));
   }
   // npt = 4 consecutive elements as one 16-byte access
-  static __device__ __forceinline__ void load_h_shared(const E* p, T h[4], int) {
+  static __device__ __forceinline__ void load_h_plain(const E* p, T h[4], int) {
     const float4 v = *reinterpret_cast<const float4*>(p);
     h[0] = v.x;
     h[1] = v.y;
@@ -162,7 +165,7 @@ __device__ __forceinline__ float dither(float h, unsigned r) {
   return __uint_as_float(__float_as_uint(h) + (r >> (32 - DROP)));
 }
 template <> struct Store<kF16> : Store16<__half> {
-  static __device__ __forceinline__ void load_h_shared(const E* p, T h[4], int a) {
+  static __device__ __forceinline__ void load_h_plain(const E* p, T h[4], int a) {
     unpack(*reinterpret_cast<const uint2*>(p), h);
   }
   static __device__ __forceinline__ void load_h(const E* p, T h[4], int) {
@@ -205,7 +208,7 @@ template <> struct Store<kF16> : Store16<__half> {
   }
 };
 template <> struct Store<kBF16> : Store16<__nv_bfloat16> {
-  static __device__ __forceinline__ void load_h_shared(const E* p, T h[4], int) {
+  static __device__ __forceinline__ void load_h_plain(const E* p, T h[4], int) {
     unpack(*reinterpret_cast<const uint2*>(p), h);
   }
   static __device__ __forceinline__ void load_h(const E* p, T h[4], int) {
@@ -340,37 +343,20 @@ __device__ __forceinline__ typename S::T pull_bc(const StepParams& p, const type
   return load_h<S>(src + (long long)as * p.plane + (long long)ys * p.pitch + xs, A);
 }
 
-template <class S, int A>
-__device__ __forceinline__ typename S::T pull_interior(const StepParams& p,
-                                                       const typename S::E* src, long long i) {
-  return load_h<S>(src + (long long)A * p.plane + i - cx(A) - (long long)cy(A) * p.pitch, A);
-}
-
+// The nine pulled populations of node (x, y), one at a time with the boundary
+// rules (the diagnostics' scalar pull; the fused step pulls whole vectors).
 template <class S>
-__device__ __forceinline__ void pull_node(const StepParams& p, const typename S::E* src,
-                                          bool interior, int x, int y, typename S::T h[9]) {
-  if (interior) {
-    const long long i = (long long)y * p.pitch + x;
-    h[0] = pull_interior<S, 0>(p, src, i);
-    h[1] = pull_interior<S, 1>(p, src, i);
-    h[2] = pull_interior<S, 2>(p, src, i);
-    h[3] = pull_interior<S, 3>(p, src, i);
-    h[4] = pull_interior<S, 4>(p, src, i);
-    h[5] = pull_interior<S, 5>(p, src, i);
-    h[6] = pull_interior<S, 6>(p, src, i);
-    h[7] = pull_interior<S, 7>(p, src, i);
-    h[8] = pull_interior<S, 8>(p, src, i);
-  } else {
-    h[0] = pull_bc<S, 0>(p, src, x, y);
-    h[1] = pull_bc<S, 1>(p, src, x, y);
-    h[2] = pull_bc<S, 2>(p, src, x, y);
-    h[3] = pull_bc<S, 3>(p, src, x, y);
-    h[4] = pull_bc<S, 4>(p, src, x, y);
-    h[5] = pull_bc<S, 5>(p, src, x, y);
-    h[6] = pull_bc<S, 6>(p, src, x, y);
-    h[7] = pull_bc<S, 7>(p, src, x, y);
-    h[8] = pull_bc<S, 8>(p, src, x, y);
-  }
+__device__ __forceinline__ void pull_node(const StepParams& p, const typename S::E* src, int x,
+                                          int y, typename S::T h[9]) {
+  h[0] = pull_bc<S, 0>(p, src, x, y);
+  h[1] = pull_bc<S, 1>(p, src, x, y);
+  h[2] = pull_bc<S, 2>(p, src, x, y);
+  h[3] = pull_bc<S, 3>(p, src, x, y);
+  h[4] = pull_bc<S, 4>(p, src, x, y);
+  h[5] = pull_bc<S, 5>(p, src, x, y);
+  h[6] = pull_bc<S, 6>(p, src, x, y);
+  h[7] = pull_bc<S, 7>(p, src, x, y);
+  h[8] = pull_bc<S, 8>(p, src, x, y);
 }
 
 // ---------------------------------------------------------------------------
@@ -577,8 +563,9 @@ __device__ __forceinline__ void block_sum3(double v[3], double (*sm)[3]) {
 // Finishes the per-step reduction once this tile's partial is written: the
 // last tile of each group of kGroup tiles sums the group in tile order, and
 // the last group to finish sums the groups in group order and writes the
-// step's record. Both levels are fixed-order, so the result does not depend
-// on which blocks ran when.
+// step's record (a grid of a single group writes its group sum directly).
+// Both levels are fixed-order, so the result does not depend on which blocks
+// ran when.
 __device__ __forceinline__ void finish_reduction(const StepParams& p, int tile, long long t,
                                                  const double tile_sum[3], double (*sm)[3]) {
   __shared__ int s_last;
@@ -610,14 +597,23 @@ __device__ __forceinline__ void finish_reduction(const StepParams& p, int tile, 
     }
     block_sum3(v, sm);
     if (tid == 0) {
-      double* g = p.group_partials + 3ll * group;
-      __stcg(g + 0, v[0]);
-      __stcg(g + 1, v[1]);
-      __stcg(g + 2, v[2]);
       p.counters[group] = 0u;  // ready for the next step
-      __threadfence();
-      const unsigned prev = atomicAdd(p.counters + n_groups, 1u);
-      s_last = (prev == (unsigned)(n_groups - 1));
+      if (n_groups == 1) {
+        // one group (a small grid): its sum is the step's record
+        double* r = p.ring + 3ll * (t % p.ring_len);
+        r[0] = v[0];
+        r[1] = v[1];
+        r[2] = p.reduce_mass ? v[2] : 0.0;
+        s_last = 0;
+      } else {
+        double* g = p.group_partials + 3ll * group;
+        __stcg(g + 0, v[0]);
+        __stcg(g + 1, v[1]);
+        __stcg(g + 2, v[2]);
+        __threadfence();
+        const unsigned prev = atomicAdd(p.counters + n_groups, 1u);
+        s_last = (prev == (unsigned)(n_groups - 1));
+      }
     }
     __syncthreads();
   }
@@ -703,7 +699,7 @@ __device__ __forceinline__ void pull_dir_vec(const StepParams& p, const typename
   T v[N];
   if (!GEN || lane_active) {
     if (AA)
-      S::load_h_shared(row + xb, v, A);  // a plain generic load
+      S::load_h_plain(row + xb, v, A);
     else
       S::load_h(row + xb, v, A);
   } else {
@@ -987,7 +983,7 @@ __device__ __forceinline__ void pull_dir_smem(const typename S::E* row, int lane
   using E = typename S::E;
   constexpr int HALO = 16 / int(sizeof(E));
   T v[N];
-  S::load_h_shared(row + HALO + lane * N, v, A);
+  S::load_h_plain(row + HALO + lane * N, v, A);
   if (cx(A) == 0) {
 #pragma unroll
     for (int k = 0; k < N; ++k) h[k][A] = v[k];
@@ -1147,7 +1143,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
         T v[N];
-        S::load_h_shared(buf + (long long)a * p.plane + i, v, a);  // a plain generic load
+        S::load_h_plain(buf + (long long)a * p.plane + i, v, a);
 #pragma unroll
         for (int k = 0; k < N; ++k) h[k][a] = v[k];
       }
@@ -1346,7 +1342,7 @@ template <class S>
 __device__ __forceinline__ void pull_node_any(const StepParams& p, int x, int y, typename S::T h[9]) {
   const typename S::E* buf = static_cast<const typename S::E*>(p.src);
   if (p.mode == kModeAB) {
-    pull_node<S>(p, buf, false, x, y, h);
+    pull_node<S>(p, buf, x, y, h);
   } else if (p.mode == kModeAALocal) {
 #pragma unroll
     for (int a = 0; a < 9; ++a) h[a] = S::in(buf[(long long)a * p.plane + (long long)y * p.pitch + x], a);
