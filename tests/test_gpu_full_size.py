@@ -141,3 +141,70 @@ def test_bench_workload_in_place_bitwise():
             fa, fb = a.forces(), b.forces()
             for u, v in zip(fa, fb):
                 assert np.array_equal(u, v)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_cylinder_re1000_whole_grid_one_step(storage):
+    """The bench's 4096 x 1024 cylinder workload is small enough for the
+    oracle to step whole: every node of one step against the oracle, from the
+    GPU's own stored state after the bench's warm-up."""
+    import torch
+    w = I.c3_cylinder_re1000(storage)
+    cfg, _ = V.config_from_workload(w)
+    with V.Solver.from_workload(w, ring_len=64) as s:
+        s.step(WARMUP)
+        f_t = _export(torch, s, w.nx, w.ny).cpu().numpy()
+        s.step(1)
+        f_gpu = _export(torch, s, w.nx, w.ny).cpu().numpy()
+        fx, _, mass = s.forces()
+    ocfg = _oracle_config(w, cfg)
+    fx_ref, _, m_ref = O.run(ocfg, f_t, 1, t0=WARMUP)
+    err = np.abs(f_gpu - f_t)
+    if storage == "f32":
+        assert err.max() < 4e-7
+    else:
+        h = np.abs(f_t - O.weights()[:, None, None])
+        drop = 10 if storage == "f16" else 7
+        step = 2.0 ** (np.floor(np.log2(np.maximum(h, 2.0 ** -14))) - drop)
+        assert (err < step + 2e-6).all()
+    assert fx[-1] == pytest.approx(fx_ref[0], rel=2e-5)
+    assert mass[-1] == pytest.approx(m_ref[0], rel=1e-7)
+
+
+def test_grid_beyond_2_31_population_elements():
+    """A 32768 x 8192 periodic grid (9 planes of 2^28 nodes: offsets past
+    2^31 elements) started from a transverse plane shear wave
+    u = U e sin(k.x), e perpendicular to k (its advective term vanishes, so it
+    decays as exp(-nu |k|^2 t) exactly in the incompressible limit): every
+    sampled velocity follows that decay and the total mass stays N. An index
+    that wrapped at 32 bits would scramble whole population planes."""
+    import torch
+    nx, ny, U, n, tau = 32768, 8192, 0.01, 200, 0.8
+    cfg = V.make_config(nx, ny, "mrt", "f32", tau, bc="periodic", ring_len=n + 8)
+    kx, ky = 2 * np.pi * 8 / nx, 2 * np.pi * 4 / ny
+    kk = np.hypot(kx, ky)
+    ex, ey = ky / kk, -kx / kk
+    phase = kx * np.arange(nx)[None, :] + ky * np.arange(ny)[:, None]
+    u = np.empty((2, ny, nx))
+    np.sin(phase, out=u[0])
+    u[1] = u[0] * (U * ey)
+    u[0] *= U * ex
+    del phase
+    with V.Solver(cfg, [], u) as s:
+        del u
+        s.step(n)
+        _, _, mass = s.forces()
+        mom = torch.empty((3, ny, nx), dtype=torch.float64, device="cuda")
+        V.vplbm_moments(s.h, mom[0], mom[1], mom[2], on_device=True)
+        s.synchronize()
+    nu = (tau - 0.5) / 3.0
+    rng = np.random.default_rng(7)
+    xs, ys = rng.integers(0, nx, 20000), rng.integers(0, ny, 20000)
+    xs[:4], ys[:4] = [0, nx - 1, 0, nx - 1], [0, 0, ny - 1, ny - 1]
+    xi, yi = torch.as_tensor(xs, device="cuda"), torch.as_tensor(ys, device="cuda")
+    ux = mom[1][yi, xi].cpu().numpy()
+    uy = mom[2][yi, xi].cpu().numpy()
+    amp = U * np.sin(kx * xs + ky * ys) * np.exp(-nu * kk * kk * n)
+    assert np.abs(ux - ex * amp).max() < 2e-6, np.abs(ux - ex * amp).max()
+    assert np.abs(uy - ey * amp).max() < 2e-6, np.abs(uy - ey * amp).max()
+    assert np.abs(mass / (nx * ny) - 1.0).max() < 1e-6
