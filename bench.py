@@ -368,6 +368,7 @@ def run_gpu(args):
         extra["serving"] = rep
 
     peak, peak_src = hbm_peak()
+    l2_bytes = getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0)
     kms = fused_ms / max(fused_n, 1)
     achieved = ALGO_BYTES[args.storage] * nodes / (kms / 1e3) / 1e9
     traffic = traffic_per_launch(args.workload, args.storage, args.streaming)
@@ -389,8 +390,8 @@ def run_gpu(args):
                    "collision": w.collision, "re": w.re, "u_in": w.u_ref,
                    "step": "mask update of the moving body + fused pull/penalize/collide/reduce kernel",
                    "streaming": args.streaming,
-                   "l2": "inputs larger than L2 (%s population buffer%s of %.2f GB)" % (
-                       "two" if args.streaming == "ab" else "one in-place",
+                   "l2": "inputs larger than L2 (%.0f MB): %s population buffer%s of %.2f GB" % (
+                       l2_bytes / 1e6, "two" if args.streaming == "ab" else "one in-place",
                        "s" if args.streaming == "ab" else "",
                        9 * nodes * {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}[args.storage] / 1e9),
                    "parallelism": f"replicas x{world}"},
