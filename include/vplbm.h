@@ -152,8 +152,9 @@ double vplbm_tau_from_reynolds(double u_ref, double l_ref, double re);
 size_t vplbm_footprint_bytes(const vplbm_config* cfg);
 
 /* Allocates the solver and sets the store to f*(0) = f_eq(rho0, u0) with an
- * all-fluid mask. INVALID for nx or ny < 1, tau <= 1/2, eta <= 0, unknown
- * enums; NOMEM if the device allocation fails. *out is NULL on failure. */
+ * all-fluid mask. INVALID for nx or ny < 1, tau <= 1/2, eta <= 0, a negative
+ * or non-finite u_conv with the convective outlet, unknown enums; NOMEM if
+ * the device allocation fails. *out is NULL on failure. */
 vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out);
 
 /* Restarts from f*(0) = f_eq(rho0, u(x)) with u a host [2][ny][nx] array
@@ -211,10 +212,12 @@ vplbm_status vplbm_mask(vplbm_solver* s, uint8_t* chi);
 /* Checkpoint and restart. vplbm_state_bytes: size of a saved state.
  * vplbm_save_state writes into the caller's host buffer (synchronizes) the
  * store f*(t) exactly as stored, the mask, the static solid-velocity field if
- * one is set, and the step counter t. vplbm_load_state restores them into a
- * solver created with the same grid and storage (and the same bodies, whose
- * motion depends on t): stepping on from a loaded state is bitwise identical
- * to never having stopped. INVALID if the state does not match the solver. */
+ * one is set, the convective outlet state, the in-place scheme's phase and
+ * side arrays, and the step counter t. vplbm_load_state restores them into a
+ * solver created with the same grid, storage, outlet and streaming scheme
+ * (and the same bodies, whose motion depends on t): stepping on from a loaded
+ * state is bitwise identical to never having stopped. INVALID if the state
+ * does not match the solver. */
 size_t vplbm_state_bytes(const vplbm_solver* s);
 vplbm_status vplbm_save_state(vplbm_solver* s, void* buf);
 vplbm_status vplbm_load_state(vplbm_solver* s, const void* buf);
