@@ -79,3 +79,20 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(V, "LIB_PATH", str(tmp_path / "libvplbm.so"))
     with pytest.raises(ImportError):
         V.lib()
+
+
+def test_header_and_library_from_c(lib, tmp_path):
+    """The header is plain C: a C program compiled against it and linked with
+    libvplbm.so makes the host-only calls (no GPU needed)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("needs gcc")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_1812_05401_gb300")
+    exe = str(tmp_path / "abi_host_calls")
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(root, "include"),
+                    os.path.join(root, "tests", "c", "abi_host_calls.c"), "-o", exe,
+                    "-L", pkg, "-lvplbm", "-Wl,-rpath," + pkg, "-lm"], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
