@@ -123,16 +123,10 @@ __device__ __forceinline__ constexpr unsigned round_mul(int a) {
 }
 
 // Packed conversion of two FP32 values to two 16-bit values in one register
-// (lo in the low half, the lower address): round to nearest even or toward
-// zero.
+// (lo in the low half, the lower address): round to nearest even.
 __device__ __forceinline__ unsigned pack_f16_rn(float lo, float hi) {
   unsigned d;
   asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
-  return d;
-}
-__device__ __forceinline__ unsigned pack_f16_rz(float lo, float hi) {
-  unsigned d;
-  asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
   return d;
 }
 __device__ __forceinline__ unsigned pack_bf16_rn(float lo, float hi) {
@@ -140,10 +134,25 @@ __device__ __forceinline__ unsigned pack_bf16_rn(float lo, float hi) {
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
   return d;
 }
-__device__ __forceinline__ unsigned pack_bf16_rz(float lo, float hi) {
+// Stochastic rounding of two FP32 values to two 16-bit values with the
+// hardware conversion (cvt.rs): each result adds random bits below its kept
+// significand bits and truncates, so the magnitude rounds up with probability
+// equal to its distance from the lower neighbour. The low result takes its
+// bits from the low half of rbits, the high result from the high half (the
+// lowest 13 bits of each half for FP16, all 16 for BF16).
+__device__ __forceinline__ unsigned pack_f16_rs(float lo, float hi, unsigned rbits) {
   unsigned d;
-  asm("cvt.rz.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
   return d;
+}
+__device__ __forceinline__ unsigned pack_bf16_rs(float lo, float hi, unsigned rbits) {
+  unsigned d;
+  asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+  return d;
+}
+// Random word of a pair of nodes: the top halves of their direction words.
+__device__ __forceinline__ unsigned pair_bits(unsigned r_lo, unsigned r_hi) {
+  return __byte_perm(r_lo, r_hi, 0x7632);
 }
 
 // 16-bit offset forms: npt = 4 elements as one 8-byte access.
@@ -153,17 +162,6 @@ struct Store16 {
   using T = float;
   static constexpr bool kSixteen = true;
 };
-// Stochastic rounding of an FP32 value to a format keeping the top 23 - DROP
-// significand bits: add DROP uniformly random bits (the top bits of r) below
-// the kept ones and truncate toward zero, so the magnitude rounds up with
-// probability equal to its distance from the lower neighbour (exact for
-// normal results). The addition acts on the magnitude bits alone: a carry can
-// reach the exponent (rounding up to the next binade) but never the sign for
-// the finite values stored here.
-template <int DROP>
-__device__ __forceinline__ float dither(float h, unsigned r) {
-  return __uint_as_float(__float_as_uint(h) + (r >> (32 - DROP)));
-}
 template <> struct Store<kF16> : Store16<__half> {
   static __device__ __forceinline__ void load_h_plain(const E* p, T h[4], int a) {
     unpack(*reinterpret_cast<const uint2*>(p), h);
@@ -185,8 +183,8 @@ template <> struct Store<kF16> : Store16<__half> {
     uint2 v;
     if (sr) {
       const unsigned m = round_mul(a);
-      v.x = pack_f16_rz(dither<13>(h[0], r[0] * m), dither<13>(h[1], r[1] * m));
-      v.y = pack_f16_rz(dither<13>(h[2], r[2] * m), dither<13>(h[3], r[3] * m));
+      v.x = pack_f16_rs(h[0], h[1], pair_bits(r[0] * m, r[1] * m));
+      v.y = pack_f16_rs(h[2], h[3], pair_bits(r[2] * m, r[3] * m));
     } else {
       v.x = pack_f16_rn(h[0], h[1]);
       v.y = pack_f16_rn(h[2], h[3]);
@@ -198,7 +196,8 @@ template <> struct Store<kF16> : Store16<__half> {
   // one element as store_h rounds it (the packed conversions round each half alike)
   using R = unsigned short;
   static __device__ __forceinline__ R round_e(T h, int a, unsigned r, bool sr) {
-    return __half_as_ushort(sr ? __float2half_rz(dither<13>(h, r * round_mul(a))) : __float2half_rn(h));
+    return sr ? (unsigned short)(pack_f16_rs(h, 0.f, (r * round_mul(a)) >> 16) & 0xffffu)
+              : __half_as_ushort(__float2half_rn(h));
   }
   static __device__ __forceinline__ double to_f64(const E* p, int a) {
     return wgt<double>(a) + double(__half2float(*p));
@@ -226,8 +225,8 @@ template <> struct Store<kBF16> : Store16<__nv_bfloat16> {
     uint2 v;
     if (sr) {
       const unsigned m = round_mul(a);
-      v.x = pack_bf16_rz(dither<16>(h[0], r[0] * m), dither<16>(h[1], r[1] * m));
-      v.y = pack_bf16_rz(dither<16>(h[2], r[2] * m), dither<16>(h[3], r[3] * m));
+      v.x = pack_bf16_rs(h[0], h[1], pair_bits(r[0] * m, r[1] * m));
+      v.y = pack_bf16_rs(h[2], h[3], pair_bits(r[2] * m, r[3] * m));
     } else {
       v.x = pack_bf16_rn(h[0], h[1]);
       v.y = pack_bf16_rn(h[2], h[3]);
@@ -238,8 +237,8 @@ template <> struct Store<kBF16> : Store16<__nv_bfloat16> {
   static __device__ __forceinline__ E out(T h, int) { return __float2bfloat16_rn(h); }
   using R = unsigned short;
   static __device__ __forceinline__ R round_e(T h, int a, unsigned r, bool sr) {
-    return __bfloat16_as_ushort(sr ? __float2bfloat16_rz(dither<16>(h, r * round_mul(a)))
-                                   : __float2bfloat16_rn(h));
+    return sr ? (unsigned short)(pack_bf16_rs(h, 0.f, (r * round_mul(a)) >> 16) & 0xffffu)
+              : __bfloat16_as_ushort(__float2bfloat16_rn(h));
   }
   static __device__ __forceinline__ double to_f64(const E* p, int a) {
     return wgt<double>(a) + double(__bfloat162float(*p));
