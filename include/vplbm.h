@@ -131,6 +131,27 @@ typedef struct {
   double u_conv;           /* convective outlet velocity U_c >= 0 (bc_x = INLET_CONVECTIVE) */
   int32_t streaming;       /* VPLBM_STREAM_AB (default) | VPLBM_STREAM_AA */
   int32_t reserved;        /* 0 */
+  /* Device memory hook (optional): both set, or both NULL (the default:
+   * stream-ordered allocation from the CUDA memory pool on the solver's
+   * stream). When set, every device buffer the solver owns comes from
+   * dev_alloc(bytes, alloc_ctx) and goes back through dev_free(ptr,
+   * alloc_ctx): the populations, mask, reduction scratch and rings at
+   * vplbm_create, the solid-velocity and momentum-exchange buffers when first
+   * needed, and the staging buffers of host transfers. dev_alloc returns
+   * memory on the current device, aligned to 256 bytes and ready for work
+   * queued afterwards on the solver's stream (PyTorch's caching allocator on
+   * that stream qualifies), or NULL when it has none: the call then fails
+   * with VPLBM_ERR_NOMEM. A pointer that is not 256-byte aligned goes back
+   * through dev_free and the call fails with VPLBM_ERR_INVALID. The library
+   * waits for the solver's stream before every dev_free, so the allocator may
+   * hand the block out again at once; calls that stage through a temporary
+   * buffer therefore return after their device work. Both functions are
+   * called on the thread that makes the library call. vplbm_group_step's
+   * small per-call launch tables and vplbm_step_noalloc (which allocates
+   * nothing) do not use the hook. */
+  void* (*dev_alloc)(size_t bytes, void* ctx);
+  void (*dev_free)(void* ptr, void* ctx);
+  void* alloc_ctx;
 } vplbm_config;
 
 typedef struct vplbm_solver vplbm_solver;
@@ -153,8 +174,9 @@ size_t vplbm_footprint_bytes(const vplbm_config* cfg);
 
 /* Allocates the solver and sets the store to f*(0) = f_eq(rho0, u0) with an
  * all-fluid mask. INVALID for nx or ny < 1, tau <= 1/2, eta <= 0, a negative
- * or non-finite u_conv with the convective outlet, unknown enums; NOMEM if
- * the device allocation fails. *out is NULL on failure. */
+ * or non-finite u_conv with the convective outlet, unknown enums, or only one
+ * of dev_alloc and dev_free set; NOMEM if the device allocation fails. *out
+ * is NULL on failure, and every buffer already taken has been released. */
 vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out);
 
 /* Restarts from f*(0) = f_eq(rho0, u(x)) with u a host [2][ny][nx] array

@@ -274,6 +274,67 @@ vplbm_status cuda_fail(vplbm_solver* s, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail((s), e_, #call); \
   } while (0)
 
+#define VP_OK(call)                          \
+  do {                                       \
+    vplbm_status st_ = (call);               \
+    if (st_ != VPLBM_OK) return st_;         \
+  } while (0)
+
+// Device memory of a solver: from the caller's allocator when the
+// configuration sets dev_alloc / dev_free, else stream-ordered from the CUDA
+// memory pool on the solver's stream (neither allocation nor release
+// synchronizes the device, so solvers can come and go while others run).
+constexpr uintptr_t kAllocAlign = 256;
+
+vplbm_status mem_get(vplbm_solver* s, void** p, size_t bytes) {
+  *p = nullptr;
+  if (!s->cfg.dev_alloc) {
+    cudaError_t e = cudaMallocAsync(p, bytes, s->stream);
+    return e == cudaSuccess ? VPLBM_OK : cuda_fail(s, e, "cudaMallocAsync");
+  }
+  void* q = s->cfg.dev_alloc(bytes, s->cfg.alloc_ctx);
+  if (!q)
+    return fail(s, VPLBM_ERR_NOMEM, "dev_alloc returned NULL for " + std::to_string(bytes) + " bytes");
+  if (reinterpret_cast<uintptr_t>(q) % kAllocAlign != 0) {
+    s->cfg.dev_free(q, s->cfg.alloc_ctx);
+    return fail(s, VPLBM_ERR_INVALID, "dev_alloc returned a pointer not aligned to 256 bytes");
+  }
+  *p = q;
+  return VPLBM_OK;
+}
+
+template <class T>
+vplbm_status mem_get(vplbm_solver* s, T** p, size_t bytes) {
+  void* q = nullptr;
+  const vplbm_status st = mem_get(s, &q, bytes);
+  *p = static_cast<T*>(q);
+  return st;
+}
+
+// Releases a solver buffer. The caller's allocator may hand the block out
+// again at once, so the work already queued on the stream finishes first.
+void mem_put(vplbm_solver* s, void* p) {
+  if (!p) return;
+  if (!s->cfg.dev_free) {
+    cudaFreeAsync(p, s->stream);
+    return;
+  }
+  cudaStreamSynchronize(s->stream);
+  s->cfg.dev_free(p, s->cfg.alloc_ctx);
+}
+
+// A staging buffer of one call, released when the call returns on any path.
+template <class T>
+struct Staging {
+  vplbm_solver* s;
+  T* p = nullptr;
+  explicit Staging(vplbm_solver* solver) : s(solver) {}
+  Staging(const Staging&) = delete;
+  Staging& operator=(const Staging&) = delete;
+  ~Staging() { mem_put(s, p); }
+  vplbm_status get(size_t n) { return mem_get(s, &p, n * sizeof(T)); }
+};
+
 void body_state(const vplbm_body& b, int64_t t, BodyState* st) {
   // centre(t) = c + amp sin(2 pi t / period), velocity = its time derivative
   if (b.period > 0.0) {
@@ -369,10 +430,9 @@ vplbm_status update_static_box(vplbm_solver* s) {
 vplbm_status ensure_me_buffers(vplbm_solver* s) {
   if (s->me_scratch) return VPLBM_OK;
   const size_t L = size_t(s->cfg.force_ring_len);
-  VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&s->me_ring), 2 * sizeof(double) * L, s->stream));
-  VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&s->me_scratch),
-                             2 * sizeof(double) * (kMeBlocks + 1), s->stream));
-  VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&s->me_counter), sizeof(unsigned), s->stream));
+  if (!s->me_ring) VP_OK(mem_get(s, &s->me_ring, 2 * sizeof(double) * L));
+  if (!s->me_counter) VP_OK(mem_get(s, &s->me_counter, sizeof(unsigned)));
+  VP_OK(mem_get(s, &s->me_scratch, 2 * sizeof(double) * (kMeBlocks + 1)));
   VP_CUDA(s, cudaMemsetAsync(s->me_ring, 0, 2 * sizeof(double) * L, s->stream));
   VP_CUDA(s, cudaMemsetAsync(s->me_counter, 0, sizeof(unsigned), s->stream));
   return VPLBM_OK;
@@ -542,6 +602,8 @@ vplbm_status validate(const vplbm_config* c, std::string* why) {
   if (c->force_ring_len < 1) return *why = "force_ring_len must be >= 1", VPLBM_ERR_INVALID;
   if (c->rounding != VPLBM_ROUND_NEAREST && c->rounding != VPLBM_ROUND_STOCHASTIC)
     return *why = "unknown rounding", VPLBM_ERR_INVALID;
+  if (!c->dev_alloc != !c->dev_free)
+    return *why = "dev_alloc and dev_free must both be set or both be NULL", VPLBM_ERR_INVALID;
   return VPLBM_OK;
 }
 
@@ -672,20 +734,18 @@ vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
   }
   const size_t pop = size_t(9) * size_t(s->plane) * s->esize;
   cudaError_t e = cudaSuccess;
-  // Stream-ordered allocations: neither allocation nor release synchronizes
-  // the device, so solvers can come and go while others run (serving).
   cudaStream_t st0 = s->stream;
   s->aa = cfg->streaming == VPLBM_STREAM_AA;
-  if ((e = cudaMallocAsync(&s->f[0], pop, st0)) != cudaSuccess ||
-      (!s->aa && (e = cudaMallocAsync(&s->f[1], pop, st0)) != cudaSuccess) ||
-      (e = cudaMallocAsync(reinterpret_cast<void**>(&s->mask), size_t(s->plane), st0)) != cudaSuccess ||
-      (e = cudaMallocAsync(reinterpret_cast<void**>(&s->partials), 3 * sizeof(double) * s->n_tiles, st0)) != cudaSuccess ||
-      (e = cudaMallocAsync(reinterpret_cast<void**>(&s->group_partials), 3 * sizeof(double) * s->n_groups, st0)) != cudaSuccess ||
-      (e = cudaMallocAsync(reinterpret_cast<void**>(&s->counters), sizeof(unsigned) * (s->n_groups + 1), st0)) != cudaSuccess ||
-      (e = cudaMallocAsync(reinterpret_cast<void**>(&s->ring), 3 * sizeof(double) * cfg->force_ring_len, st0)) != cudaSuccess ||
-      (e = cudaMallocAsync(reinterpret_cast<void**>(&s->flag), sizeof(int), st0)) != cudaSuccess ||
-      (e = cudaMallocAsync(reinterpret_cast<void**>(&s->static_box), sizeof(kEmptyBox), st0)) != cudaSuccess) {
-    return bail(cuda_fail(s, e, "cudaMallocAsync"));
+  if ((st = mem_get(s, &s->f[0], pop)) != VPLBM_OK ||
+      (!s->aa && (st = mem_get(s, &s->f[1], pop)) != VPLBM_OK) ||
+      (st = mem_get(s, &s->mask, size_t(s->plane))) != VPLBM_OK ||
+      (st = mem_get(s, &s->partials, 3 * sizeof(double) * s->n_tiles)) != VPLBM_OK ||
+      (st = mem_get(s, &s->group_partials, 3 * sizeof(double) * s->n_groups)) != VPLBM_OK ||
+      (st = mem_get(s, &s->counters, sizeof(unsigned) * (s->n_groups + 1))) != VPLBM_OK ||
+      (st = mem_get(s, &s->ring, 3 * sizeof(double) * cfg->force_ring_len)) != VPLBM_OK ||
+      (st = mem_get(s, &s->flag, sizeof(int))) != VPLBM_OK ||
+      (st = mem_get(s, &s->static_box, sizeof(kEmptyBox))) != VPLBM_OK) {
+    return bail(st);
   }
   if ((e = cudaMemsetAsync(s->mask, 0, size_t(s->plane), s->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(s->counters, 0, sizeof(unsigned) * (s->n_groups + 1), s->stream)) != cudaSuccess ||
@@ -700,18 +760,18 @@ vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
   if (s->aa) {
     s->f[1] = s->f[0];
     if (cfg->bc_x != VPLBM_BC_PERIODIC) {
-      if ((e = cudaMallocAsync(&s->z, 3 * size_t(cfg->ny) * s->esize, st0)) != cudaSuccess ||
-          (e = cudaMallocAsync(&s->lost, 6 * size_t(cfg->ny) * s->esize, st0)) != cudaSuccess)
-        return bail(cuda_fail(s, e, "cudaMallocAsync"));
+      if ((st = mem_get(s, &s->z, 3 * size_t(cfg->ny) * s->esize)) != VPLBM_OK ||
+          (st = mem_get(s, &s->lost, 6 * size_t(cfg->ny) * s->esize)) != VPLBM_OK)
+        return bail(st);
       if ((e = cudaMemsetAsync(s->lost, 0, 6 * size_t(cfg->ny) * s->esize, st0)) != cudaSuccess)
         return bail(cuda_fail(s, e, "cudaMemsetAsync"));
     }
   }
   if (cfg->bc_x == VPLBM_BC_INLET_CONVECTIVE) {
     const size_t gb = 3 * size_t(cfg->ny) * ghost_elem(cfg->storage);
-    if ((e = cudaMallocAsync(&s->ghost[0], gb, st0)) != cudaSuccess ||
-        (e = cudaMallocAsync(&s->ghost[1], gb, st0)) != cudaSuccess)
-      return bail(cuda_fail(s, e, "cudaMallocAsync"));
+    if ((st = mem_get(s, &s->ghost[0], gb)) != VPLBM_OK ||
+        (st = mem_get(s, &s->ghost[1], gb)) != VPLBM_OK)
+      return bail(st);
   }
 
   StepParams& p = s->base;
@@ -790,16 +850,15 @@ vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
 vplbm_status vplbm_set_initial_velocity(vplbm_solver* s, const double* u) {
   vplbm_status st = check_usable(s);
   if (st != VPLBM_OK) return st;
-  double* du = nullptr;
+  Staging<double> du(s);
   const size_t n = size_t(s->cfg.nx) * size_t(s->cfg.ny);
   if (u) {
-    VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&du), 2 * n * sizeof(double), s->stream));
-    VP_CUDA(s, cudaMemcpyAsync(du, u, 2 * n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    VP_OK(du.get(2 * n));
+    VP_CUDA(s, cudaMemcpyAsync(du.p, u, 2 * n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
   }
   s->cur = 0;
-  VP_CUDA(s, launch_init(s, s->base, s->f[0], du));
+  VP_CUDA(s, launch_init(s, s->base, s->f[0], du.p));
   if ((st = init_outlet_state(s)) != VPLBM_OK) return st;
-  if (du) VP_CUDA(s, cudaFreeAsync(du, s->stream));
   s->t = 0;
   s->ring_read = 0;
   s->me_read = 0;
@@ -819,16 +878,16 @@ vplbm_status vplbm_set_mask_and_solid_velocity(vplbm_solver* s, const uint8_t* c
   const size_t n = size_t(nx) * ny;
   const uint8_t* dchi = chi;
   const double* dus = us;
-  uint8_t* tchi = nullptr;
-  double* tus = nullptr;
+  Staging<uint8_t> tchi(s);
+  Staging<double> tus(s);
   if (!on_device) {
-    VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&tchi), n, s->stream));
-    VP_CUDA(s, cudaMemcpyAsync(tchi, chi, n, cudaMemcpyHostToDevice, s->stream));
-    dchi = tchi;
+    VP_OK(tchi.get(n));
+    VP_CUDA(s, cudaMemcpyAsync(tchi.p, chi, n, cudaMemcpyHostToDevice, s->stream));
+    dchi = tchi.p;
     if (us) {
-      VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&tus), 2 * n * sizeof(double), s->stream));
-      VP_CUDA(s, cudaMemcpyAsync(tus, us, 2 * n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-      dus = tus;
+      VP_OK(tus.get(2 * n));
+      VP_CUDA(s, cudaMemcpyAsync(tus.p, us, 2 * n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+      dus = tus.p;
     }
   }
   const dim3 blk(64, 4);
@@ -837,7 +896,7 @@ vplbm_status vplbm_set_mask_and_solid_velocity(vplbm_solver* s, const uint8_t* c
   if ((st = update_static_box(s)) != VPLBM_OK) return st;
   if (dus) {
     const size_t vs = s->cfg.storage == kF64 ? sizeof(double2) : sizeof(float2);
-    if (!s->us) VP_CUDA(s, cudaMallocAsync(&s->us, vs * size_t(s->plane), s->stream));
+    if (!s->us) VP_OK(mem_get(s, &s->us, vs * size_t(s->plane)));
     if (s->cfg.storage == kF64)
       us_import_kernel<double2><<<grid2d(nx, ny, blk), blk, 0, s->stream>>>(
           static_cast<double2*>(s->us), s->pitch, nx, ny, dus);
@@ -849,8 +908,6 @@ vplbm_status vplbm_set_mask_and_solid_velocity(vplbm_solver* s, const uint8_t* c
   } else {
     s->base.us = nullptr;
   }
-  if (tchi) VP_CUDA(s, cudaFreeAsync(tchi, s->stream));
-  if (tus) VP_CUDA(s, cudaFreeAsync(tus, s->stream));
   // Rebuild the bodies where the static layer changed.
   if (!s->bodies.empty()) {
     st = launch_mask_update(s, Box{0, 0, nx - 1, ny - 1}, s->t);
@@ -936,13 +993,12 @@ vplbm_status vplbm_moments(vplbm_solver* s, double* rho, double* ux, double* uy,
     VP_CUDA(s, launch_moments(s, p, rho, ux, uy));
     return VPLBM_OK;
   }
-  double* d = nullptr;
-  VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&d), 3 * n * sizeof(double), s->stream));
-  VP_CUDA(s, launch_moments(s, p, d, d + n, d + 2 * n));
-  VP_CUDA(s, cudaMemcpyAsync(rho, d, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  VP_CUDA(s, cudaMemcpyAsync(ux, d + n, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  VP_CUDA(s, cudaMemcpyAsync(uy, d + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  VP_CUDA(s, cudaFreeAsync(d, s->stream));
+  Staging<double> d(s);
+  VP_OK(d.get(3 * n));
+  VP_CUDA(s, launch_moments(s, p, d.p, d.p + n, d.p + 2 * n));
+  VP_CUDA(s, cudaMemcpyAsync(rho, d.p, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  VP_CUDA(s, cudaMemcpyAsync(ux, d.p + n, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  VP_CUDA(s, cudaMemcpyAsync(uy, d.p + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   VP_CUDA(s, cudaStreamSynchronize(s->stream));
   return VPLBM_OK;
 }
@@ -956,11 +1012,10 @@ vplbm_status vplbm_populations(vplbm_solver* s, double* f, int32_t on_device) {
     VP_CUDA(s, launch_export(s, step_params(s, s->t, 0), s->f[s->cur], f));
     return VPLBM_OK;
   }
-  double* d = nullptr;
-  VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&d), 9 * n * sizeof(double), s->stream));
-  VP_CUDA(s, launch_export(s, step_params(s, s->t, 0), s->f[s->cur], d));
-  VP_CUDA(s, cudaMemcpyAsync(f, d, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  VP_CUDA(s, cudaFreeAsync(d, s->stream));
+  Staging<double> d(s);
+  VP_OK(d.get(9 * n));
+  VP_CUDA(s, launch_export(s, step_params(s, s->t, 0), s->f[s->cur], d.p));
+  VP_CUDA(s, cudaMemcpyAsync(f, d.p, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   VP_CUDA(s, cudaStreamSynchronize(s->stream));
   return VPLBM_OK;
 }
@@ -974,11 +1029,10 @@ vplbm_status vplbm_set_populations(vplbm_solver* s, const double* f, int32_t on_
   if (on_device) {
     VP_CUDA(s, launch_import(s, s->base, s->f[s->cur], f));
   } else {
-    double* d = nullptr;
-    VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&d), 9 * n * sizeof(double), s->stream));
-    VP_CUDA(s, cudaMemcpyAsync(d, f, 9 * n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-    VP_CUDA(s, launch_import(s, s->base, s->f[s->cur], d));
-    VP_CUDA(s, cudaFreeAsync(d, s->stream));
+    Staging<double> d(s);
+    VP_OK(d.get(9 * n));
+    VP_CUDA(s, cudaMemcpyAsync(d.p, f, 9 * n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    VP_CUDA(s, launch_import(s, s->base, s->f[s->cur], d.p));
   }
   // the convective outlet restarts from a zero-gradient copy of the new store
   return init_outlet_state(s);
@@ -991,13 +1045,12 @@ vplbm_status vplbm_mask(vplbm_solver* s, uint8_t* chi) {
   if ((st = ensure_mask(s, s->t)) != VPLBM_OK) return st;
   const int nx = s->cfg.nx, ny = s->cfg.ny;
   const size_t n = size_t(nx) * ny;
-  uint8_t* d = nullptr;
-  VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&d), n, s->stream));
+  Staging<uint8_t> d(s);
+  VP_OK(d.get(n));
   const dim3 blk(64, 4);
-  mask_export_kernel<<<grid2d(nx, ny, blk), blk, 0, s->stream>>>(s->mask, s->pitch, nx, ny, d);
+  mask_export_kernel<<<grid2d(nx, ny, blk), blk, 0, s->stream>>>(s->mask, s->pitch, nx, ny, d.p);
   VP_CUDA(s, cudaGetLastError());
-  VP_CUDA(s, cudaMemcpyAsync(chi, d, n, cudaMemcpyDeviceToHost, s->stream));
-  VP_CUDA(s, cudaFreeAsync(d, s->stream));
+  VP_CUDA(s, cudaMemcpyAsync(chi, d.p, n, cudaMemcpyDeviceToHost, s->stream));
   VP_CUDA(s, cudaStreamSynchronize(s->stream));
   return VPLBM_OK;
 }
@@ -1129,7 +1182,7 @@ vplbm_status vplbm_load_state(vplbm_solver* s, const void* buf) {
     const size_t vs = s->cfg.storage == kF64 ? sizeof(double2) : sizeof(float2);
     if (h.us_bytes != vs * size_t(s->plane))
       return fail(s, VPLBM_ERR_INVALID, "state's solid-velocity field does not match");
-    if (!s->us) VP_CUDA(s, cudaMallocAsync(&s->us, h.us_bytes, s->stream));
+    if (!s->us) VP_OK(mem_get(s, &s->us, h.us_bytes));
     VP_CUDA(s, cudaMemcpyAsync(s->us, in, h.us_bytes, cudaMemcpyHostToDevice, s->stream));
     s->base.us = s->us;
     in += h.us_bytes;
@@ -1238,17 +1291,16 @@ vplbm_status vplbm_set_initial_perturbation(vplbm_solver* s, double u0x, double 
   if (st != VPLBM_OK) return st;
   if (!(amp >= 0.0)) return fail(s, VPLBM_ERR_INVALID, "amp must be >= 0");
   const size_t n = size_t(s->cfg.nx) * s->cfg.ny;
-  double* du = nullptr;
-  VP_CUDA(s, cudaMallocAsync(reinterpret_cast<void**>(&du), 2 * n * sizeof(double), s->stream));
+  Staging<double> du(s);
+  VP_OK(du.get(2 * n));
   const int threads = 256;
   const long long blocks = (long long)((n + threads - 1) / threads);
-  perturbation_kernel<<<unsigned(blocks), threads, 0, s->stream>>>(du, s->cfg.nx, s->cfg.ny, u0x, u0y,
-                                                                    amp, seed);
+  perturbation_kernel<<<unsigned(blocks), threads, 0, s->stream>>>(du.p, s->cfg.nx, s->cfg.ny, u0x,
+                                                                    u0y, amp, seed);
   VP_CUDA(s, cudaGetLastError());
   s->cur = 0;
-  VP_CUDA(s, launch_init(s, s->base, s->f[0], du));
+  VP_CUDA(s, launch_init(s, s->base, s->f[0], du.p));
   if ((st = init_outlet_state(s)) != VPLBM_OK) return st;
-  VP_CUDA(s, cudaFreeAsync(du, s->stream));
   s->t = 0;
   s->ring_read = 0;
   s->me_read = 0;
@@ -1296,14 +1348,26 @@ vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int
     classes[s->cfg.storage][s->aa ? 1 + s->cur : 0].push_back({i, steps[i]});
   }
   struct Plan {
-    int storage;
-    int cls;
-    StepParams* d_params;
-    GroupTile* d_table;
+    int storage = 0;
+    int cls = 0;
+    StepParams* d_params = nullptr;
+    GroupTile* d_table = nullptr;
     std::vector<int64_t> prefix_steps;  // steps of the j-th member (descending)
     std::vector<int> prefix_tiles;      // tiles of members 0..j
   };
-  std::vector<Plan> plans;
+  // The launch tables live for this call only and go back to the memory pool
+  // (stream-ordered, after the launches that read them) on every return path.
+  struct Plans {
+    std::vector<Plan> v;
+    cudaStream_t stream;
+    ~Plans() {
+      for (auto& pl : v) {
+        if (pl.d_params) cudaFreeAsync(pl.d_params, stream);
+        if (pl.d_table) cudaFreeAsync(pl.d_table, stream);
+      }
+    }
+  } owned{{}, stream};
+  std::vector<Plan>& plans = owned.v;
   for (int sg = 0; sg < 4; ++sg) {
     for (int cls = 0; cls < 3; ++cls) {
       auto& mem = classes[sg][cls];
@@ -1312,7 +1376,8 @@ vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int
                        [](const Member& a, const Member& b) { return a.steps > b.steps; });
       std::vector<StepParams> hp;
       std::vector<GroupTile> ht;
-      Plan pl;
+      plans.emplace_back();
+      Plan& pl = plans.back();
       pl.storage = sg;
       pl.cls = cls;
       for (size_t j = 0; j < mem.size(); ++j) {
@@ -1331,7 +1396,6 @@ vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int
                                   cudaMemcpyHostToDevice, stream));
       VP_CUDA(s0, cudaMemcpyAsync(pl.d_table, ht.data(), ht.size() * sizeof(GroupTile),
                                   cudaMemcpyHostToDevice, stream));
-      plans.push_back(std::move(pl));
     }
   }
   for (int64_t k = 0; k < max_steps; ++k) {
@@ -1351,10 +1415,6 @@ vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int
         if (st != VPLBM_OK) return st;
       }
     }
-  }
-  for (auto& pl : plans) {
-    VP_CUDA(s0, cudaFreeAsync(pl.d_params, stream));
-    VP_CUDA(s0, cudaFreeAsync(pl.d_table, stream));
   }
   for (int i = 0; i < n; ++i) {
     vplbm_solver* s = solvers[i];
@@ -1417,8 +1477,14 @@ void vplbm_destroy(vplbm_solver* s) {
     void* bufs[] = {s->f[0], s->aa ? nullptr : s->f[1], s->mask, s->us, s->partials, s->group_partials,
                     s->counters, s->ring, s->flag, s->static_box, s->me_ring,
                     s->me_scratch, s->me_counter, s->ghost[0], s->ghost[1], s->z, s->lost};
-    for (void* b : bufs)
-      if (b) cudaFreeAsync(b, s->stream);
+    if (s->cfg.dev_free) cudaStreamSynchronize(s->stream);  // once, for all of them
+    for (void* b : bufs) {
+      if (!b) continue;
+      if (s->cfg.dev_free)
+        s->cfg.dev_free(b, s->cfg.alloc_ctx);
+      else
+        cudaFreeAsync(b, s->stream);
+    }
     if (s->own_stream) cudaStreamDestroy(s->stream);
   }
   delete s;

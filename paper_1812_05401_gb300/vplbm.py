@@ -40,6 +40,11 @@ class vplbm_body(C.Structure):
                 ("omega", C.c_double), ("outside", C.c_int32), ("reserved", C.c_int32)]
 
 
+# the device memory hook of vplbm_config: void* dev_alloc(size_t, void*), void dev_free(void*, void*)
+DEV_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+DEV_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
 class vplbm_config(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("collision", C.c_int32),
                 ("storage", C.c_int32), ("bc_x", C.c_int32), ("bc_y", C.c_int32),
@@ -48,7 +53,8 @@ class vplbm_config(C.Structure):
                 ("u_in", C.c_double * 2), ("rho0", C.c_double), ("u0", C.c_double * 2),
                 ("body_force", C.c_double * 2), ("rates", C.c_double * 9),
                 ("force_ring_len", C.c_int32), ("rounding", C.c_int32), ("stream", C.c_void_p),
-                ("u_conv", C.c_double), ("streaming", C.c_int32), ("reserved", C.c_int32)]
+                ("u_conv", C.c_double), ("streaming", C.c_int32), ("reserved", C.c_int32),
+                ("dev_alloc", DEV_ALLOC_FN), ("dev_free", DEV_FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
 class VplbmError(RuntimeError):
@@ -320,13 +326,83 @@ def vplbm_destroy(h):
 # Convenience wrapper
 # ---------------------------------------------------------------------------
 
+class TorchAllocator:
+    """The device memory hook of vplbm_config served by PyTorch's caching
+    allocator: blocks come from torch.cuda.caching_allocator_alloc and go back
+    through caching_allocator_delete, so a solver's buffers count in
+    torch.cuda.memory_allocated and share PyTorch's pool. Keeps counts of the
+    calls (allocs, frees) and of the bytes it has out (live_bytes).
+
+    The caching allocator reuses a block in stream order only on the stream it
+    was allocated for, so the allocator and the solver share one stream:
+    `stream` (a torch.cuda.Stream or a raw handle), else the config's stream
+    at install(), else a new torch.cuda.Stream (never the legacy NULL stream,
+    for which the library would create a private stream of its own).
+
+    A config carrying the hook holds a reference to this object; keep the
+    config (a Solver does) or the allocator alive while a solver created with
+    it exists."""
+
+    def __init__(self, stream=None, device=None):
+        import torch
+        self._torch = torch
+        self.device = torch.cuda.current_device() if device is None else device
+        self._stream_obj = stream
+        self.stream = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+        self.allocs = 0
+        self.frees = 0
+        self.live_bytes = 0
+        self._sizes = {}
+        self._alloc = DEV_ALLOC_FN(self._do_alloc)
+        self._free = DEV_FREE_FN(self._do_free)
+
+    def _do_alloc(self, nbytes, _ctx):
+        try:
+            ptr = self._torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream)
+        except Exception:  # out of memory (or any failure): the library reports NOMEM
+            return None
+        self.allocs += 1
+        self._sizes[ptr] = int(nbytes)
+        self.live_bytes += int(nbytes)
+        return ptr
+
+    def _do_free(self, ptr, _ctx):
+        try:
+            self._torch.cuda.caching_allocator_delete(ptr)
+        except Exception:  # interpreter shutdown: the process is ending anyway
+            return
+        self.frees += 1
+        self.live_bytes -= self._sizes.pop(ptr, 0)
+
+    def install(self, cfg: vplbm_config) -> vplbm_config:
+        if self.stream is None:
+            if cfg.stream:
+                self.stream = int(cfg.stream)
+            else:
+                self._stream_obj = self._torch.cuda.Stream(self.device)
+                self.stream = self._stream_obj.cuda_stream
+        if self.stream == 0:
+            raise ValueError("the legacy default stream cannot carry a solver with this allocator")
+        if cfg.stream and int(cfg.stream) != self.stream:
+            raise ValueError("the allocator's stream must be the solver's stream")
+        cfg.stream = C.c_void_p(self.stream)
+        cfg.dev_alloc = self._alloc
+        cfg.dev_free = self._free
+        cfg.alloc_ctx = None
+        cfg._allocator = self  # the callbacks live as long as the config
+        return cfg
+
+
 def make_config(nx, ny, collision="srt", storage="f32", tau=0.8, lam=3.0 / 16.0, eta=1e-7,
                 bc="periodic", u_in=(0.0, 0.0), u0=(0.0, 0.0), rho0=1.0, body_force=(0.0, 0.0),
                 rates=None, reduce_mass=True, ring_len=4096, stream=None,
-                rounding="stochastic", u_conv=None, streaming="ab") -> vplbm_config:
+                rounding="stochastic", u_conv=None, streaming="ab",
+                allocator: TorchAllocator | None = None) -> vplbm_config:
     """bc: "periodic", "channel" (inlet, zero-gradient outlet, free-slip walls),
     "channel-convective" (the same with the convective outlet; U_c = u_conv,
-    by default the inlet speed), or a (bc_x, bc_y) pair."""
+    by default the inlet speed), or a (bc_x, bc_y) pair. allocator: a
+    TorchAllocator (or any object with install(cfg)) for the device memory
+    hook; None keeps the library's stream-ordered pool."""
     c = vplbm_config_init()
     c.nx, c.ny = int(nx), int(ny)
     c.collision = COLLISION[collision] if isinstance(collision, str) else int(collision)
@@ -357,11 +433,13 @@ def make_config(nx, ny, collision="srt", storage="f32", tau=0.8, lam=3.0 / 16.0,
         if isinstance(rounding, str) else int(rounding)
     if stream is not None:
         c.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    if allocator is not None:
+        allocator.install(c)
     return c
 
 
 def config_from_workload(w, ring_len: int = 4096, stream=None, reduce_mass: bool = True,
-                         rounding: str = "stochastic", streaming: str = "ab"):
+                         rounding: str = "stochastic", streaming: str = "ab", allocator=None):
     """vplbm_config and body list for an inputs.Workload (tau from its
     Reynolds number when it gives one)."""
     tau = w.tau if w.tau is not None else vplbm_tau_from_reynolds(w.u_ref, w.l_ref, w.re)
@@ -369,7 +447,7 @@ def config_from_workload(w, ring_len: int = 4096, stream=None, reduce_mass: bool
     bc = "channel-convective" if w.bc == "channel" and w.outlet == "convective" else w.bc
     cfg = make_config(w.nx, w.ny, w.collision, w.storage, tau, w.lam, bc=bc, u_in=u_in,
                       ring_len=ring_len, stream=stream, reduce_mass=reduce_mass, rounding=rounding,
-                      streaming=streaming)
+                      streaming=streaming, allocator=allocator)
     return cfg, list(w.bodies)
 
 
@@ -396,10 +474,11 @@ class Solver:
     @classmethod
     def from_workload(cls, w, stream=None, ring_len: int = 4096, reduce_mass: bool = True,
                       with_initial_velocity: bool = True, rounding: str = "stochastic",
-                      device_init: bool = False, streaming: str = "ab"):
+                      device_init: bool = False, streaming: str = "ab", allocator=None):
         """device_init: generate the workload's seeded initial field on the
         device (bit-identical to w.initial_velocity())."""
-        cfg, bodies = config_from_workload(w, ring_len, stream, reduce_mass, rounding, streaming)
+        cfg, bodies = config_from_workload(w, ring_len, stream, reduce_mass, rounding, streaming,
+                                           allocator)
         if not with_initial_velocity:
             return cls(cfg, bodies)
         if device_init:

@@ -1,12 +1,21 @@
 /* A C program against include/vplbm.h and libvplbm.so, using only the calls
  * that need no GPU: configuration defaults, the relaxation time from the
- * Reynolds number, footprints, and the refusal of invalid configurations.
+ * Reynolds number, footprints, and the refusal of invalid configurations
+ * (including a device memory hook with only one of its two functions).
  * Prints one line per check and exits non-zero on the first failure. */
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
 
 #include "vplbm.h"
+
+static int alloc_calls = 0;
+static void* host_only_alloc(size_t bytes, void* ctx) {
+  (void)bytes;
+  (void)ctx;
+  ++alloc_calls;
+  return NULL;
+}
 
 static int fail(const char* what) {
   printf("FAIL %s\n", what);
@@ -47,6 +56,15 @@ int main(void) {
   c.streaming = 7;
   if (vplbm_create(&c, &s) != VPLBM_ERR_INVALID) return fail("unknown streaming refused");
   if (vplbm_create(NULL, &s) != VPLBM_ERR_INVALID) return fail("NULL config refused");
+  /* the device memory hook: unset by default; one function without the other is refused */
+  vplbm_config_init(&c);
+  if (c.dev_alloc != NULL || c.dev_free != NULL || c.alloc_ctx != NULL) return fail("hook default");
+  c.nx = 64;
+  c.ny = 32;
+  c.dev_alloc = host_only_alloc;
+  if (vplbm_footprint_bytes(&c) != 0) return fail("half-set hook: no footprint");
+  if (vplbm_create(&c, &s) != VPLBM_ERR_INVALID || s != NULL) return fail("half-set hook refused");
+  if (alloc_calls != 0) return fail("refused before any allocation");
   if (vplbm_step_count(NULL) != -1 || vplbm_launch_count(NULL) != -1) return fail("NULL handle");
   if (strcmp(vplbm_status_string(VPLBM_ERR_DIVERGED), "diverged") != 0) return fail("status string");
   vplbm_destroy(NULL);

@@ -1,5 +1,6 @@
 """CPU checks of the C ABI library: it loads without a GPU, exports every entry
 point include/vplbm.h declares, and its host-only helpers behave."""
+import ctypes
 import os
 import re
 
@@ -96,3 +97,34 @@ def test_header_and_library_from_c(lib, tmp_path):
                     "-L", pkg, "-lvplbm", "-Wl,-rpath," + pkg, "-lm"], check=True)
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every field of the ctypes vplbm_config and vplbm_body sits at the
+    offset and has the size a C compiler gives it from the header (the
+    binding's `lam` is the header's `lambda`)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("needs gcc")
+    from paper_1812_05401_gb300 import vplbm as V
+    exe = str(tmp_path / "abi_layout")
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c", "abi_layout.c"), "-o", exe], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=60, check=True).stdout
+    structs = {"vplbm_config": V.vplbm_config, "vplbm_body": V.vplbm_body}
+    rename = {"lambda": "lam"}
+    seen = {name: [] for name in structs}
+    for line in out.split("\n"):
+        if not line:
+            continue
+        sname, field, *nums = line.split()
+        S = structs[sname]
+        if field == "sizeof":
+            assert ctypes.sizeof(S) == int(nums[0]), (sname, ctypes.sizeof(S), nums)
+            continue
+        desc = getattr(S, rename.get(field, field))
+        assert (desc.offset, desc.size) == (int(nums[0]), int(nums[1])), (sname, field, nums)
+        seen[sname].append(rename.get(field, field))
+    for sname, S in structs.items():
+        assert seen[sname] == [f[0] for f in S._fields_], sname
