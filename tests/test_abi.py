@@ -128,3 +128,23 @@ def test_binding_structs_match_the_header(tmp_path):
         seen[sname].append(rename.get(field, field))
     for sname, S in structs.items():
         assert seen[sname] == [f[0] for f in S._fields_], sname
+
+
+def test_torch_allocator_binds_one_stream_without_gpu():
+    """The binding's stream rule for the device memory hook, on raw handles
+    (no CUDA call): the allocator's stream becomes the config's; a config on
+    another stream, or the legacy NULL stream, is refused."""
+    from paper_1812_05401_gb300 import vplbm as V
+    A = V.TorchAllocator(stream=0x1230, device=0)
+    c = V.make_config(64, 32, allocator=A)
+    assert c.stream == 0x1230 and bool(c.dev_alloc) and bool(c.dev_free)
+    assert c._allocator is A and A.allocs == A.frees == 0
+    assert V.make_config(64, 32, stream=0x1230, allocator=A).stream == 0x1230
+    with pytest.raises(ValueError):
+        V.make_config(64, 32, stream=0x4560, allocator=A)
+    with pytest.raises(ValueError):
+        V.make_config(64, 32, allocator=V.TorchAllocator(stream=0, device=0))
+    # a config's own stream binds an allocator made without one
+    B = V.TorchAllocator(device=0)
+    assert V.make_config(64, 32, stream=0x7890, allocator=B).stream == 0x7890
+    assert B.stream == 0x7890
