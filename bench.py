@@ -66,7 +66,7 @@ def hbm_peak():
 def traffic_per_launch(workload: str, storage: str, streaming: str = "ab"):
     """DRAM bytes per fused launch from the committed ncu summary, if it was
     taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "fused_step_traffic.json")
+    p = os.path.join(ROOT, "profiles", "fused_step_dram_moving_cylinder_16384x4096.json")
     try:
         d = json.load(open(p))
         e = d.get(f"{workload}:{storage}" + ("" if streaming == "ab" else f":{streaming}"))
