@@ -169,7 +169,10 @@ void vplbm_config_init(vplbm_config* cfg);
  * number re: nu = u_ref l_ref / re, tau = 3 nu + 1/2 (Section 2.1.1). */
 double vplbm_tau_from_reynolds(double u_ref, double l_ref, double re);
 
-/* Device bytes a solver with this configuration allocates (admission). */
+/* Device bytes a solver with this configuration allocates at creation
+ * (admission). Buffers taken later come on top when used: the static
+ * solid-velocity field, the momentum-exchange records, the staging buffers
+ * of host transfers. 0 for an invalid configuration. */
 size_t vplbm_footprint_bytes(const vplbm_config* cfg);
 
 /* Allocates the solver and sets the store to f*(0) = f_eq(rho0, u0) with an

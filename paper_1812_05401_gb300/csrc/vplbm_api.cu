@@ -698,6 +698,7 @@ size_t vplbm_footprint_bytes(const vplbm_config* c) {
   b += 3 * sizeof(double) * (size_t(nt) + size_t(ng));   // reduction partials
   b += sizeof(unsigned) * (size_t(ng) + 1);
   b += 3 * sizeof(double) * size_t(c->force_ring_len);
+  b += sizeof(int) + sizeof(kEmptyBox);                  // error flag, static solid box
   if (c->bc_x == VPLBM_BC_INLET_CONVECTIVE) b += 2 * 3 * size_t(c->ny) * ghost_elem(c->storage);
   return b;
 }

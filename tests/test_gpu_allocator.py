@@ -119,6 +119,21 @@ def test_grouped_solvers_on_the_hook():
     assert A.frees == A.allocs and A.live_bytes == 0
 
 
+@pytest.mark.parametrize("storage,streaming,bc", [
+    ("f32", "ab", "periodic"), ("f16", "aa", "channel-convective"), ("f64", "ab", "channel"),
+    ("bf16", "aa", "channel"), ("f32", "aa", "periodic"), ("f16", "ab", "channel-convective")])
+def test_footprint_is_what_creation_allocates(storage, streaming, bc):
+    """vplbm_footprint_bytes (the serving admission figure) equals, to the
+    byte, what vplbm_create takes through the hook."""
+    A = V.TorchAllocator()
+    cfg = V.make_config(1000, 333, "mrt", storage, 0.6, bc=bc, u_in=(0.05, 0.0), ring_len=777,
+                        streaming=streaming, allocator=A)
+    with V.Solver(cfg) as s:
+        assert A.live_bytes == V.vplbm_footprint_bytes(cfg)
+        s.step(2)
+    assert A.live_bytes == 0
+
+
 class _FailingAt(object):
     """Wraps a TorchAllocator so that its k-th allocation returns NULL."""
 
