@@ -18,8 +18,10 @@
  *    (component, then row, then column), populations [9][ny][nx] with the
  *    velocity order of Eq. vecteurs_D2Q9: 0 rest, 1..4 = E, N, W, S,
  *    5..8 = NE, NW, SW, SE.
- *  - The solver owns its device memory; the caller owns every pointer it
- *    passes and every output buffer. Nothing is retained after a call returns.
+ *  - The solver owns its device memory (taken from the caller's allocator when
+ *    the configuration sets the device memory hook); the caller owns every
+ *    pointer it passes and every output buffer. Nothing is retained after a
+ *    call returns.
  *  - Calls are asynchronous on the solver's stream unless stated; a call that
  *    returns data to the host synchronizes that stream.
  *  - No C++ exception crosses the ABI. A failing call returns a status and
@@ -56,7 +58,8 @@ enum { VPLBM_SRT = 0, /* BGK, Eq. LatticeBoltz with Guo forcing, Eq. Guo1 */
 /* Population storage. Arithmetic is FP64 for VPLBM_F64 and FP32 otherwise.
  * VPLBM_F64 stores f_alpha; VPLBM_F32 stores f_alpha - w_alpha in 32 bits
  * (the same bytes, a finer rounding step); the *_OFFSET forms store
- * f_alpha - w_alpha in 16 bits (round to nearest even). */
+ * f_alpha - w_alpha in 16 bits, rounded as vplbm_config.rounding says
+ * (stochastically by default). */
 enum { VPLBM_F64 = 0, VPLBM_F32 = 1, VPLBM_F16_OFFSET = 2, VPLBM_BF16_OFFSET = 3 };
 
 /* Rounding of the 16-bit stores. NEAREST: round to nearest even.
