@@ -25,6 +25,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -40,10 +41,21 @@ KERNEL_SOURCES = ["paper_1812_05401_gb300/csrc/vplbm_device.cuh", "paper_1812_05
                   "paper_1812_05401_gb300/csrc/vplbm_kernels_impl.cuh"]
 
 
+def _code_only(text: str) -> str:
+    """Kernel source without its comments and with runs of blank space made
+    one space: an edit to a comment leaves the compiled kernel, and so its
+    hash, unchanged. (No string literal in these sources holds // or /*.)"""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_hash() -> str:
+    """Identifies the fused kernel's code (its comments aside); DRAM counters
+    taken on another code are not reported as this kernel's traffic."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+        h.update(_code_only(open(os.path.join(ROOT, f)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -6,7 +6,7 @@
  * kernel that, for every node (fluid and solid alike, Section 2.2), pulls the
  * nine populations, forms the density (Eq. density) and the implicit penalized
  * velocity (Eq. vitesse_fluide_penalisation_1), evaluates the penalization
- * force f = -rho (chi/eta)(u - u_s) (Eq. 261), collides with SRT + Guo
+ * force f = -rho (chi/eta)(u - u_s) (Eq. 17), collides with SRT + Guo
  * forcing (Eqs. LatticeBoltz, Guo1) or MRT + Lu forcing (Eqs. equa_lbl_mrt,
  * Guo2), writes the post-collision populations, and reduces in FP64 the force
  * on the solids and the total mass. Moving rigid bodies get their staircase
@@ -198,7 +198,7 @@ vplbm_status vplbm_set_initial_velocity(vplbm_solver* s, const double* u);
 vplbm_status vplbm_set_initial_perturbation(vplbm_solver* s, double u0x, double u0y, double amp,
                                             uint64_t seed);
 
-/* Static mask and solid velocity (Section 2.2, Eq. 261): chi [ny][nx] bytes,
+/* Static mask and solid velocity (Section 2.2, Eq. 17): chi [ny][nx] bytes,
  * nonzero = solid; us [2][ny][nx] doubles or NULL (u_s = 0). on_device = 1:
  * both are device pointers. Replaces any earlier static mask; bodies set with
  * vplbm_set_bodies stay, and a static solid node takes precedence. */
@@ -251,7 +251,7 @@ vplbm_status vplbm_save_state(vplbm_solver* s, void* buf);
 vplbm_status vplbm_load_state(vplbm_solver* s, const void* buf);
 
 /* Per-step record since the previous call (synchronizes): F_x, F_y, the force
- * the fluid exerts on all solid nodes (minus the sum of Eq. 261 over them,
+ * the fluid exerts on all solid nodes (minus the sum of Eq. 17 over them,
  * reduced in FP64), and the total density (0 if reduce_mass = 0). Returns up
  * to cap entries, oldest first, in *count; if more than force_ring_len steps
  * went unread the oldest were overwritten. Any pointer may be NULL. */

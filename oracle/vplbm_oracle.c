@@ -229,15 +229,15 @@ void orc_guo_force_srt(double tau, double ux, double uy, double fx, double fy,
  * ------------------------------------------------------------------------- */
 
 /* Density (Eq. density), implicit velocity (Eq. vitesse_fluide_penalisation_1)
- * and penalization force (Eq. 261) of one node.
+ * and penalization force (Eq. 17) of one node.
  *
  * Velocity: rho u = sum xi f + (1/2) f_tot (Eq. velocity) with the total force
  * f_tot = f_pen + rho g and f_pen = -rho (chi/eta)(u - u_s). Solving for u gives
- * Eq. 276, extended by the uniform body force g:
+ * Eq. 18, extended by the uniform body force g:
  *   u = (j + rho g/2 + (chi/(2 eta)) rho u_s) / (rho + (chi/(2 eta)) rho).
- * Force: substituting that u into Eq. 261 gives, exactly,
+ * Force: substituting that u into Eq. 17 gives, exactly,
  *   f_pen = -kappa (j + rho g/2 - rho u_s),  kappa = (chi/eta) / (1 + chi/(2 eta)),
- * which is Eq. 261 without the subtraction u - u_s of two nearly equal numbers
+ * which is Eq. 17 without the subtraction u - u_s of two nearly equal numbers
  * whose rounding error chi/eta = 1e7 would multiply. */
 static void node_macros(const orc_model* m, const orc_config* c, const double f[9],
                         int32_t chi, double usx, double usy, double* rho,
@@ -268,7 +268,7 @@ void orc_node_macros(const orc_config* c, const double f[9], int32_t chi,
   node_macros(&m, c, f, chi, usx, usy, rho, ux, uy, fpx, fpy);
 }
 
-/* Literal Eqs. 276 and 261: the same u, then f_pen = -rho (chi/eta)(u - u_s). */
+/* Literal Eqs. 18 and 17: the same u, then f_pen = -rho (chi/eta)(u - u_s). */
 void orc_node_macros_literal(const orc_config* c, const double f[9], int32_t chi,
                              double usx, double usy, double* rho, double* ux,
                              double* uy, double* fpx, double* fpy) {

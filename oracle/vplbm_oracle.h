@@ -76,12 +76,12 @@ void orc_guo_force_srt(double tau, double ux, double uy, double fx, double fy, d
 void orc_guo_force_mrt(double ux, double uy, double fx, double fy, double F[9]);
 void orc_mrt_equilibrium_moments(double rho, double ux, double uy, double meq[9]);
 
-/* Macroscopic step of one node: density, implicit velocity (Eq. 276) and the
- * penalization force (Eq. 261) for mask value chi and solid velocity us. */
+/* Macroscopic step of one node: density, implicit velocity (Eq. 18) and the
+ * penalization force (Eq. 17) for mask value chi and solid velocity us. */
 void orc_node_macros(const orc_config* c, const double f[9], int32_t chi,
                      double usx, double usy, double* rho, double* ux, double* uy,
                      double* fpx, double* fpy);
-/* The same quantities from the literal Eqs. 276 and 261 (for the pin test of
+/* The same quantities from the literal Eqs. 18 and 17 (for the pin test of
  * the algebraically rearranged force). */
 void orc_node_macros_literal(const orc_config* c, const double f[9], int32_t chi,
                              double usx, double usy, double* rho, double* ux,

@@ -360,10 +360,10 @@ __device__ __forceinline__ void pull_node(const StepParams& p, const typename S:
 
 // ---------------------------------------------------------------------------
 // Density, implicit velocity and penalization force of one node
-// (Eqs. density, velocity, 261 and 276).
+// (Eqs. density, velocity, 17 and 18).
 //   d = j + rho g / 2 - rho u_s,  u = u_s + d / (rho (1 + a)),
 //   f_pen = -kappa d,  a = chi/(2 eta),  kappa = (chi/eta)/(1 + a).
-// This is Eq. 276 rewritten so that neither u - u_s nor a rho u_s appear:
+// This is Eq. 18 rewritten so that neither u - u_s nor a rho u_s appear:
 // the 1/eta factor never multiplies a rounding error.
 // ---------------------------------------------------------------------------
 // Correctly rounded reciprocal.

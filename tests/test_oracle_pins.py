@@ -123,7 +123,7 @@ def test_implicit_velocity_solves_its_definition(seed):
         ftot = np.array([fpx, fpy]) + rho * np.array(cfg.g)
         # Eq. velocity: rho u = sum xi f + f_tot / 2.
         np.testing.assert_allclose(rho * np.array([ux, uy]), j + 0.5 * ftot, rtol=0, atol=1e-16)
-        # Eq. 261: f_pen = -rho (chi/eta)(u - u_s); compare in the form that
+        # Eq. 17: f_pen = -rho (chi/eta)(u - u_s); compare in the form that
         # does not amplify rounding: u - u_s = -f_pen eta / (rho chi).
         if chi:
             np.testing.assert_allclose(np.array([ux - usx, uy - usy]),
@@ -133,7 +133,7 @@ def test_implicit_velocity_solves_its_definition(seed):
             assert np.hypot(ux - usx, uy - usy) <= slip0 / (1.0 + 0.5 / cfg.eta) * (1 + 1e-9)
         else:
             assert fpx == 0.0 and fpy == 0.0
-        # Literal Eq. 276 + Eq. 261 agree with the rearranged force to the
+        # Literal Eq. 18 + Eq. 17 agree with the rearranged force to the
         # literal form's own rounding (chi/eta times the rounding of u).
         lit = O.node_macros(cfg, f, chi, usx, usy, literal=True)
         np.testing.assert_allclose(lit[1:3], (ux, uy), rtol=1e-14, atol=1e-17)
@@ -152,7 +152,7 @@ def test_single_node_collision_exact_rational_brute_force():
         rho = sum(Fraction(v) for v in f)
         jx = sum(Fraction(int(xi[a, 0])) * Fraction(f[a]) for a in range(9))
         jy = sum(Fraction(int(xi[a, 1])) * Fraction(f[a]) for a in range(9))
-        # exact kappa-form force from the exact j (Eq. 261 with Eq. 276)
+        # exact kappa-form force from the exact j (Eq. 17 with Eq. 18)
         ce = Fraction(chi) / Fraction(cfg.eta)
         kappa = ce / (1 + ce / 2)
         fx = -kappa * (jx - rho * Fraction(us[0]))
