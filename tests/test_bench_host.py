@@ -97,3 +97,15 @@ def test_algorithmic_bytes_per_node(storage, expected):
     """9 populations read and written in the storage type plus the 1-byte mask."""
     size = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}[storage]
     assert bench.ALGO_BYTES[storage] == expected == 2 * 9 * size + 1
+
+
+def test_clock_records_that_disqualify_a_run():
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 9}
+    assert bench.clocks_rejected(ok) is None
+    assert bench.clocks_rejected(None) is None  # nvidia-smi unavailable: nothing to judge
+    capped = dict(ok, sm_mhz=1500.0, reasons=["sw_power_cap"])
+    assert bench.clocks_rejected(capped) is None  # kept, and noted by its reasons
+    assert bench.clocks_rejected(dict(ok, reasons=["hw_slowdown"])) == "hw_slowdown"
+    assert bench.clocks_rejected(dict(ok, reasons=["sw_power_cap", "sw_thermal_slowdown"])) \
+        == "sw_thermal_slowdown"
+    assert "no reason" in bench.clocks_rejected(dict(ok, sm_mhz=1200.0))  # a leftover clock lock
