@@ -66,7 +66,13 @@ def test_invalid_configs_rejected_without_gpu(lib):
     for kw in (dict(nx=0, ny=4), dict(nx=4, ny=4, tau=0.5), dict(nx=4, ny=4, eta=0.0),
                dict(nx=4, ny=4, storage=7), dict(nx=4, ny=4, ring_len=0),
                dict(nx=4, ny=4, streaming=2), dict(nx=4, ny=4, bc=(3, 2), u_in=(0.05, 0.0),
-                                                   u_conv=-1.0)):
+                                                   u_conv=-1.0),
+               dict(nx=1 << 17, ny=1 << 18),  # 2^35 nodes: beyond the 2^34 limit
+               dict(nx=4, ny=4, rounding=5), dict(nx=4, ny=4, collision=2),
+               dict(nx=4, ny=4, bc=(2, 0)),  # free slip is a y condition only
+               dict(nx=4, ny=4, bc=(0, 1)),  # inlet/outlet is an x condition only
+               dict(nx=4, ny=4, tau=float("nan")), dict(nx=4, ny=4, rho0=0.0),
+               dict(nx=4, ny=4, collision="mrt", lam=0.0)):
         nx, ny = kw.pop("nx"), kw.pop("ny")
         c = V.make_config(nx, ny, **kw)
         with pytest.raises(V.VplbmError) as e:
