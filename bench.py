@@ -540,6 +540,53 @@ def run_serving(args, n_requests=None, rate=None, storage=None, quiet=False, wan
     return (rep, results) if want_results else rep
 
 
+def run_grouped(args):
+    """Grouped-launch throughput by grid size (the serving kernel): for each
+    side s, a batch of k cylinder channels of 4s x s nodes (k s.t. the batch
+    holds ~16M nodes; diameter 40 s / 256, Re 200, FP32, SRT and MRT
+    alternating) advanced by vplbm_group_step; CUDA events around `steps`
+    grouped steps after 20 untimed ones. Prints one JSON line."""
+    import torch
+
+    from paper_1812_05401_gb300 import inputs as I
+    from paper_1812_05401_gb300 import vplbm as V
+    stream = torch.cuda.Stream()
+    rows = []
+    for side in args.grouped:
+        nx, ny = 4 * side, side
+        k = max(1, (16 << 20) // (nx * ny))
+        solvers = []
+        try:
+            for i in range(k):
+                w = I.cylinder_channel(nx, ny, max(4.0, round(40 * side / 256)), 0.05, 200.0, 0,
+                                       storage="f32", seed=i + 1)
+                w.collision = "mrt" if i % 2 else "srt"
+                solvers.append(V.Solver.from_workload(w, stream=stream, ring_len=args.steps + 32))
+            hs = [x.h for x in solvers]
+            V.vplbm_group_step(hs, [20] * k)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+            V.vplbm_group_step(hs, [args.steps] * k)
+            with torch.cuda.stream(stream):
+                e1.record(stream)
+            torch.cuda.synchronize()
+            for x in solvers:
+                x.synchronize()  # raises if a solve diverged
+            ms = e0.elapsed_time(e1)
+            rows.append({"grid": f"{nx}x{ny}", "solves": k, "nodes": k * nx * ny,
+                         "steps": args.steps, "ms_per_step": round(ms / args.steps, 4),
+                         "mlups": round(k * nx * ny * args.steps / (ms / 1e3) / 1e6, 1)})
+        finally:
+            for x in solvers:
+                x.close()
+    print(json.dumps({"metric": "grouped-launch MLUPS by grid size (FP32 cylinder channels, "
+                                "SRT/MRT alternating, ~16M nodes per batch)", "unit": "MLUPS",
+                      "grouped": rows}), flush=True)
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle on the host cores. One step = one oracle
     step over a window of the workload's grid (rows around the body, at most
@@ -628,6 +675,10 @@ def main():
                     help="Poisson arrival rate of the serving measurement in the default run "
                          "(0.8 x the measured closed-loop capacity of 9.8 solves/s)")
     ap.add_argument("--serve-round", type=int, default=500)
+    ap.add_argument("--grouped", type=lambda v: [int(x) for x in v.split(",")], default=None,
+                    metavar="S1,S2,...",
+                    help="grouped-launch throughput for batches of 4S x S channels (serving "
+                         "kernel), timed over --steps grouped steps (e.g. --steps 200)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -641,6 +692,8 @@ def main():
             B.build()
         if args.serving:
             run_serving_passes(args)
+        elif args.grouped:
+            run_grouped(args)
         else:
             run_gpu(args)
 
