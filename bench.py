@@ -671,9 +671,9 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--no-serving", dest="serve_in_bench", action="store_false",
                     help="skip the serving measurement in the default run")
-    ap.add_argument("--serve-rate-bench", type=float, default=7.8,
+    ap.add_argument("--serve-rate-bench", type=float, default=8.2,
                     help="Poisson arrival rate of the serving measurement in the default run "
-                         "(0.8 x the measured closed-loop capacity of 9.8 solves/s)")
+                         "(0.8 x the measured closed-loop capacity of 10.2 solves/s)")
     ap.add_argument("--serve-round", type=int, default=500)
     ap.add_argument("--grouped", type=lambda v: [int(x) for x in v.split(",")], default=None,
                     metavar="S1,S2,...",
