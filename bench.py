@@ -184,13 +184,13 @@ def replica_totals(units: float, ms: float, device=None):
 
 def make_workload(name: str, storage: str):
     from paper_1812_05401_gb300 import inputs as I
-    if name == "moving-cylinder":
-        return I.c5_moving_cylinder(storage)
-    if name == "cylinder-re1000":
-        return I.c3_cylinder_re1000(storage)
-    if name == "cylinder-re100":
-        return I.c2_cylinder_re100()
-    raise ValueError(name)
+    makers = {"moving-cylinder": I.c5_moving_cylinder, "cylinder-re1000": I.c3_cylinder_re1000,
+              "cylinder-re100": I.c2_cylinder_re100, "circular-couette": I.c1_circular_couette}
+    if name not in makers:
+        raise ValueError(name)
+    w = makers[name]()
+    w.storage = storage
+    return w
 
 
 # -----------------------------------------------------------------------------
@@ -407,6 +407,16 @@ def run_gpu(args):
 
     peak, peak_src = hbm_peak()
     l2_bytes = getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0)
+    esize = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}[args.storage]
+    pop_bytes = (2 if args.streaming == "ab" else 1) * 9 * nodes * esize
+    resident = pop_bytes < l2_bytes
+    if resident:
+        l2_note = ("inputs fit in L2 (%.0f MB): population buffers of %.1f MB, cache-resident, so "
+                   "the roofline fraction is not a DRAM figure" % (l2_bytes / 1e6, pop_bytes / 1e6))
+    else:
+        l2_note = "inputs larger than L2 (%.0f MB): %s population buffer%s of %.2f GB" % (
+            l2_bytes / 1e6, "two" if args.streaming == "ab" else "one in-place",
+            "s" if args.streaming == "ab" else "", 9 * nodes * esize / 1e9)
     kms = fused_ms / max(fused_n, 1)
     achieved = ALGO_BYTES[args.storage] * nodes / (kms / 1e3) / 1e9
     traffic = traffic_per_launch(args.workload, args.storage, args.streaming)
@@ -428,10 +438,7 @@ def run_gpu(args):
                    "collision": w.collision, "re": w.re, "u_in": w.u_ref,
                    "step": "mask update of the moving body + fused pull/penalize/collide/reduce kernel",
                    "streaming": args.streaming,
-                   "l2": "inputs larger than L2 (%.0f MB): %s population buffer%s of %.2f GB" % (
-                       l2_bytes / 1e6, "two" if args.streaming == "ab" else "one in-place",
-                       "s" if args.streaming == "ab" else "",
-                       9 * nodes * {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}[args.storage] / 1e9),
+                   "l2": l2_note,
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": round(e2e, 1), "unit": "MLUPS", "h2d_bytes_per_step": 704,
                 "d2h_bytes_per_step": 24,
@@ -439,10 +446,11 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_source": f"{peak_src} copy bandwidth",
-                     "kernel": f"fused_step_kernel<{args.storage.upper()},MRT>" + (
+                     "kernel": f"fused_step_kernel<{args.storage.upper()},{w.collision.upper()}>" + (
                          "" if args.streaming == "ab" else " (in place: push and local steps)"),
                      "kernel_ms": round(kms, 4), "algo_bytes_per_node": ALGO_BYTES[args.storage],
-                     "algo_bytes_per_launch": ALGO_BYTES[args.storage] * nodes},
+                     "algo_bytes_per_launch": ALGO_BYTES[args.storage] * nodes,
+                     "cache_resident": resident},
         "gpu_launches": launches,
         "clocks": clk,
     }
@@ -652,7 +660,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="moving-cylinder",
-                    choices=["moving-cylinder", "cylinder-re1000", "cylinder-re100"])
+                    choices=["moving-cylinder", "cylinder-re1000", "cylinder-re100",
+                             "circular-couette"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f64"])
     ap.add_argument("--no-compare-f16", dest="compare_f16", action="store_false")
     ap.add_argument("--no-compare-aa", dest="compare_aa", action="store_false",

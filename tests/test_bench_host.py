@@ -109,3 +109,11 @@ def test_clock_records_that_disqualify_a_run():
     assert bench.clocks_rejected(dict(ok, reasons=["sw_power_cap", "sw_thermal_slowdown"])) \
         == "sw_thermal_slowdown"
     assert "no reason" in bench.clocks_rejected(dict(ok, sm_mhz=1200.0))  # a leftover clock lock
+
+
+@pytest.mark.parametrize("name,nx,ny,collision", [
+    ("circular-couette", 128, 128, "srt"), ("cylinder-re100", 1024, 256, "mrt"),
+    ("cylinder-re1000", 4096, 1024, "mrt"), ("moving-cylinder", 16384, 4096, "mrt")])
+def test_workloads_are_the_configurations_and_take_the_storage(name, nx, ny, collision):
+    w = bench.make_workload(name, "bf16")
+    assert (w.nx, w.ny, w.collision, w.storage) == (nx, ny, collision, "bf16")
