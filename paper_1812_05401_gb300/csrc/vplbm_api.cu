@@ -1315,6 +1315,7 @@ vplbm_status vplbm_set_initial_perturbation(vplbm_solver* s, double u0x, double 
 vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int64_t* steps) {
   if (n < 0 || (n > 0 && (!solvers || !steps))) return VPLBM_ERR_INVALID;
   if (n == 0) return VPLBM_OK;
+  if (!solvers[0]) return VPLBM_ERR_INVALID;
   cudaStream_t stream = solvers[0]->stream;
   int64_t max_steps = 0;
   for (int i = 0; i < n; ++i) {
