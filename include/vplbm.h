@@ -245,10 +245,12 @@ vplbm_status vplbm_mask(vplbm_solver* s, uint8_t* chi);
  * solver created with the same grid, storage, outlet and streaming scheme
  * (and the same bodies, whose motion depends on t): stepping on from a loaded
  * state is bitwise identical to never having stopped. INVALID if the state
- * does not match the solver. */
+ * does not match the solver. `bytes` is the size of buf: save refuses a
+ * buffer shorter than vplbm_state_bytes, load one shorter than the state its
+ * header describes (INVALID), so neither call reads or writes past it. */
 size_t vplbm_state_bytes(const vplbm_solver* s);
-vplbm_status vplbm_save_state(vplbm_solver* s, void* buf);
-vplbm_status vplbm_load_state(vplbm_solver* s, const void* buf);
+vplbm_status vplbm_save_state(vplbm_solver* s, void* buf, size_t bytes);
+vplbm_status vplbm_load_state(vplbm_solver* s, const void* buf, size_t bytes);
 
 /* Per-step record since the previous call (synchronizes): F_x, F_y, the force
  * the fluid exerts on all solid nodes (minus the sum of Eq. 17 over them,

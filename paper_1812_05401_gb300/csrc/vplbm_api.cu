@@ -1119,10 +1119,12 @@ size_t vplbm_state_bytes(const vplbm_solver* s) {
          ghost_bytes(s) + side_bytes(s);
 }
 
-vplbm_status vplbm_save_state(vplbm_solver* s, void* buf) {
+vplbm_status vplbm_save_state(vplbm_solver* s, void* buf, size_t bytes) {
   vplbm_status st = check_usable(s);
   if (st != VPLBM_OK) return st;
   if (!buf) return fail(s, VPLBM_ERR_INVALID, "buffer is NULL");
+  if (bytes < vplbm_state_bytes(s))
+    return fail(s, VPLBM_ERR_INVALID, "buffer shorter than vplbm_state_bytes");
   if ((st = ensure_mask(s, s->t)) != VPLBM_OK) return st;
   StateHeader h{};
   h.magic = kStateMagic;
@@ -1163,12 +1165,24 @@ vplbm_status vplbm_save_state(vplbm_solver* s, void* buf) {
   return VPLBM_OK;
 }
 
-vplbm_status vplbm_load_state(vplbm_solver* s, const void* buf) {
+vplbm_status vplbm_load_state(vplbm_solver* s, const void* buf, size_t bytes) {
   vplbm_status st = check_usable(s);
   if (st != VPLBM_OK) return st;
   if (!buf) return fail(s, VPLBM_ERR_INVALID, "buffer is NULL");
+  if (bytes < sizeof(StateHeader)) return fail(s, VPLBM_ERR_INVALID, "buffer shorter than a state");
   StateHeader h;
   std::memcpy(&h, buf, sizeof(h));
+  // every section the header announces must lie inside the buffer (each size
+  // is checked against the buffer alone first, so the sum cannot wrap)
+  const uint64_t avail = uint64_t(bytes) - sizeof(h);
+  const uint64_t parts[5] = {h.pop_bytes, h.mask_bytes, h.has_us ? h.us_bytes : 0, h.ghost_bytes,
+                             h.side_bytes};
+  uint64_t total = 0;
+  for (uint64_t b : parts) {
+    if (b > avail || total + b > avail)
+      return fail(s, VPLBM_ERR_INVALID, "buffer shorter than the state its header describes");
+    total += b;
+  }
   if (h.magic != kStateMagic || h.nx != s->cfg.nx || h.ny != s->cfg.ny || h.pitch != s->pitch ||
       h.storage != s->cfg.storage || h.pop_bytes != 9 * uint64_t(s->plane) * s->esize ||
       h.mask_bytes != uint64_t(s->plane) || h.t < 0 || h.ghost_bytes != ghost_bytes(s) ||

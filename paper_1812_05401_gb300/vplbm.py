@@ -91,8 +91,8 @@ def lib() -> C.CDLL:
         L.vplbm_forces_async.argtypes = [P, dp, C.c_int64, C.POINTER(C.c_int64)]
         L.vplbm_state_bytes.argtypes = [P]
         L.vplbm_state_bytes.restype = C.c_size_t
-        L.vplbm_save_state.argtypes = [P, P]
-        L.vplbm_load_state.argtypes = [P, P]
+        L.vplbm_save_state.argtypes = [P, P, C.c_size_t]
+        L.vplbm_load_state.argtypes = [P, P, C.c_size_t]
         L.vplbm_set_mask_and_solid_velocity.argtypes = [P, P, P, C.c_int32]
         L.vplbm_set_bodies.argtypes = [P, C.POINTER(vplbm_body), C.c_int32]
         L.vplbm_step.argtypes = [P, C.c_int64]
@@ -155,9 +155,14 @@ def _check(handle, st: int, what: str):
         raise VplbmError(st, f"{what}: {lib().vplbm_status_string(st).decode()} {msg}".strip())
 
 
+# Grid of each handle made by vplbm_create here, for the buffer checks below.
+_grids: dict = {}
+
+
 def vplbm_create(cfg: vplbm_config) -> int:
     h = C.c_void_p()
     _check(None, lib().vplbm_create(C.byref(cfg), C.byref(h)), "vplbm_create")
+    _grids[h.value] = (cfg.nx, cfg.ny)
     return h.value
 
 
@@ -169,10 +174,36 @@ def _dev(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _buffer(h, a, per_node: int, dtype, on_device: bool, what: str, write: bool = False):
+    """Refuses, before the library sees it, a buffer that it would read or
+    write past the end of: the C calls take bare pointers and fill whole
+    fields ([per_node][ny][nx] elements). Checks the element type, that the
+    memory is contiguous (and writable for an output), that a device buffer
+    is a CUDA tensor and a host buffer a numpy array, and the element count
+    when the handle's grid is known."""
+    if on_device:
+        import torch
+        tdt = {np.float64: torch.float64, np.uint8: torch.uint8}[dtype]
+        ok = isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == tdt and a.is_contiguous()
+        n = a.numel() if ok else 0
+    else:
+        ok = (isinstance(a, np.ndarray) and a.dtype == dtype and a.flags.c_contiguous
+              and (a.flags.writeable or not write))
+        n = a.size if ok else 0
+    grid = _grids.get(h)
+    need = None if grid is None else per_node * grid[0] * grid[1]
+    if not ok or (need is not None and n != need):
+        kind = "CUDA tensor" if on_device else "numpy array"
+        size = "" if need is None else f" of {need} elements"
+        raise ValueError(f"{what}: needs a contiguous{' writable' if write else ''} "
+                         f"{np.dtype(dtype).name} {kind}{size}")
+
+
 def vplbm_set_initial_velocity(h, u=None):
     dp = None
     if u is not None:
         u = np.ascontiguousarray(u, dtype=np.float64)
+        _buffer(h, u, 2, np.float64, False, "vplbm_set_initial_velocity")
         dp = u.ctypes.data_as(C.POINTER(C.c_double))
     _check(h, lib().vplbm_set_initial_velocity(h, dp), "vplbm_set_initial_velocity")
 
@@ -185,6 +216,9 @@ def vplbm_set_initial_perturbation(h, u0x: float, u0y: float, amp: float, seed: 
 def vplbm_forces_async(h, records) -> int:
     """records: page-locked float64 array [cap][3] (e.g. a pinned torch
     tensor's numpy view); valid once the solver's stream reaches this point."""
+    if not (isinstance(records, np.ndarray) and records.dtype == np.float64 and records.ndim == 2
+            and records.shape[1] == 3 and records.flags.c_contiguous and records.flags.writeable):
+        raise ValueError("vplbm_forces_async: needs a contiguous writable float64 array [cap][3]")
     cnt = C.c_int64()
     _check(h, lib().vplbm_forces_async(h, records.ctypes.data_as(C.POINTER(C.c_double)),
                                        records.shape[0], C.byref(cnt)), "vplbm_forces_async")
@@ -196,23 +230,31 @@ def vplbm_state_bytes(h) -> int:
 
 
 def vplbm_save_state(h) -> bytes:
-    buf = (C.c_char * vplbm_state_bytes(h))()
-    _check(h, lib().vplbm_save_state(h, buf), "vplbm_save_state")
+    n = vplbm_state_bytes(h)
+    buf = (C.c_char * n)()
+    _check(h, lib().vplbm_save_state(h, buf, n), "vplbm_save_state")
     return bytes(buf)
 
 
 def vplbm_load_state(h, state: bytes):
-    buf = (C.c_char * len(state)).from_buffer_copy(state)
-    _check(h, lib().vplbm_load_state(h, buf), "vplbm_load_state")
+    buf = (C.c_char * max(1, len(state))).from_buffer_copy(bytes(state) or b"\0")
+    _check(h, lib().vplbm_load_state(h, buf, len(state)), "vplbm_load_state")
 
 
 def vplbm_set_mask_and_solid_velocity(h, chi, us=None, on_device: bool = False):
+    what = "vplbm_set_mask_and_solid_velocity"
     if on_device:
+        _buffer(h, chi, 1, np.uint8, True, what)
+        if us is not None:
+            _buffer(h, us, 2, np.float64, True, what)
         _check(h, lib().vplbm_set_mask_and_solid_velocity(
             h, _dev(chi), None if us is None else _dev(us), 1), "vplbm_set_mask_and_solid_velocity")
         return
     chi = np.ascontiguousarray(chi, dtype=np.uint8)
     us = None if us is None else np.ascontiguousarray(us, dtype=np.float64)
+    _buffer(h, chi, 1, np.uint8, False, what)
+    if us is not None:
+        _buffer(h, us, 2, np.float64, False, what)
     _check(h, lib().vplbm_set_mask_and_solid_velocity(h, _ptr(chi), _ptr(us), 0),
            "vplbm_set_mask_and_solid_velocity")
 
@@ -238,6 +280,8 @@ def vplbm_step_count(h) -> int:
 
 
 def vplbm_moments(h, rho, ux, uy, on_device: bool = False):
+    for a in (rho, ux, uy):
+        _buffer(h, a, 1, np.float64, on_device, "vplbm_moments", write=True)
     if on_device:
         _check(h, lib().vplbm_moments(h, _dev(rho), _dev(ux), _dev(uy), 1), "vplbm_moments")
     else:
@@ -245,6 +289,7 @@ def vplbm_moments(h, rho, ux, uy, on_device: bool = False):
 
 
 def vplbm_populations(h, f, on_device: bool = False):
+    _buffer(h, f, 9, np.float64, on_device, "vplbm_populations", write=True)
     _check(h, lib().vplbm_populations(h, _dev(f) if on_device else _ptr(f), int(on_device)),
            "vplbm_populations")
 
@@ -252,11 +297,13 @@ def vplbm_populations(h, f, on_device: bool = False):
 def vplbm_set_populations(h, f, on_device: bool = False):
     if not on_device:
         f = np.ascontiguousarray(f, dtype=np.float64)
+    _buffer(h, f, 9, np.float64, on_device, "vplbm_set_populations")
     _check(h, lib().vplbm_set_populations(h, _dev(f) if on_device else _ptr(f), int(on_device)),
            "vplbm_set_populations")
 
 
 def vplbm_mask(h, chi):
+    _buffer(h, chi, 1, np.uint8, False, "vplbm_mask", write=True)
     _check(h, lib().vplbm_mask(h, _ptr(chi)), "vplbm_mask")
 
 
@@ -320,6 +367,7 @@ def vplbm_last_error(h) -> str:
 
 def vplbm_destroy(h):
     lib().vplbm_destroy(h)
+    _grids.pop(h, None)
 
 
 # ---------------------------------------------------------------------------

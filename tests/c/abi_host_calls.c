@@ -85,8 +85,9 @@ int main(void) {
         vplbm_synchronize(NULL) != inv || vplbm_moments(NULL, d, d, d, 0) != inv ||
         vplbm_populations(NULL, d, 0) != inv || vplbm_set_populations(NULL, d, 0) != inv ||
         vplbm_mask(NULL, chi) != inv || vplbm_forces(NULL, d, d, d, 1, &cnt) != inv ||
-        vplbm_forces_async(NULL, d, 1, &cnt) != inv || vplbm_save_state(NULL, buf) != inv ||
-        vplbm_load_state(NULL, buf) != inv || vplbm_momentum_exchange(NULL, d, d) != inv ||
+        vplbm_forces_async(NULL, d, 1, &cnt) != inv ||
+        vplbm_save_state(NULL, buf, sizeof(buf)) != inv ||
+        vplbm_load_state(NULL, buf, sizeof(buf)) != inv || vplbm_momentum_exchange(NULL, d, d) != inv ||
         vplbm_enable_momentum_exchange(NULL, 1) != inv ||
         vplbm_momentum_exchange_forces(NULL, d, d, 1, &cnt) != inv ||
         vplbm_enable_timing(NULL, 1) != inv || vplbm_fused_timing(NULL, d, &cnt) != inv)
