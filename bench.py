@@ -538,7 +538,12 @@ def run_serving(args, n_requests=None, rate=None, storage=None, quiet=False, wan
     srv = serve.Server(budget_bytes=int(0.5 * free), max_active=args.serve_slots,
                        round_steps=args.serve_round)
     torch.cuda.synchronize()
-    results, rep = srv.run(reqs, realtime=rate > 0)
+    log = open(args.serve_log, "a") if args.serve_log else None
+    try:
+        results, rep = srv.run(reqs, realtime=rate > 0, log=log)
+    finally:
+        if log:
+            log.close()
     rep.update({"requests": n, "arrival_rate_per_s": rate if rate > 0 else "all at t=0",
                 "storage": storage or "f32/f16 50-50", "budget_bytes": int(0.5 * free),
                 "slots": args.serve_slots, "round_steps": args.serve_round,
@@ -684,6 +689,8 @@ def main():
                     help="Poisson arrival rate of the serving measurement in the default run "
                          "(0.8 x the measured closed-loop capacity of 10.2 solves/s)")
     ap.add_argument("--serve-round", type=int, default=500)
+    ap.add_argument("--serve-log", default=None, metavar="PATH",
+                    help="append one JSON line per served request (result, rejection or drop)")
     ap.add_argument("--grouped", type=lambda v: [int(x) for x in v.split(",")], default=None,
                     metavar="S1,S2,...",
                     help="grouped-launch throughput for batches of 4S x S channels (serving "

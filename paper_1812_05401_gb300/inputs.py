@@ -177,6 +177,7 @@ class Request:
     rid: int
     arrival: float           # seconds after the start of the run
     workload: Workload
+    deadline: float | None = None  # seconds after arrival the result is wanted by (None: no limit)
 
 
 def serving_mix(n_requests: int = 256, rate: float = 4.0, seed: int = 1234,

@@ -11,6 +11,12 @@ solves already running. A finished solve's force series is read back and its
 memory released once the GPU has completed its last round (CUDA event), which
 is the request's completion time; latency = completion - arrival.
 
+A request may carry a deadline (seconds after its arrival), and any thread may
+cancel one (Server.cancel). A withdrawn request that is still waiting is
+dropped; a running one stops at the next round boundary and is reported as
+failed, with the force series of the steps it ran. run(log=...) writes one
+JSON line per request: its result, or why it was rejected or dropped.
+
 All solves share one CUDA stream (grouped launches require it). The host never
 waits for the GPU except for the oldest round in flight: solver memory is
 allocated and released stream-ordered, the initial field is generated on the
@@ -21,6 +27,8 @@ deterministic fixed-order reductions.
 """
 from __future__ import annotations
 
+import json
+import threading
 import time
 from collections import deque
 from dataclasses import dataclass, field
@@ -37,14 +45,14 @@ class Result:
     arrival: float
     admitted: float
     finished: float
-    steps: int
+    steps: int               # steps run (fewer than requested for a solve stopped early)
     nodes: int
     storage: str
     collision: str
     fx: np.ndarray = field(repr=False, default=None)
     fy: np.ndarray = field(repr=False, default=None)
     populations: np.ndarray | None = field(repr=False, default=None)
-    error: str | None = None  # set if the solve diverged (its results are not valid)
+    error: str | None = None  # set if the solve diverged or was stopped (results not valid)
 
     @property
     def latency(self) -> float:
@@ -59,13 +67,16 @@ class _Active:
     admitted: float
     footprint: int
     records: object = None  # pinned [steps][3] float64 tensor, filled behind the last round
+    n_records: int = 0
+    stopped: str | None = None  # why the solve was stopped before its last step
 
 
 class Server:
     def __init__(self, budget_bytes: int, max_active: int = 256, round_steps: int = 500,
-                 stream=None, keep_populations: bool = False, on_admit=None):
+                 stream=None, keep_populations: bool = False, on_admit=None, clock=None):
         """on_admit(request, solver): optional hook called right after a solve is
-        created (before its first step)."""
+        created (before its first step). clock: the time source (seconds),
+        time.perf_counter by default."""
         import torch
         self.torch = torch
         self.budget = int(budget_bytes)
@@ -74,8 +85,19 @@ class Server:
         self.stream = stream or torch.cuda.Stream()
         self.keep_populations = keep_populations
         self.on_admit = on_admit
+        self.clock = clock or time.perf_counter
         self.rejected = []
         self.errors = {}
+        self.dropped = {}  # rid -> why a request was withdrawn before it ran
+        self._cancelled = set()
+        self._lock = threading.Lock()
+
+    def cancel(self, rid: int):
+        """Withdraws a request (from any thread): one still waiting is dropped,
+        one running stops at the next round boundary and is reported as
+        failed with the force series of the steps it ran."""
+        with self._lock:
+            self._cancelled.add(rid)
 
     def _create(self, w):
         cfg, bodies = V.config_from_workload(w, ring_len=max(1, w.steps), stream=self.stream,
@@ -84,19 +106,42 @@ class Server:
         s = V.Solver(cfg, bodies, perturbation=(u0[0], u0[1], w.perturbation, w.seed))
         return s, V.vplbm_footprint_bytes(cfg)
 
-    def run(self, requests, realtime: bool = True):
+    def run(self, requests, realtime: bool = True, log=None):
         """Serves the requests; returns (results, report). With realtime=False
-        every request counts as arrived at time 0."""
+        every request counts as arrived at time 0. log: a text stream that
+        gets one JSON line per request (its result, or why it was rejected or
+        dropped)."""
         torch = self.torch
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         active: list[_Active] = []
-        inflight = deque()  # (event, [finished _Active])
+        inflight = deque()  # (event, [finished or stopped _Active])
         results = []
         used = 0
-        t0 = time.perf_counter()
+        t0 = self.clock()
 
         def now():
-            return time.perf_counter() - t0
+            return self.clock() - t0
+
+        def arrived(req):
+            return req.arrival if realtime else 0.0
+
+        def withdrawn(req, t):
+            with self._lock:
+                if req.rid in self._cancelled:
+                    return "cancelled"
+            if req.deadline is not None and t - arrived(req) > req.deadline:
+                return "deadline"
+            return None
+
+        def emit(rec):
+            if log is not None:
+                log.write(json.dumps(rec) + "\n")
+
+        def read_back(a):
+            """Copies the solve's force series behind its last queued round."""
+            n = max(1, a.req.workload.steps - a.remaining)
+            a.records = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+            a.n_records = V.vplbm_forces_async(a.solver.h, a.records.numpy())
 
         def retire(block: bool):
             nonlocal used
@@ -104,7 +149,7 @@ class Server:
                 ev, fin = inflight.popleft()
                 ev.synchronize()
                 for a in fin:
-                    rec = a.records.numpy()
+                    rec = a.records.numpy()[:a.n_records]
                     fx, fy = rec[:, 0].copy(), rec[:, 1].copy()
                     pops = a.solver.populations() if self.keep_populations else None
                     err = None
@@ -112,11 +157,19 @@ class Server:
                         a.solver.synchronize()
                     except V.VplbmError as e:  # this solve diverged; the others are unaffected
                         err = str(e)
-                    t_done = now()
                     w = a.req.workload
-                    results.append(Result(a.req.rid, w.name, a.req.arrival if realtime else 0.0,
-                                          a.admitted, t_done, w.steps, w.nx * w.ny, w.storage,
-                                          w.collision, fx, fy, pops, err))
+                    ran = w.steps - a.remaining
+                    if a.stopped:
+                        err = f"{a.stopped}: stopped after {ran} of {w.steps} steps" + (
+                            f"; {err}" if err else "")
+                    t_done = now()
+                    r = Result(a.req.rid, w.name, arrived(a.req), a.admitted, t_done, ran,
+                               w.nx * w.ny, w.storage, w.collision, fx, fy, pops, err)
+                    results.append(r)
+                    emit({"rid": r.rid, "name": r.name, "arrival": r.arrival,
+                          "admitted": r.admitted, "finished": r.finished, "latency": r.latency,
+                          "steps": r.steps, "nodes": r.nodes, "storage": r.storage,
+                          "collision": r.collision, "error": r.error})
                     a.solver.close()
                     used -= a.footprint
                 if not block and not inflight:
@@ -124,14 +177,35 @@ class Server:
 
         while pending or active or inflight:
             t = now()
+            # withdrawn solves stop at this round boundary, behind their queued rounds
+            stop = []
+            for a in active:
+                a.stopped = withdrawn(a.req, t)
+                if a.stopped:
+                    read_back(a)
+                    stop.append(a)
+            if stop:
+                ev = torch.cuda.Event()
+                ev.record(self.stream)
+                inflight.append((ev, stop))
+                active = [a for a in active if not a.stopped]
             # admission: FIFO while a slot and memory are free
             while pending and (not realtime or pending[0].arrival <= t) and len(active) < self.max_active:
                 req = pending[0]
+                why = withdrawn(req, t)
+                if why:
+                    self.dropped[req.rid] = why
+                    pending.popleft()
+                    emit({"rid": req.rid, "name": req.workload.name, "arrival": arrived(req),
+                          "dropped": why, "at": t})
+                    continue
                 cfg, _ = V.config_from_workload(req.workload, ring_len=max(1, req.workload.steps))
                 fp = V.vplbm_footprint_bytes(cfg)
                 if fp > self.budget:
                     self.rejected.append(req.rid)
                     pending.popleft()
+                    emit({"rid": req.rid, "name": req.workload.name, "arrival": arrived(req),
+                          "rejected": f"footprint {fp} bytes over the budget"})
                     continue
                 if used + fp > self.budget:
                     break
@@ -141,6 +215,8 @@ class Server:
                 except V.VplbmError as e:  # e.g. out of device memory: refuse this request only
                     self.rejected.append(req.rid)
                     self.errors[req.rid] = str(e)
+                    emit({"rid": req.rid, "name": req.workload.name, "arrival": arrived(req),
+                          "rejected": str(e)})
                     continue
                 if self.on_admit:
                     self.on_admit(req, s)
@@ -150,7 +226,7 @@ class Server:
                 if inflight:
                     retire(block=True)
                     continue
-                if pending:
+                if pending and realtime:
                     time.sleep(max(0.0, min(0.01, pending[0].arrival - now())))
                 continue
             steps = [min(a.remaining, self.round_steps) for a in active]
@@ -159,9 +235,7 @@ class Server:
                 a.remaining -= k
             done = [a for a in active if a.remaining == 0]
             for a in done:  # force series copied behind the solve's last round
-                a.records = torch.empty((max(1, a.req.workload.steps), 3), dtype=torch.float64,
-                                        pin_memory=True)
-                V.vplbm_forces_async(a.solver.h, a.records.numpy())
+                read_back(a)
             ev = torch.cuda.Event()
             ev.record(self.stream)
             active = [a for a in active if a.remaining > 0]
@@ -169,7 +243,11 @@ class Server:
             retire(block=False)
         retire(block=True)
         t_end = now()
-        return results, self.report(results, t_end)
+        rep = self.report(results, t_end)
+        rep["dropped"] = len(self.dropped)
+        rep["stopped"] = sum(1 for r in results if r.error and r.error.startswith(
+            ("deadline:", "cancelled:")))
+        return results, rep
 
     @staticmethod
     def report(results, makespan: float):

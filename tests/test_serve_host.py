@@ -34,6 +34,7 @@ class FakeLib:
         self.created = []       # names in creation order
         self.live_bytes = 0
         self.peak_bytes = 0
+        self.time = 0.0         # fake clock: 1 ms per grouped step
         lib = self
 
         class Solver:
@@ -69,13 +70,16 @@ class FakeLib:
         self.rounds.append([(self.solvers[h].w.name, k) for h, k in zip(handles, steps)])
         for h, k in zip(handles, steps):
             self.solvers[h].t += k
+        self.time += 1e-3 * max(steps)
 
     def vplbm_forces_async(self, h, rec):
+        """The records of every step run so far (the ring holds them all)."""
         s = self.solvers[h]
-        assert s.t == s.w.steps and rec.shape == (s.w.steps, 3)
-        rec[:, 0] = np.arange(s.w.steps) + 1000.0 * s.w.seed
-        rec[:, 1] = -rec[:, 0]
-        rec[:, 2] = 1.0
+        assert rec.shape == (max(1, s.t), 3)
+        rec[:s.t, 0] = np.arange(s.t) + 1000.0 * s.w.seed
+        rec[:s.t, 1] = -rec[:s.t, 0]
+        rec[:s.t, 2] = 1.0
+        return s.t
 
 
 def fake_torch(gpu_done: bool):
@@ -105,12 +109,15 @@ def workload(name, nx, ny, steps, seed):
                                  seed=seed, bodies=[])
 
 
-def serve(monkeypatch, reqs, budget, gpu_done=True, realtime=False, **kw):
+def serve(monkeypatch, reqs, budget, gpu_done=True, realtime=False, log=None, fake_clock=False,
+          **kw):
     lib = FakeLib(kw.pop("fail_create", ()), kw.pop("diverge", ()))
     monkeypatch.setattr(S, "V", lib)
+    if fake_clock:
+        kw["clock"] = lambda: lib.time
     srv = S.Server(budget, stream=object(), **kw)
     srv.torch = fake_torch(gpu_done)
-    results, rep = srv.run(reqs, realtime=realtime)
+    results, rep = srv.run(reqs, realtime=realtime, log=log)
     return lib, srv, {r.name: r for r in results}, rep
 
 
@@ -208,3 +215,75 @@ def test_report_percentiles():
     assert rep["p99_latency_s"] == pytest.approx(np.percentile(lat, 99), abs=1e-4)
     assert rep["solves_per_s"] == 5.0
     assert rep["mlups"] == 100 * 1000 * 100_000 / 20.0 / 1e6  # 500 MLUPS
+
+
+def test_deadlines_drop_waiting_requests_and_stop_running_ones(monkeypatch):
+    """Fake clock, 1 ms per grouped step. "long" runs 3 rounds of 100 steps
+    (0.3 s); "late" waits behind it for memory and its 0.15 s deadline passes
+    first: dropped. "short" (deadline 0.15 s) is stopped at the first round
+    boundary past it, with the force series of the steps it ran."""
+    ws = [workload("long", 100, 10, 300, 1), workload("short", 10, 10, 400, 2),
+          workload("late", 100, 10, 100, 3)]
+    reqs = [I.Request(0, 0.0, ws[0]), I.Request(1, 0.0, ws[1], deadline=0.15),
+            I.Request(2, 0.0, ws[2], deadline=0.15)]
+    budget = (100 * 10 + 10 * 10) * BYTES_PER_NODE  # "late" cannot join "long"
+    lib, srv, res, rep = serve(monkeypatch, reqs, budget, True, round_steps=100,
+                               fake_clock=True)
+    assert srv.dropped == {2: "deadline"} and "late" not in lib.created
+    assert res["long"].error is None and res["long"].steps == 300
+    assert res["short"].error == "deadline: stopped after 200 of 400 steps"
+    assert res["short"].steps == 200 and len(res["short"].fx) == 200
+    assert np.array_equal(res["short"].fx, np.arange(200) + 2000.0)
+    assert rep["dropped"] == 1 and rep["stopped"] == 1 and rep["failed"] == 1
+    assert lib.live_bytes == 0
+
+
+@pytest.mark.parametrize("gpu_done", [True, False])
+def test_cancel_drops_a_waiting_request_and_stops_a_running_one(monkeypatch, gpu_done):
+    """Cancelled from the admission hook of "b" (any thread may call cancel):
+    "a", admitted in the same pass, runs the round that follows and stops at
+    the next round boundary; the waiting "c" is dropped when it reaches the
+    head of the queue."""
+    ws = [workload("a", 10, 10, 500, 1), workload("b", 10, 10, 300, 2),
+          workload("c", 10, 10, 100, 3)]
+    reqs = [I.Request(i, 0.0, w) for i, w in enumerate(ws)]
+    srv_ref = {}
+
+    def on_admit(req, solver):
+        if req.rid == 1:
+            srv_ref["srv"].cancel(0)
+            srv_ref["srv"].cancel(2)
+
+    lib = FakeLib()
+    monkeypatch.setattr(S, "V", lib)
+    srv = S.Server(10**6, stream=object(), round_steps=100, max_active=2, on_admit=on_admit)
+    srv.torch = fake_torch(gpu_done)
+    srv_ref["srv"] = srv
+    results, rep = srv.run(reqs, realtime=False)
+    res = {r.name: r for r in results}
+    assert res["a"].error == "cancelled: stopped after 100 of 500 steps" and res["a"].steps == 100
+    assert len(res["a"].fx) == 100
+    assert res["b"].error is None and res["b"].steps == 300
+    assert srv.dropped == {2: "cancelled"} and "c" not in lib.created
+    assert rep["stopped"] == 1 and rep["dropped"] == 1
+
+
+def test_one_log_line_per_request(monkeypatch):
+    import io
+    import json
+    ws = [workload("big", 1000, 1000, 100, 1), workload("ok", 10, 10, 200, 2),
+          workload("broken", 10, 10, 200, 3), workload("gone", 10, 10, 200, 4)]
+    reqs = [I.Request(i, 0.0, w) for i, w in enumerate(ws)]
+    reqs[3].deadline = -1.0  # already past: dropped at admission
+    buf = io.StringIO()
+    lib, srv, res, rep = serve(monkeypatch, reqs, 10**6, True, round_steps=100, log=buf,
+                               fail_create=["broken"])
+    lines = [json.loads(x) for x in buf.getvalue().splitlines()]
+    by = {x["rid"]: x for x in lines}
+    assert len(lines) == 4 and sorted(by) == [0, 1, 2, 3]
+    assert "over the budget" in by[0]["rejected"]
+    assert by[1]["steps"] == 200 and by[1]["error"] is None and by[1]["nodes"] == 100
+    assert by[1]["latency"] == pytest.approx(by[1]["finished"] - by[1]["arrival"])
+    assert "out of device memory" in by[2]["rejected"]
+    assert by[3]["dropped"] == "deadline"
+
