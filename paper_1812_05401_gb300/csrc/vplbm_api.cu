@@ -8,6 +8,7 @@
 // of the mask update over the region the bodies sweep.
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <climits>
@@ -273,6 +274,16 @@ vplbm_status cuda_fail(vplbm_solver* s, cudaError_t e, const char* where) {
     cudaError_t e_ = (call);                              \
     if (e_ != cudaSuccess) return cuda_fail((s), e_, #call); \
   } while (0)
+
+// A named NVTX range over one library call, so that a profiler's timeline
+// shows which launches a step or a grouped round made; without a profiler
+// attached the calls do nothing.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 #define VP_OK(call)                          \
   do {                                       \
@@ -941,6 +952,7 @@ vplbm_status vplbm_step(vplbm_solver* s, int64_t n) {
   vplbm_status st = check_usable(s);
   if (st != VPLBM_OK) return st;
   if (n < 0) return fail(s, VPLBM_ERR_INVALID, "n must be >= 0");
+  TraceRange trace("vplbm_step");
   for (int64_t k = 0; k < n; ++k) {
     if ((st = ensure_mask(s, s->t)) != VPLBM_OK) return st;
     const StepParams p = step_params(s, s->t, 0);
@@ -1343,6 +1355,7 @@ vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int
     max_steps = std::max(max_steps, steps[i]);
   }
   vplbm_solver* s0 = solvers[0];
+  TraceRange trace("vplbm_group_step");
   // Solvers with moving bodies need a mask update between steps, and those
   // recording the momentum exchange a reduction before each step: step them
   // alone, interleaved with the grouped launches of the others.
