@@ -193,6 +193,30 @@ def test_c1_circular_couette_fp64_1000_steps():
     assert np.abs(ux - ux2).max() < 1e-14 and np.abs(uy - uy2).max() < 1e-14
 
 
+def test_c1_error_equals_the_locked_oracle_value():
+    """C1 on the GPU in FP64 for 10^4 steps: its circular Couette error
+    (Eq. err against Eq. Sltan) equals the oracle's locked value
+    (tests/golden/c1_circular_couette.json) to FP64 parity."""
+    import importlib.util
+    import json
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("c1_regression", os.path.join(here, "c1_regression.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    with open(os.path.join(here, "c1_circular_couette.json")) as fh:
+        stored = json.load(fh)["l2_error"]
+    w = I.c1_circular_couette()
+    assert w.storage == "f64" and w.steps == 10_000
+    with V.Solver.from_workload(w) as s:
+        s.step(w.steps)
+        _, ux, uy = s.moments()
+        chi = s.mask()
+    r1, r2 = w.bodies[0].radius, w.bodies[1].radius
+    e = mod.c1_error(ux, uy, chi, w.nx, r1, r2, w.bodies[0].omega * r1)
+    assert e == pytest.approx(stored, rel=1e-9)
+
+
 @pytest.mark.parametrize("coll", ["srt", "mrt"])
 def test_fp32_velocity_within_1e5_of_U(coll):
     """FP32 storage and arithmetic: velocity within 1e-5 U of the FP64 oracle

@@ -699,3 +699,27 @@ def test_step_nodes_equals_a_grid_step(bcs):
     solid = mk.astype(bool)
     np.testing.assert_allclose(-fpx[solid].sum(), fx[0], rtol=1e-13, atol=1e-16)
     np.testing.assert_allclose(-fpy[solid].sum(), fy[0], rtol=1e-13, atol=1e-16)
+
+
+def _c1_golden():
+    """The C1 regression writer (tests/golden/c1_regression.py) and its stored value."""
+    import importlib.util
+    import json
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("c1_regression", os.path.join(here, "c1_regression.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    with open(os.path.join(here, "c1_circular_couette.json")) as fh:
+        return mod, json.load(fh)["l2_error"]
+
+
+def test_c1_circular_couette_error_is_locked():
+    """Section 3.2 plots the curved-wall error (Fig. 11) without printing it,
+    so the oracle's C1 value (10^4 steps) is locked as a regression: a change
+    to the oracle's arithmetic moves it. It is also the staircase error the
+    paper describes: nonzero and small."""
+    mod, stored = _c1_golden()
+    assert mod.oracle_c1_error() == pytest.approx(stored, rel=1e-12)
+    assert 1e-3 < stored < 5e-2
+
