@@ -361,6 +361,11 @@ vplbm_status vplbm_step_noalloc(const vplbm_config* cfg, const vplbm_body* bodie
 
 /* Message for the last failing call on this handle (never NULL). */
 const char* vplbm_last_error(const vplbm_solver* s);
+
+/* Why the calling thread's last vplbm_create failed ("" after a success;
+ * never NULL): a failed creation leaves no handle to carry the message.
+ * Valid until the thread's next vplbm_create. */
+const char* vplbm_create_error(void);
 const char* vplbm_status_string(vplbm_status st);
 
 /* Frees everything the solver owns, stream-ordered: the memory returns once

@@ -278,6 +278,10 @@ vplbm_status cuda_fail(vplbm_solver* s, cudaError_t e, const char* where) {
 // A named NVTX range over one library call, so that a profiler's timeline
 // shows which launches a step or a grouped round made; without a profiler
 // attached the calls do nothing.
+// Why the calling thread's last vplbm_create failed (no handle exists to
+// carry the message).
+thread_local std::string g_create_error;
+
 struct TraceRange {
   explicit TraceRange(const char* name) { nvtxRangePushA(name); }
   ~TraceRange() { nvtxRangePop(); }
@@ -715,16 +719,24 @@ size_t vplbm_footprint_bytes(const vplbm_config* c) {
 }
 
 vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
-  if (!out) return VPLBM_ERR_INVALID;
+  g_create_error.clear();
+  if (!out) {
+    g_create_error = "out is NULL";
+    return VPLBM_ERR_INVALID;
+  }
   *out = nullptr;
   std::string why;
   vplbm_status v = validate(cfg, &why);
   if (v != VPLBM_OK) {
     std::fprintf(stderr, "vplbm_create: %s\n", why.c_str());
+    g_create_error = why;
     return v;
   }
   vplbm_solver* s = new (std::nothrow) vplbm_solver();
-  if (!s) return VPLBM_ERR_NOMEM;
+  if (!s) {
+    g_create_error = "host allocation of the solver failed";
+    return VPLBM_ERR_NOMEM;
+  }
   s->cfg = *cfg;
   s->esize = element_size(cfg->storage);
   s->pitch = row_pitch(cfg->nx, cfg->storage);
@@ -733,6 +745,7 @@ vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
 
   auto bail = [&](vplbm_status st) {
     std::fprintf(stderr, "vplbm_create: %s\n", s->err.c_str());
+    g_create_error = s->err;
     vplbm_destroy(s);
     return st;
   };
@@ -1474,6 +1487,8 @@ vplbm_status vplbm_fused_timing(vplbm_solver* s, double* total_ms, int64_t* laun
   s->timed_count = 0;
   return VPLBM_OK;
 }
+
+const char* vplbm_create_error(void) { return g_create_error.c_str(); }
 
 const char* vplbm_last_error(const vplbm_solver* s) {
   if (!s) return "no solver";

@@ -114,6 +114,8 @@ def lib() -> C.CDLL:
         L.vplbm_fused_timing.argtypes = [P, dp, C.POINTER(C.c_int64)]
         L.vplbm_last_error.argtypes = [P]
         L.vplbm_last_error.restype = C.c_char_p
+        L.vplbm_create_error.argtypes = []
+        L.vplbm_create_error.restype = C.c_char_p
         L.vplbm_status_string.argtypes = [C.c_int]
         L.vplbm_status_string.restype = C.c_char_p
         L.vplbm_destroy.argtypes = [P]
@@ -161,7 +163,10 @@ _grids: dict = {}
 
 def vplbm_create(cfg: vplbm_config) -> int:
     h = C.c_void_p()
-    _check(None, lib().vplbm_create(C.byref(cfg), C.byref(h)), "vplbm_create")
+    st = lib().vplbm_create(C.byref(cfg), C.byref(h))
+    if st != VPLBM_OK:
+        why = lib().vplbm_create_error().decode()
+        raise VplbmError(st, f"vplbm_create: {lib().vplbm_status_string(st).decode()}: {why}")
     _grids[h.value] = (cfg.nx, cfg.ny)
     return h.value
 

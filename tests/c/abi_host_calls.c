@@ -47,6 +47,7 @@ int main(void) {
   vplbm_solver* s = (vplbm_solver*)1;
   c.tau = 0.5;
   if (vplbm_create(&c, &s) != VPLBM_ERR_INVALID || s != NULL) return fail("tau = 1/2 refused");
+  if (strstr(vplbm_create_error(), "tau") == NULL) return fail("creation error names tau");
   vplbm_config_init(&c);
   c.nx = 64;
   c.ny = 32;

@@ -78,6 +78,12 @@ def test_invalid_configs_rejected_without_gpu(lib):
         with pytest.raises(V.VplbmError) as e:
             V.vplbm_create(c)
         assert e.value.status == V.VPLBM_ERR_INVALID
+        # the reason travels with the error (no handle exists to carry it)
+        why = V.lib().vplbm_create_error().decode()
+        assert why and why in str(e.value)
+    c = V.make_config(4, 4, tau=0.5)
+    with pytest.raises(V.VplbmError, match="tau must be > 1/2"):
+        V.vplbm_create(c)
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
