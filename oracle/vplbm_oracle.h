@@ -7,6 +7,14 @@
  * benchmark may load or call it; the product path never does. It shares no
  * code, header, table or helper with the CUDA library.
  *
+ * Pins (tests/test_oracle_pins.py): every function is checked against what
+ * the paper and the mathematics fix (printed constants, exact rational
+ * single-node collisions, invariants, closed forms, symmetries, limits).
+ * Parity unpinned: the magnitude of the curved-wall (staircase) error, which
+ * the paper gives only in figures (Section 3.2). It is pinned as nonzero and
+ * falling with refinement, and the 128 x 128 circular Couette value is
+ * locked as a regression of this oracle.
+ *
  * Layout: populations f[alpha][y][x], alpha = 0..8, row length nx, no padding.
  * Node (i, j) sits at the point (x, y) = (i, j); lattice spacing and time step
  * are 1 (Section 2.1.1, after Eq. vecteurs_D2Q9).
