@@ -65,6 +65,19 @@ MUTANTS = [
      "const double f_last = src[(size_t)a * plane + (size_t)y * nx + (nx - 1)];",
      "const double f_last = src[(size_t)a * plane + (size_t)y * nx + (nx - 2)];"),
     ("convective outlet: row of the ghost", "return ghost[(size_t)as * ny + ys];", "return ghost[(size_t)as * ny + y];"),
+    ("SRT: relaxation times tau instead of over it",
+     "fout[a] = f[a] - (f[a] - feq[a]) / c->tau + pre * F[a];",
+     "fout[a] = f[a] - (f[a] - feq[a]) * c->tau + pre * F[a];"),
+    ("force record: sign of the reaction", "sfx -= px;", "sfx += px;"),
+    ("mass record: rest population dropped", "for (int a = 0; a < 9; ++a) smass += fl[a];",
+     "for (int a = 1; a < 9; ++a) smass += fl[a];"),
+    ("node-by-node step: bodies of the next step",
+     "double* st = body_states(c, t);\n  double* ghost = (double*)calloc(9 * (size_t)ny, sizeof(double));",
+     "double* st = body_states(c, t + 1);\n  double* ghost = (double*)calloc(9 * (size_t)ny, sizeof(double));"),
+    ("node-by-node step: outlet state not advanced",
+     "if (outlet_advance(c, f, ghost) != 0) { /* the state itself is not advanced */\n    free(st);\n"
+     "    free(ghost);\n    return 1;\n  }\n  for (int64_t k = 0; k < n; ++k) {",
+     "if (0) {\n    free(st);\n    free(ghost);\n    return 1;\n  }\n  for (int64_t k = 0; k < n; ++k) {"),
 ]
 
 
