@@ -78,6 +78,11 @@ MUTANTS = [
      "if (outlet_advance(c, f, ghost) != 0) { /* the state itself is not advanced */\n    free(st);\n"
      "    free(ghost);\n    return 1;\n  }\n  for (int64_t k = 0; k < n; ++k) {",
      "if (0) {\n    free(st);\n    free(ghost);\n    return 1;\n  }\n  for (int64_t k = 0; k < n; ++k) {"),
+    ("moments: mask of the next time",
+     "orc_mask(c, t, chi, us);\n  if (outlet_advance(c, f, ghost) != 0) { /* the state itself is not advanced */\n"
+     "    free(chi);",
+     "orc_mask(c, t + 1, chi, us);\n  if (outlet_advance(c, f, ghost) != 0) { /* the state itself is not advanced */\n"
+     "    free(chi);"),
 ]
 
 

@@ -723,3 +723,32 @@ def test_c1_circular_couette_error_is_locked():
     assert mod.oracle_c1_error() == pytest.approx(stored, rel=1e-12)
     assert 1e-3 < stored < 5e-2
 
+
+def test_moments_are_what_the_next_step_computes():
+    """orc_moments returns the density and implicit velocity (Eq. 18) that
+    step t computes from f*(t): the pulled populations with the mask and solid
+    velocity of time t. Their total is that step's mass record, and the
+    penalization force evaluated literally from them (Eq. 17) over the solid
+    nodes is that step's force record (a moving body, so the mask of another
+    time would differ at its edge)."""
+    nx, ny = 40, 24
+    cfg = O.Config(nx=nx, ny=ny, collision=O.MRT, tau=0.6, bc_x=O.BC_INLET_OUTLET,
+                   bc_y=O.BC_FREE_SLIP, u_in=(0.04, 0.0),
+                   bodies=[O.Body(15.0, 11.5, 5.0, amp_y=3.0, period=20.0, omega=0.01)])
+    f = I.random_populations(nx, ny, 91, 0.05)
+    t = 3
+    rho, ux, uy = O.moments(cfg, f, t)
+    chi, us = O.mask(cfg, t)
+    fx, fy, mass = O.run(cfg, f.copy(), 1, t0=t)
+    assert rho.sum() == pytest.approx(mass[0], rel=1e-13)
+    s = chi.astype(bool)
+    # Eq. 17 on the solid nodes, literally: f = -rho (chi/eta)(u - u_s); the
+    # record is the reaction on the body, minus their sum
+    fpx = -rho[s] / cfg.eta * (ux[s] - us[0][s])
+    fpy = -rho[s] / cfg.eta * (uy[s] - us[1][s])
+    assert -fpx.sum() == pytest.approx(fx[0], rel=1e-6)
+    assert -fpy.sum() == pytest.approx(fy[0], rel=1e-6, abs=1e-6 * abs(fx[0]))
+    # the mask of the next time differs at the moving edge
+    chi1, _ = O.mask(cfg, t + 1)
+    assert (chi1 != chi).any()
+
