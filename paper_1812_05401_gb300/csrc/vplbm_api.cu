@@ -275,13 +275,13 @@ vplbm_status cuda_fail(vplbm_solver* s, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail((s), e_, #call); \
   } while (0)
 
-// A named NVTX range over one library call, so that a profiler's timeline
-// shows which launches a step or a grouped round made; without a profiler
-// attached the calls do nothing.
 // Why the calling thread's last vplbm_create failed (no handle exists to
 // carry the message).
 thread_local std::string g_create_error;
 
+// A named NVTX range over one library call, so that a profiler's timeline
+// shows which launches a step or a grouped round made; without a profiler
+// attached the calls do nothing.
 struct TraceRange {
   explicit TraceRange(const char* name) { nvtxRangePushA(name); }
   ~TraceRange() { nvtxRangePop(); }
