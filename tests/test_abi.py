@@ -160,3 +160,18 @@ def test_torch_allocator_binds_one_stream_without_gpu():
     B = V.TorchAllocator(device=0)
     assert V.make_config(64, 32, stream=0x7890, allocator=B).stream == 0x7890
     assert B.stream == 0x7890
+
+
+def test_c_example_builds_against_the_header(lib, tmp_path):
+    """tests/c/example_cylinder.c, the C usage example, compiles and links
+    with -Wall -Werror (running it needs a GPU)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("needs gcc")
+    pkg = os.path.join(ROOT, "paper_1812_05401_gb300")
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c", "example_cylinder.c"), "-o",
+                    str(tmp_path / "cylinder"), "-L", pkg, "-lvplbm", "-Wl,-rpath," + pkg],
+                   check=True)
+    assert os.path.exists(tmp_path / "cylinder")
