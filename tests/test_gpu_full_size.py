@@ -8,8 +8,8 @@ collision for the listed nodes, from the GPU's own stored f*(t)): random
 nodes, every kind of boundary node, tile-border nodes, the ring around the
 moving body, and every solid node for the force record of the step.
 Tolerances: FP32 storage 4e-7 on one step's populations (FP32 arithmetic on
-values <= 0.5); FP16 offsets (stochastically rounded) one rounding step of
-each offset's own binade plus FP32 arithmetic; the force within 2e-5 relative
+values <= 0.5); FP16 and BF16 offsets (stochastically rounded) one rounding
+step of each offset's own binade plus FP32 arithmetic; the force within 2e-5 relative
 (FP32 node forces summed in FP64).
 The in-place scheme is bitwise the A/B scheme at this size as well.
 """
@@ -86,7 +86,7 @@ def _solid_nodes(w, t):
     return xx.ravel(), yy.ravel()
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 def test_bench_workload_sampled_against_oracle(storage):
     import torch
     w = I.c5_moving_cylinder(storage)
@@ -111,10 +111,12 @@ def test_bench_workload_sampled_against_oracle(storage):
     if storage == "f32":
         assert err.max() < 4e-7, err.max()
     else:
-        # stochastic FP16 rounding of the offset h = f - w: less than one
-        # rounding step of the binade of h (10 stored bits), plus FP32 arithmetic
+        # stochastic 16-bit rounding of the offset h = f - w: less than one
+        # rounding step of the binade of h (10 stored bits for FP16, 7 for
+        # BF16), plus FP32 arithmetic
         h = np.abs(ref - O.weights()[None, :])
-        step = 2.0 ** (np.floor(np.log2(np.maximum(h, 2.0 ** -14))) - 10)
+        drop = 10 if storage == "f16" else 7
+        step = 2.0 ** (np.floor(np.log2(np.maximum(h, 2.0 ** -14))) - drop)
         assert (err < step + 2e-6).all(), (err.max(), (err - step).max())
         assert h.max() < 0.5
     # the step's force record against the oracle's node forces over every solid node
