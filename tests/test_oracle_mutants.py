@@ -34,6 +34,7 @@ MUTANTS = [
     ("forcing: sign of u in (xi - u)", "double vx = (m->xi[a][0] - ux) / CS2", "double vx = (m->xi[a][0] + ux) / CS2"),
     ("MRT: s_q from Lambda", "double sq = 1.0 / (0.5 + c->lambda / (1.0 / sn - 0.5));",
      "double sq = 1.0 / (0.5 + c->lambda * (1.0 / sn - 0.5));"),
+    ("MRT: energy-square moment relaxed at s_q", "S[2] = sn;", "S[2] = sq;"),
     ("MRT: sign of the forcing moments", "- (1.0 - m->S[k] / 2.0) * MF[k];", "+ (1.0 - m->S[k] / 2.0) * MF[k];"),
     ("SRT: forcing prefactor dropped", "double pre = 1.0 - 1.0 / (2.0 * c->tau);", "double pre = 1.0;"),
     ("velocity: half force dropped", "double bx = jx + 0.5 * r * c->g[0];", "double bx = jx + r * c->g[0];"),

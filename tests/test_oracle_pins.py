@@ -163,6 +163,101 @@ def test_single_node_collision_exact_rational_brute_force():
         assert abs(px - float(fx)) < 1e-14 and abs(py - float(fy)) < 1e-14
 
 
+def _exact_inverse(A):
+    """Inverse of a square matrix of Fractions by Gauss-Jordan elimination."""
+    n = len(A)
+    a = [list(row) + [Fraction(int(i == j)) for j in range(n)] for i, row in enumerate(A)]
+    for c in range(n):
+        p = next(r for r in range(c, n) if a[r][c] != 0)
+        a[c], a[p] = a[p], a[c]
+        pv = a[c][c]
+        a[c] = [v / pv for v in a[c]]
+        for r in range(n):
+            if r != c and a[r][c] != 0:
+                k = a[r][c]
+                a[r] = [x - k * y for x, y in zip(a[r], a[c])]
+    return [row[n:] for row in a]
+
+
+def _exact_collision(coll, f, chi, us, g, tau, lam, eta):
+    """Post-collision populations of one node in exact rational arithmetic,
+    written from the printed model and not through the oracle's helpers:
+    the printed velocity set, weights and M (tests/golden/paper_constants.json),
+    rho and rho u from Eqs. density and velocity with the penalization force
+    of Eq. 17 and a uniform body force g, solved for u as in Eq. 18; then
+    Eq. LatticeBoltz with the printed equilibrium and Eq. Guo1 (SRT), or
+    Eq. equa_lbl_mrt with the printed m_eq, S = diag(0, s_n, s_n, 0, s_q, 0,
+    s_q, s_n, s_n), s_n = 1/tau, s_q from Eq. lambda_parameter, and Eq. Guo2
+    (MRT). c_s^2 = 1/3."""
+    Fr = Fraction
+    xi = GOLDEN["velocity_set"]["value"]
+    w = [Fr(s) for s in GOLDEN["weights"]["value"]]
+    M = [[Fr(v) for v in row] for row in GOLDEN["moment_matrix"]["value"]]
+    cs2 = Fr(1, 3)
+    f = [Fr(v) for v in f]
+    tau, lam, eta = Fr(tau), Fr(lam), Fr(eta)
+    usx, usy, gx, gy = Fr(us[0]), Fr(us[1]), Fr(g[0]), Fr(g[1])
+    rho = sum(f)
+    jx = sum(xi[a][0] * f[a] for a in range(9))
+    jy = sum(xi[a][1] * f[a] for a in range(9))
+    # rho u = j + (f_pen + rho g)/2 with f_pen = -rho (chi/eta)(u - u_s)
+    h = Fr(chi) / eta / 2
+    ux = (jx + rho * gx / 2 + h * rho * usx) / (rho * (1 + h))
+    uy = (jy + rho * gy / 2 + h * rho * usy) / (rho * (1 + h))
+    fpx = -rho * Fr(chi) / eta * (ux - usx)
+    fpy = -rho * Fr(chi) / eta * (uy - usy)
+    ftx, fty = fpx + rho * gx, fpy + rho * gy
+    uu = ux * ux + uy * uy
+    # Eq. Guo1 / Eq. Guo2 without the SRT prefactor
+    Ft = []
+    for a in range(9):
+        xu = xi[a][0] * ux + xi[a][1] * uy
+        bx = (xi[a][0] - ux) / cs2 + xu / (cs2 * cs2) * xi[a][0]
+        by = (xi[a][1] - uy) / cs2 + xu / (cs2 * cs2) * xi[a][1]
+        Ft.append(w[a] * (bx * ftx + by * fty))
+    if coll == O.SRT:
+        out = []
+        for a in range(9):
+            xu = xi[a][0] * ux + xi[a][1] * uy
+            feq = w[a] * rho * (1 + xu / cs2 + (xu * xu - cs2 * uu) / (2 * cs2 * cs2))
+            out.append(f[a] - (f[a] - feq) / tau + (1 - 1 / (2 * tau)) * Ft[a])
+        return out, (fpx, fpy)
+    sn = 1 / tau
+    sq = 1 / (Fr(1, 2) + lam / (1 / sn - Fr(1, 2)))
+    S = [Fr(0), sn, sn, Fr(0), sq, Fr(0), sq, sn, sn]
+    meq = [rho, rho * (-2 + 3 * uu), rho * (1 - 3 * uu), rho * ux, -rho * ux, rho * uy, -rho * uy,
+           rho * (ux * ux - uy * uy), rho * ux * uy]
+    m = [sum(M[k][a] * f[a] for a in range(9)) for k in range(9)]
+    MF = [sum(M[k][a] * Ft[a] for a in range(9)) for k in range(9)]
+    r = [S[k] * (m[k] - meq[k]) - (1 - S[k] / 2) * MF[k] for k in range(9)]
+    Minv = _exact_inverse(M)
+    return [f[a] - sum(Minv[a][k] * r[k] for k in range(9)) for a in range(9)], (fpx, fpy)
+
+
+@pytest.mark.parametrize("coll", [O.SRT, O.MRT])
+@pytest.mark.parametrize("seed", range(3))
+def test_single_node_full_collision_exact_rational(coll, seed):
+    """All nine post-collision populations of one node, SRT and MRT, fluid and
+    solid, with a nonzero body force, against the exact rational result of
+    the printed equations: agreement to 1e-15 relative (of the largest
+    population, so about four units in the last place of the rest one)."""
+    r = _rng(900 + seed)
+    tau = 0.51 + 1.5 * r.random()
+    g = tuple(1e-4 * r.standard_normal(2))
+    cfg = O.Config(nx=1, ny=1, collision=coll, tau=tau, lam=3 / 16, g=g)
+    f = I.random_populations(1, 1, 80 + seed, 0.05)[:, 0, 0]
+    us = tuple(0.03 * r.standard_normal(2))
+    for chi in (0, 1):
+        fo, (px, py) = O.collide_node(cfg, f, chi, *us)
+        ex, (ex_px, ex_py) = _exact_collision(coll, f, chi, us, g, tau, 3 / 16, cfg.eta)
+        scale = max(abs(v) for v in ex)
+        for a in range(9):
+            assert abs(Fraction(fo[a]) - ex[a]) <= Fraction(1, 10**15) * scale, (chi, a)
+        # the penalization force the oracle reports (kappa form) is Eq. 17's
+        assert abs(px - float(ex_px)) <= 1e-9 * max(abs(float(ex_px)), 1e-12)
+        assert abs(py - float(ex_py)) <= 1e-9 * max(abs(float(ex_py)), 1e-12)
+
+
 @pytest.mark.parametrize("coll", [O.SRT, O.MRT])
 @pytest.mark.parametrize("seed", range(4))
 def test_collision_conserves_mass_and_adds_force(coll, seed):
