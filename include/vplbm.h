@@ -47,7 +47,7 @@ typedef enum {
   VPLBM_ERR_NOMEM = 2,    /* device allocation failed or budget exceeded */
   VPLBM_ERR_CUDA = 3,     /* CUDA runtime error (sticky) */
   VPLBM_ERR_DIVERGED = 4, /* a step produced rho <= 0 or a non-finite velocity */
-  VPLBM_ERR_TIMEOUT = 5,  /* a bounded device-side wait gave up */
+  VPLBM_ERR_TIMEOUT = 5,  /* reserved: no kernel of this library waits on the device */
   VPLBM_ERR_STATE = 6     /* call not valid in the handle's current state */
 } vplbm_status;
 
@@ -158,10 +158,6 @@ typedef struct {
 } vplbm_config;
 
 typedef struct vplbm_solver vplbm_solver;
-
-/* Environment: VPLBM_TMA=1 (read by vplbm_create) stages the interior tiles
- * of the single-solver step through shared memory with TMA tensor copies
- * instead of pulling them with vector loads; results are bitwise the same. */
 
 /* Fills cfg with defaults: SRT, FP32, periodic, tau 0.8, Lambda 3/16,
  * eta 1e-7, rho0 1, mass reduction on, ring of 4096 steps, stochastic
@@ -322,7 +318,9 @@ vplbm_status vplbm_fused_timing(vplbm_solver* s, double* total_ms, int64_t* laun
  *
  *  cfg       the solver's configuration (nx, ny, collision, storage, boundary
  *            conditions, tau, lambda, eta, u_in, body_force, rates,
- *            reduce_mass, stream); rho0, u0 and force_ring_len are unused.
+ *            reduce_mass, rounding, stream); rho0, u0 and force_ring_len are
+ *            not read (a config filled by hand may leave them zero). stream
+ *            must belong to the current device (NULL: its default stream).
  *  bodies    host array of n_bodies <= VPLBM_MAX_BODIES rigid bodies, evaluated
  *            at step t, or NULL with n_bodies = 0.
  *  f_src     device populations f*(t) in the storage type, [9][ny][pitch]
@@ -330,7 +328,7 @@ vplbm_status vplbm_fused_timing(vplbm_solver* s, double* total_ms, int64_t* laun
  *  f_dst     device output f*(t+1), same layout; must not alias f_src.
  *  mask      device [ny][pitch] bytes: 0 fluid, k = 1..n_bodies solid of body
  *            k (solid velocity from its motion), 255 solid with the velocity
- *            from us. Other values are not allowed.
+ *            from us; any other nonzero value is a solid at rest (u_s = 0).
  *  us        device solid velocity, float2 (double2 for VPLBM_F64 storage)
  *            [ny][pitch], read at mask = 255 nodes, or NULL for u_s = 0.
  *  pitch     row length in elements: >= nx and a multiple of 8.
@@ -342,12 +340,15 @@ vplbm_status vplbm_fused_timing(vplbm_solver* s, double* total_ms, int64_t* laun
  *
  * Scratch: the per-tile and per-group reduction sums live in a fixed 1 MiB
  * device array inside the library, which every GPU that loads the library
- * holds until the process exits. Grids needing more than that (about 40,000
- * tiles, e.g. 160M nodes with FP32 storage) are rejected with
- * VPLBM_ERR_INVALID and a message; use vplbm_create/vplbm_step for them.
+ * holds until the process exits. It holds at most 43,491 tiles of the fused
+ * step: with tiles of 128 x 32 nodes (FP32 and 16-bit storage) about 178.1M
+ * nodes, with tiles of 64 x 32 (FP64) about 89.1M. Larger grids are rejected
+ * with VPLBM_ERR_INVALID and a message; use vplbm_create/vplbm_step for them.
  * The first call on a device looks up the array's device address (done once
- * per device, with that device current); make that first call before any
- * stream capture. Each call clears the array's counters on cfg->stream
+ * per device, with that device current) and keeps it for the rest of the
+ * process: make that first call before any stream capture, and call nothing
+ * here after a cudaDeviceReset of that device (the kept address belongs to
+ * the context the reset destroyed). Each call clears the array's counters on cfg->stream
  * before launching. All calls share the one array, so calls whose kernels
  * can overlap on the GPU (different streams without ordering) race and give
  * wrong results: order them on one stream. Asynchronous on cfg->stream;

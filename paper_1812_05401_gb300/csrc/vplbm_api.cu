@@ -7,7 +7,6 @@
 // one launch of the fused kernel, preceded, when a body moves, by one launch
 // of the mask update over the region the bodies sweep.
 #include <cuda_runtime.h>
-#include <cudaTypedefs.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
@@ -144,36 +143,6 @@ __global__ void perturbation_kernel(double* u, int nx, int ny, double u0x, doubl
   u[nn + node] = amp > 0.0 ? __dadd_rn(u0y, r2[1]) : u0y;
 }
 
-// Tensor map of a population buffer for the TMA staging of interior tiles:
-// a [9][ny][pitch] tensor in the storage type, box {tile + 2 halos, 8 rows,
-// 1 plane}. The encoder comes from the driver through the runtime's entry
-// point query. Returns false if it cannot be built (the kernel then pulls
-// interior tiles with vector loads).
-bool make_tensor_map(CUtensorMap* map, void* base, int storage, int pitch, int ny) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
-                                         &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn)
-      return false;
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
-  const CUtensorMapDataType dt = storage == kF64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
-                                 : storage == kF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                 : storage == kF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                                   : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  const cuuint64_t esize = cuuint64_t(elem_bytes(storage));
-  const cuuint64_t dims[3] = {cuuint64_t(pitch), cuuint64_t(ny), 9};
-  const cuuint64_t strides[2] = {cuuint64_t(pitch) * esize, cuuint64_t(pitch) * cuuint64_t(ny) * esize};
-  const cuuint32_t box[3] = {cuuint32_t(tma_box_x(storage)), cuuint32_t(kTmaRows), 1};
-  const cuuint32_t estride[3] = {1, 1, 1};
-  return encode(map, dt, 3, base, dims, strides, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 dim3 grid2d(int w, int h, dim3 blk) {
   return dim3((w + blk.x - 1) / blk.x, (h + blk.y - 1) / blk.y);
 }
@@ -231,7 +200,6 @@ struct vplbm_solver {
 
   int tiles_x = 0, tiles_y = 0, n_tiles = 0, n_groups = 0;
   StepParams base{};  // constants; src/dst/t/bodies filled per step
-  CUtensorMap tmap[2];  // TMA descriptors of f[0] and f[1] (when base.use_tma)
 
   int64_t t = 0;
   int64_t ring_read = 0;  // first step not yet returned by vplbm_forces
@@ -495,7 +463,6 @@ StepParams step_params(const vplbm_solver* s, int64_t t, int parity) {
   p.ghost_src = s->ghost[c];
   p.ghost_dst = s->ghost[c ^ 1];
   p.mode = s->aa ? (c == 0 ? kModeAAPush : kModeAALocal) : kModeAB;
-  if (p.use_tma) p.tmap = s->tmap[c];
   p.t = t;
   fill_bodies(s, t, &p);
   return p;
@@ -853,19 +820,6 @@ vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
   p.reduce_mass = cfg->reduce_mass ? 1 : 0;
   p.stochastic = cfg->rounding == VPLBM_ROUND_STOCHASTIC ? 1 : 0;
   p.collision = cfg->collision;
-  // TMA staging of interior tiles, opt-in with VPLBM_TMA=1 in the environment:
-  // measured slower than the direct vector pull on the 16384 x 4096 step
-  // (FP32 0.876 vs 0.759 ms, FP16 0.677 vs 0.588 ms) -- with one tile per
-  // block each block pays the pipeline fill, and the FP32 stages (78 KB)
-  // leave room for only two blocks per SM.
-  {
-    const char* env = std::getenv("VPLBM_TMA");
-    const bool want = env && env[0] == '1' && !s->aa;
-    p.use_tma = want && make_tensor_map(&s->tmap[0], s->f[0], cfg->storage, s->pitch, cfg->ny) &&
-                        make_tensor_map(&s->tmap[1], s->f[1], cfg->storage, s->pitch, cfg->ny)
-                    ? 1
-                    : 0;
-  }
 
   if ((st = vplbm_set_initial_velocity(s, nullptr)) != VPLBM_OK) return bail(st);
   *out = s;
@@ -999,8 +953,6 @@ vplbm_status vplbm_synchronize(vplbm_solver* s) {
   VP_CUDA(s, cudaStreamSynchronize(s->stream));
   if (flag) {
     VP_CUDA(s, cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream));
-    if (flag & 2)
-      return fail(s, VPLBM_ERR_TIMEOUT, "a bounded wait for staged populations gave up");
     return fail(s, VPLBM_ERR_DIVERGED, "a step produced rho <= 0 or a non-finite velocity");
   }
   return VPLBM_OK;
@@ -1426,8 +1378,6 @@ vplbm_status vplbm_group_step(vplbm_solver* const* solvers, int32_t n, const int
         vplbm_solver* s = solvers[mem[j].idx];
         hp.push_back(step_params(s, s->t, 0));
         hp.push_back(step_params(s, s->t, 1));
-        hp[hp.size() - 2].use_tma = 0;  // grouped blocks pull directly
-        hp[hp.size() - 1].use_tma = 0;
         for (int tile = 0; tile < s->n_tiles; ++tile) ht.push_back(GroupTile{int(j), tile});
         pl.prefix_steps.push_back(mem[j].steps);
         pl.prefix_tiles.push_back(int(ht.size()));
@@ -1550,7 +1500,9 @@ void vplbm_destroy(vplbm_solver* s) {
 
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = size_t(1) << 20;  // 1 MiB
+// 1 MiB: 24 bytes per tile, 24 per group of 256 tiles, 4 per group counter
+// (+1), 16-byte alignment and the 4-byte flag hold at most 43,491 tiles.
+constexpr size_t kNoAllocScratchBytes = size_t(1) << 20;
 
 // Shared by every call on a device; the last call's contents stay in it.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
@@ -1581,9 +1533,19 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_config* cfg, const vplbm_
                                            const uint8_t* mask, const void* us, int32_t pitch,
                                            int64_t t, double* record, int* flag) {
   std::string why;
-  if (validate(cfg, &why) != VPLBM_OK) {
-    std::fprintf(stderr, "vplbm_step_noalloc: %s\n", why.c_str());
+  if (!cfg) {
+    std::fprintf(stderr, "vplbm_step_noalloc: config is NULL\n");
     return VPLBM_ERR_INVALID;
+  }
+  {
+    // rho0, u0 and force_ring_len belong to a solver's own state: not used here
+    vplbm_config c = *cfg;
+    c.rho0 = 1.0;
+    c.force_ring_len = 1;
+    if (validate(&c, &why) != VPLBM_OK) {
+      std::fprintf(stderr, "vplbm_step_noalloc: %s\n", why.c_str());
+      return VPLBM_ERR_INVALID;
+    }
   }
   if (!f_src || !f_dst || !mask || !record || f_src == f_dst || t < 0 ||
       n_bodies < 0 || n_bodies > kMaxBodies || (n_bodies > 0 && !bodies)) {
@@ -1635,6 +1597,19 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_config* cfg, const vplbm_
   }
   unsigned char* sb = static_cast<unsigned char*>(base);
   cudaStream_t stream = static_cast<cudaStream_t>(cfg->stream);
+  {
+    // the scratch address is the current device's: the stream must be too
+    int sdev = dev;
+    if (stream && (e = cudaStreamGetDevice(stream, &sdev)) != cudaSuccess) {
+      std::fprintf(stderr, "vplbm_step_noalloc: cudaStreamGetDevice: %s\n", cudaGetErrorString(e));
+      return VPLBM_ERR_CUDA;
+    }
+    if (sdev != dev) {
+      std::fprintf(stderr, "vplbm_step_noalloc: cfg->stream belongs to device %d, the current "
+                           "device is %d\n", sdev, dev);
+      return VPLBM_ERR_INVALID;
+    }
+  }
 
   // The arrival counters must start at zero (a failed earlier call could have
   // left them mid-count); the divergence slot too when the caller gives none.

@@ -56,9 +56,8 @@ template <> struct Store<kF64> {
   static __device__ __forceinline__ double to_f64(const E* p, int) { return *p; }
   static __device__ __forceinline__ void from_f64(E* p, double f, int) { *p = f; }
   // npt = 2 consecutive elements as one 16-byte access, as offsets h = f - w.
-  // load_h_plain: a plain generic load, for shared memory (the TMA stages) and
-  // for a buffer the kernel also writes (the in-place steps); load_h takes the
-  // read-only data path.
+  // load_h_plain: a plain load, for a buffer the kernel also writes (the
+  // in-place steps); load_h takes the read-only data path.
   static __device__ __forceinline__ void load_h_plain(const E* p, T h[2], int a) {
     const double2 v = *reinterpret_cast<const double2*>(p);
     h[0] = v.x - wgt<T>(a);
@@ -391,13 +390,14 @@ __device__ __forceinline__ void solid_velocity(const StepParams& p, uint8_t m, i
         usy = T(v.y);
       }
     }
-  } else {
+  } else if (m <= p.n_bodies) {
     const T* b = consts<T>(p).body[m - 1];
     const T dx = T(x) - b[0];
     const T dy = T(y) - b[1];
     usx = b[2] - b[4] * dy;
     usy = b[3] + b[4] * dx;
   }
+  // any other label (only a caller-written mask can hold one) is solid at rest
 }
 
 template <class T>
@@ -924,91 +924,10 @@ __device__ __forceinline__ typename S::E fstar_e(const StepParams& p, const type
   return static_cast<const typename S::E*>(p.lost)[lost_index(p, a, y, x + cx(a) < 0)];
 }
 
-// ---------------------------------------------------------------------------
-// TMA (cp.async.bulk.tensor) staging of interior tiles through shared memory.
-// One elected thread arms an mbarrier with the stage's byte count and issues
-// one 3D tensor copy per plane; the block waits on the barrier's phase. Every
-// wait is bounded: on expiry the block records a timeout in the error flag,
-// waits (bounded) for its copies still in flight, and skips its tile.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned smem_u32(const void* ptr) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(ptr));
-}
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
-  unsigned done;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(done)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-// Bounded wait on a barrier phase: at most 2^20 polls and about one second
-// (2^31 SM clock cycles), whichever comes first.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  const long long start = clock64();
-  for (int i = 0; i < (1 << 20); ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (clock64() - start > (1ll << 31)) break;
-  }
-  return false;
-}
-__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map, int x, int y,
-                                            int z, unsigned bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
-      : "memory");
-}
-
-// Pull of direction A for the 8-row chunk in shared memory: `row` is this
-// warp's row of plane A (box of halo + tile + halo elements).
-template <class S, int N, int A>
-__device__ __forceinline__ void pull_dir_smem(const typename S::E* row, int lane,
-                                              typename S::T (&h)[N][9]) {
-  using T = typename S::T;
-  using E = typename S::E;
-  constexpr int HALO = 16 / int(sizeof(E));
-  T v[N];
-  S::load_h_plain(row + HALO + lane * N, v, A);
-  if (cx(A) == 0) {
-#pragma unroll
-    for (int k = 0; k < N; ++k) h[k][A] = v[k];
-  } else if (cx(A) == 1) {  // node k pulls from x - 1
-    T left = __shfl_up_sync(0xffffffffu, v[N - 1], 1);
-    if (lane == 0) left = S::in(row[HALO - 1], A);
-    h[0][A] = left;
-#pragma unroll
-    for (int k = 1; k < N; ++k) h[k][A] = v[k - 1];
-  } else {  // node k pulls from x + 1
-    T right = __shfl_down_sync(0xffffffffu, v[0], 1);
-    if (lane == kLanes - 1) right = S::in(row[HALO + kLanes * N], A);
-#pragma unroll
-    for (int k = 0; k < N - 1; ++k) h[k][A] = v[k + 1];
-    h[N - 1][A] = right;
-  }
-}
-
-// TMA: interior tiles are staged through shared memory (tma_smem, the
-// kernel's dynamic shared memory of tma_smem_bytes(STORE)); a separate kernel
-// instantiation, so the direct-pull kernel carries none of its code.
 // MODE: kModeAB (pull from p.src, store to p.dst), or one of the two in-place
 // AA steps on the one buffer p.dst (== p.src).
-template <int STORE, int COLL, bool TMA = false, int MODE = kModeAB>
-__device__ __forceinline__ void step_tile(const StepParams& p, int tile, long long t,
-                                          unsigned char* tma_smem) {
+template <int STORE, int COLL, int MODE = kModeAB>
+__device__ __forceinline__ void step_tile(const StepParams& p, int tile, long long t) {
   using S = Store<STORE>;
   using T = typename S::T;
   using E = typename S::E;
@@ -1016,7 +935,6 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
   constexpr int TX = kLanes * N;
   __shared__ double sm[kThreads / 32][3];
   __shared__ T smass[kThreads / 32];
-  __shared__ __align__(8) unsigned long long tma_bar[kTmaStages];
 
   const int lane = threadIdx.x, warp = threadIdx.y;
   const int tx = tile % p.tiles_x;
@@ -1027,7 +945,6 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
   const E* __restrict__ src = static_cast<const E*>(p.src);
   E* __restrict__ dst = static_cast<E*>(p.dst);
   E* buf = static_cast<E*>(p.dst);  // the in-place modes' one buffer (not restrict: read and written)
-  static_assert(MODE == kModeAB || !TMA, "TMA staging is for the A/B scheme");
 
   T dm = T(0);           // sum of drho over this thread's nodes
   T tfx = T(0), tfy = T(0);  // force on this thread's solid nodes (<= 16, arithmetic type)
@@ -1168,64 +1085,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
     process_row(y, h, gen);
   };
 
-  if (TMA && interior) {
-    // Chunk c (rows y0 + 8c .. y0 + 8c + 7, one per warp) of all nine planes
-    // goes to stage c % kTmaStages; plane A's box starts at row y0 + 8c - cy(A)
-    // and column x0 - halo, so the box row of warp w is the source row of
-    // direction A for node row y0 + 8c + w.
-    constexpr int HALO = tma_halo(STORE);
-    constexpr int BOX = tma_box_x(STORE);
-    constexpr unsigned STAGE = unsigned(tma_stage_bytes(STORE));
-    constexpr int PLANE = kTmaRows * BOX;  // elements of one plane's box
-    const int tid = lane + warp * kLanes;
-    auto issue = [&](int c) {
-      const unsigned bar = smem_u32(&tma_bar[c % kTmaStages]);
-      mbar_expect_tx(bar, STAGE);
-      const unsigned base = smem_u32(tma_smem + (c % kTmaStages) * STAGE);
-#pragma unroll
-      for (int a = 0; a < 9; ++a)
-        tma_load_3d(base + unsigned(a * PLANE * int(sizeof(E))), &p.tmap, x0 - HALO,
-                    y0 + c * kTmaRows - cy(a), a, bar);
-    };
-    if (tid == 0) {
-      for (int st = 0; st < kTmaStages; ++st) mbar_init(smem_u32(&tma_bar[st]), 1);
-      mbar_fence_init();
-    }
-    __syncthreads();
-    if (tid == 0)
-      for (int c = 0; c < kTmaStages && c < kRows; ++c) issue(c);
-    bool ok = true;
-#pragma unroll 1
-    for (int c = 0; c < kRows; ++c) {
-      const unsigned bar = smem_u32(&tma_bar[c % kTmaStages]);
-      const unsigned parity = unsigned(c / kTmaStages) & 1u;
-      ok = __syncthreads_and(ok && mbar_wait(bar, parity)) != 0;
-      if (!ok) {
-        // give up on this tile: record the timeout, let the copies in flight land
-        if (tid == 0) {
-          atomicOr(p.flag, 2);
-          for (int d = c; d < kRows && d < c + kTmaStages; ++d)  // issued, not yet landed
-            mbar_wait(smem_u32(&tma_bar[d % kTmaStages]), unsigned(d / kTmaStages) & 1u);
-        }
-        __syncthreads();
-        break;
-      }
-      const E* stage = reinterpret_cast<const E*>(tma_smem + (c % kTmaStages) * STAGE) + warp * BOX;
-      T h[N][9];
-      pull_dir_smem<S, N, 0>(stage + 0 * PLANE, lane, h);
-      pull_dir_smem<S, N, 1>(stage + 1 * PLANE, lane, h);
-      pull_dir_smem<S, N, 2>(stage + 2 * PLANE, lane, h);
-      pull_dir_smem<S, N, 3>(stage + 3 * PLANE, lane, h);
-      pull_dir_smem<S, N, 4>(stage + 4 * PLANE, lane, h);
-      pull_dir_smem<S, N, 5>(stage + 5 * PLANE, lane, h);
-      pull_dir_smem<S, N, 6>(stage + 6 * PLANE, lane, h);
-      pull_dir_smem<S, N, 7>(stage + 7 * PLANE, lane, h);
-      pull_dir_smem<S, N, 8>(stage + 8 * PLANE, lane, h);
-      __syncthreads();  // every warp has read stage c % kTmaStages
-      if (tid == 0 && c + kTmaStages < kRows) issue(c + kTmaStages);
-      process_row(y0 + warp + c * kWarps, h, std::false_type());
-    }
-  } else if (interior) {
+  if (interior) {
 #pragma unroll 1
     for (int r = 0; r < kRows; ++r) do_row(y0 + warp + r * kWarps, std::false_type());
   } else {
@@ -1282,10 +1142,9 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
   finish_reduction(p, tile, t, ts, sm);
 }
 
-template <int STORE, int COLL, bool TMA, int MODE = kModeAB>
+template <int STORE, int COLL, int MODE = kModeAB>
 __global__ void __launch_bounds__(kThreads, min_blocks_per_sm(STORE)) fused_step_kernel(const __grid_constant__ StepParams p) {
-  extern __shared__ __align__(128) unsigned char dyn_smem[];
-  step_tile<STORE, COLL, TMA, MODE>(p, blockIdx.x, p.t, dyn_smem);
+  step_tile<STORE, COLL, MODE>(p, blockIdx.x, p.t);
 }
 
 // Grouped launch for serving: block b runs tile table[b].tile of solver
@@ -1311,11 +1170,10 @@ __global__ void __launch_bounds__(kThreads, min_blocks_per_sm(STORE))
     for (int w = tid; w < int(sizeof(StepParams) / sizeof(int)); w += kThreads) to[w] = __ldg(from + w);
   }
   __syncthreads();
-  // grouped launches pull directly (use_tma is off in their parameters)
   if (sp.collision == kSrt)
-    step_tile<STORE, kSrt, false, MODE>(sp, gt.tile, sp.t + k, nullptr);
+    step_tile<STORE, kSrt, MODE>(sp, gt.tile, sp.t + k);
   else
-    step_tile<STORE, kMrt, false, MODE>(sp, gt.tile, sp.t + k, nullptr);
+    step_tile<STORE, kMrt, MODE>(sp, gt.tile, sp.t + k);
 }
 
 // ---------------------------------------------------------------------------

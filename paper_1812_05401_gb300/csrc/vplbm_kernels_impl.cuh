@@ -13,32 +13,14 @@ static dim3 node_grid(const StepParams& p) {
   return dim3((p.nx + kBlockX - 1) / kBlockX, (p.ny + kBlockY - 1) / kBlockY);
 }
 
-// Dynamic shared memory of the TMA-staged interior tiles (set once per
-// kernel: more than the default 48 KB needs an opt-in).
-template <int COLL>
-static cudaError_t allow_tma_smem() {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(fused_step_kernel<VPLBM_STORE, COLL, true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       tma_smem_bytes(VPLBM_STORE));
-  done = e == cudaSuccess;
-  return e;
-}
-
 template <int COLL>
 static cudaError_t launch_fused_coll(const StepParams& p, cudaStream_t st) {
   if (p.mode == kModeAAPush) {
-    fused_step_kernel<VPLBM_STORE, COLL, false, kModeAAPush><<<p.n_tiles, dim3(kLanes, kWarps), 0, st>>>(p);
+    fused_step_kernel<VPLBM_STORE, COLL, kModeAAPush><<<p.n_tiles, dim3(kLanes, kWarps), 0, st>>>(p);
   } else if (p.mode == kModeAALocal) {
-    fused_step_kernel<VPLBM_STORE, COLL, false, kModeAALocal><<<p.n_tiles, dim3(kLanes, kWarps), 0, st>>>(p);
-  } else if (p.use_tma) {
-    const cudaError_t e = allow_tma_smem<COLL>();
-    if (e != cudaSuccess) return e;
-    fused_step_kernel<VPLBM_STORE, COLL, true>
-        <<<p.n_tiles, dim3(kLanes, kWarps), tma_smem_bytes(VPLBM_STORE), st>>>(p);
+    fused_step_kernel<VPLBM_STORE, COLL, kModeAALocal><<<p.n_tiles, dim3(kLanes, kWarps), 0, st>>>(p);
   } else {
-    fused_step_kernel<VPLBM_STORE, COLL, false><<<p.n_tiles, dim3(kLanes, kWarps), 0, st>>>(p);
+    fused_step_kernel<VPLBM_STORE, COLL, kModeAB><<<p.n_tiles, dim3(kLanes, kWarps), 0, st>>>(p);
   }
   return cudaGetLastError();
 }

@@ -2,7 +2,6 @@
 // VP-LBM solver.
 #pragma once
 
-#include <cuda.h>
 #include <stdint.h>
 
 namespace vplbm {
@@ -95,27 +94,10 @@ struct StepParams {
   int reduce_mass;
   int stochastic;           // 16-bit stores: 1 = stochastic rounding, 0 = nearest even
   int collision;            // kSrt | kMrt (read by the grouped kernel)
-  int use_tma;              // interior tiles staged through shared memory by TMA
-  CUtensorMap tmap;  // src as a [9][ny][pitch] tensor, box {tile + halos, 8, 1}
 };
 
-// TMA staging of interior tiles: each chunk of 8 rows (one per warp) of all
-// nine planes, with a 16-byte halo on each side, lands in one shared-memory
-// stage; kTmaStages stages form a ring.
-constexpr int kTmaRows = 8;
-constexpr int kTmaStages = 2;
 __host__ __device__ constexpr int elem_bytes(int storage) {
   return storage == kF64 ? 8 : (storage == kF32 ? 4 : 2);
-}
-__host__ __device__ constexpr int tma_halo(int storage) { return 16 / elem_bytes(storage); }
-__host__ __device__ constexpr int tma_box_x(int storage) {
-  return tile_x(storage) + 2 * tma_halo(storage);
-}
-__host__ __device__ constexpr int tma_stage_bytes(int storage) {
-  return 9 * kTmaRows * tma_box_x(storage) * elem_bytes(storage);
-}
-__host__ __device__ constexpr int tma_smem_bytes(int storage) {
-  return kTmaStages * tma_stage_bytes(storage);
 }
 
 template <class T> __host__ __device__ inline const Consts<T>& consts(const StepParams& p);

@@ -428,24 +428,3 @@ def test_checkpoint_restart_is_bitwise(storage):
     with V.Solver(V.make_config(128, 64, "mrt", storage)) as c:
         with pytest.raises(V.VplbmError):
             V.vplbm_load_state(c.h, state)
-
-
-@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
-@pytest.mark.parametrize("bc", ["periodic", "channel"])
-def test_tma_staged_interior_matches_direct_pull(storage, bc, monkeypatch):
-    """VPLBM_TMA=1 stages interior tiles through shared memory with TMA tensor
-    copies; the arithmetic is the same, so the results are bitwise equal to the
-    direct vector pull (grid with interior and boundary tiles, a body, 30 steps)."""
-    w = I.cylinder_channel(600, 200, 24.0, 0.05, 150.0, 0, xc=200.0, storage=storage, seed=4)
-    if bc == "periodic":
-        w.bc = "periodic"
-    out = []
-    for flag in ("0", "1"):
-        monkeypatch.setenv("VPLBM_TMA", flag)
-        with V.Solver.from_workload(w) as s:
-            s.step(30)
-            s.synchronize()
-            out.append((s.populations(), s.forces()))
-    assert np.array_equal(out[0][0], out[1][0])
-    for x, y in zip(out[0][1], out[1][1]):
-        assert np.array_equal(x, y)
