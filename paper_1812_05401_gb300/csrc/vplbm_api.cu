@@ -434,12 +434,23 @@ void fill_bodies(const vplbm_solver* s, int64_t t, StepParams* p) {
   }
 }
 
+// Equilibrium offset f_eq(rho, u) - w in FP64 (host; inlet ghost column).
+void heq_host(double rho, double ux, double uy, double out[9]) {
+  static const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  static const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  static const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                              1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+  const double uu = ux * ux + uy * uy;
+  for (int a = 0; a < 9; ++a) {
+    const double xu = ex[a] * ux + ey[a] * uy;
+    out[a] = w[a] * ((rho - 1.0) + rho * (3.0 * xu + 4.5 * xu * xu - 1.5 * uu));
+  }
+}
+
 // Float copies of the FP64 constants.
 void round_consts(StepParams* p) {
   Consts<double>& d = p->cd;
   Consts<float>& f = p->cf;
-  f.omega = float(d.omega);
-  f.srt_pre = float(d.srt_pre);
   f.s_e = float(d.s_e);
   f.s_eps = float(d.s_eps);
   f.s_qx = float(d.s_qx);
@@ -453,6 +464,73 @@ void round_consts(StepParams* p) {
   for (int a = 0; a < 9; ++a) f.heq_in[a] = float(d.heq_in[a]);
   f.u_conv = float(d.u_conv);
   f.conv_inv = float(d.conv_inv);
+  f.t_hsp = float(d.t_hsp);
+  f.t_hsm = float(d.t_hsm);
+  f.t_1msp = float(d.t_1msp);
+  f.t_sp = float(d.t_sp);
+  f.t_c3p = float(d.t_c3p);
+  for (int k = 0; k < 2; ++k) {
+    f.t_a[k] = float(d.t_a[k]);
+    f.t_b[k] = float(d.t_b[k]);
+    f.t_am[k] = float(d.t_am[k]);
+    f.t_bm[k] = float(d.t_bm[k]);
+  }
+}
+
+// Collision and forcing constants of a configuration (FP64, then their float
+// copies), and the collision kernel that applies them: the two-rate form for
+// SRT and for MRT whose even moments share one rate and whose two heat-flux
+// moments share another (the printed S), the full moment-space form for any
+// other rates.
+void physics_consts(const vplbm_config* cfg, StepParams* p) {
+  Consts<double>& cd = p->cd;
+  if (cfg->use_rates) {
+    cd.s_e = cfg->rates[1];
+    cd.s_eps = cfg->rates[2];
+    cd.s_qx = cfg->rates[4];
+    cd.s_qy = cfg->rates[6];
+    cd.s_pxx = cfg->rates[7];
+    cd.s_pxy = cfg->rates[8];
+  } else {
+    // S = diag(0, s_n, s_n, 0, s_q, 0, s_q, s_n, s_n), s_n = 1/tau,
+    // Lambda = (1/s_n - 1/2)(1/s_q - 1/2)
+    const double sn = 1.0 / cfg->tau;
+    const double sq = 1.0 / (0.5 + cfg->lambda / (1.0 / sn - 0.5));
+    cd.s_e = cd.s_eps = cd.s_pxx = cd.s_pxy = sn;
+    cd.s_qx = cd.s_qy = sq;
+  }
+  double sp, sm;  // rates of the even and odd moments in the two-rate form
+  if (cfg->collision == VPLBM_SRT) {
+    sp = sm = 1.0 / cfg->tau;
+    p->collision = kTrt;
+  } else {
+    sp = cd.s_e;
+    sm = cd.s_qx;
+    const bool two_rate = cd.s_eps == sp && cd.s_pxx == sp && cd.s_pxy == sp && cd.s_qy == sm;
+    p->collision = two_rate ? kTrt : kMrt;
+  }
+  const double cp = 1.0 - 0.5 * sp, cm = 1.0 - 0.5 * sm;
+  cd.t_hsp = 0.5 * sp;
+  cd.t_hsm = 0.5 * sm;
+  cd.t_1msp = 1.0 - sp;
+  cd.t_sp = sp;
+  cd.t_c3p = 3.0 * cp;
+  cd.t_a[0] = 4.5 * sp / 9.0;
+  cd.t_a[1] = 4.5 * sp / 36.0;
+  cd.t_b[0] = 9.0 * cp / 9.0;
+  cd.t_b[1] = 9.0 * cp / 36.0;
+  cd.t_am[0] = 3.0 * sm / 9.0;
+  cd.t_am[1] = 3.0 * sm / 36.0;
+  cd.t_bm[0] = 3.0 * cm / 9.0;
+  cd.t_bm[1] = 3.0 * cm / 36.0;
+  cd.a_s = 0.5 / cfg->eta;
+  cd.kappa_s = (1.0 / cfg->eta) / (1.0 + 0.5 / cfg->eta);
+  cd.gx = cfg->body_force[0];
+  cd.gy = cfg->body_force[1];
+  heq_host(1.0, cfg->u_in[0], cfg->u_in[1], cd.heq_in);
+  cd.u_conv = cfg->u_conv;
+  cd.conv_inv = 1.0 / (1.0 + cfg->u_conv);
+  round_consts(p);
 }
 
 StepParams step_params(const vplbm_solver* s, int64_t t, int parity) {
@@ -469,7 +547,7 @@ StepParams step_params(const vplbm_solver* s, int64_t t, int parity) {
 }
 
 cudaError_t launch_fused(const vplbm_solver* s, const StepParams& p) {
-  const int coll = s->cfg.collision;
+  const int coll = p.collision;
   switch (s->cfg.storage) {
     case kF64: return launch_fused_f64(coll, p, s->stream);
     case kF32: return launch_fused_f32(coll, p, s->stream);
@@ -595,19 +673,6 @@ void tiles_of(const vplbm_config* c, int* tx, int* ty, int* nt, int* ng) {
   *ty = (c->ny + kTileY - 1) / kTileY;
   *nt = *tx * *ty;
   *ng = (*nt + kGroup - 1) / kGroup;
-}
-
-// Equilibrium offset f_eq(rho, u) - w in FP64 (host; inlet ghost column).
-void heq_host(double rho, double ux, double uy, double out[9]) {
-  static const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-  static const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-  static const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
-                              1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-  const double uu = ux * ux + uy * uy;
-  for (int a = 0; a < 9; ++a) {
-    const double xu = ex[a] * ux + ey[a] * uy;
-    out[a] = w[a] * ((rho - 1.0) + rho * (3.0 * xu + 4.5 * xu * xu - 1.5 * uu));
-  }
 }
 
 vplbm_status check_usable(vplbm_solver* s) {
@@ -781,36 +846,7 @@ vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
   p.mode = s->aa ? kModeAAPush : kModeAB;
   p.z = s->z;
   p.lost = s->lost;
-  Consts<double>& cd = p.cd;
-  cd.omega = 1.0 / cfg->tau;
-  cd.srt_pre = 1.0 - 1.0 / (2.0 * cfg->tau);
-  if (cfg->use_rates) {
-    cd.s_e = cfg->rates[1];
-    cd.s_eps = cfg->rates[2];
-    cd.s_qx = cfg->rates[4];
-    cd.s_qy = cfg->rates[6];
-    cd.s_pxx = cfg->rates[7];
-    cd.s_pxy = cfg->rates[8];
-  } else {
-    // S = diag(0, s_n, s_n, 0, s_q, 0, s_q, s_n, s_n), s_n = 1/tau,
-    // Lambda = (1/s_n - 1/2)(1/s_q - 1/2)
-    const double sn = 1.0 / cfg->tau;
-    const double sq = 1.0 / (0.5 + cfg->lambda / (1.0 / sn - 0.5));
-    cd.s_e = sn;
-    cd.s_eps = sn;
-    cd.s_qx = sq;
-    cd.s_qy = sq;
-    cd.s_pxx = sn;
-    cd.s_pxy = sn;
-  }
-  cd.a_s = 0.5 / cfg->eta;
-  cd.kappa_s = (1.0 / cfg->eta) / (1.0 + 0.5 / cfg->eta);
-  cd.gx = cfg->body_force[0];
-  cd.gy = cfg->body_force[1];
-  heq_host(1.0, cfg->u_in[0], cfg->u_in[1], cd.heq_in);
-  cd.u_conv = cfg->u_conv;
-  cd.conv_inv = 1.0 / (1.0 + cfg->u_conv);
-  round_consts(&p);
+  physics_consts(cfg, &p);
   p.partials = s->partials;
   p.group_partials = s->group_partials;
   p.counters = s->counters;
@@ -819,7 +855,6 @@ vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
   p.ring_len = cfg->force_ring_len;
   p.reduce_mass = cfg->reduce_mass ? 1 : 0;
   p.stochastic = cfg->rounding == VPLBM_ROUND_STOCHASTIC ? 1 : 0;
-  p.collision = cfg->collision;
 
   if ((st = vplbm_set_initial_velocity(s, nullptr)) != VPLBM_OK) return bail(st);
   *out = s;
@@ -1633,37 +1668,14 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_config* cfg, const vplbm_
   p.bc_y = cfg->bc_y;
   p.tiles_x = tx;
   p.n_tiles = nt;
-  Consts<double>& cd = p.cd;
-  cd.omega = 1.0 / cfg->tau;
-  cd.srt_pre = 1.0 - 1.0 / (2.0 * cfg->tau);
-  if (cfg->use_rates) {
-    cd.s_e = cfg->rates[1];
-    cd.s_eps = cfg->rates[2];
-    cd.s_qx = cfg->rates[4];
-    cd.s_qy = cfg->rates[6];
-    cd.s_pxx = cfg->rates[7];
-    cd.s_pxy = cfg->rates[8];
-  } else {
-    const double sn = 1.0 / cfg->tau;
-    const double sq = 1.0 / (0.5 + cfg->lambda / (1.0 / sn - 0.5));
-    cd.s_e = cd.s_eps = cd.s_pxx = cd.s_pxy = sn;
-    cd.s_qx = cd.s_qy = sq;
-  }
-  cd.a_s = 0.5 / cfg->eta;
-  cd.kappa_s = (1.0 / cfg->eta) / (1.0 + 0.5 / cfg->eta);
-  cd.gx = cfg->body_force[0];
-  cd.gy = cfg->body_force[1];
-  heq_host(1.0, cfg->u_in[0], cfg->u_in[1], cd.heq_in);
-  cd.u_conv = cfg->u_conv;
-  cd.conv_inv = 1.0 / (1.0 + cfg->u_conv);
-  round_consts(&p);
+  physics_consts(cfg, &p);
   p.n_bodies = n_bodies;
   for (int b = 0; b < n_bodies; ++b) {
     BodyState st;
     body_state(bodies[b], t, &st);
     const double v[5] = {st.cx, st.cy, st.vx, st.vy, st.omega};
     for (int k = 0; k < 5; ++k) {
-      cd.body[b][k] = v[k];
+      p.cd.body[b][k] = v[k];
       p.cf.body[b][k] = float(v[k]);
     }
   }
@@ -1678,10 +1690,10 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_config* cfg, const vplbm_
   p.t = t;
 
   switch (cfg->storage) {
-    case kF64: e = launch_fused_f64(cfg->collision, p, stream); break;
-    case kF32: e = launch_fused_f32(cfg->collision, p, stream); break;
-    case kF16: e = launch_fused_f16(cfg->collision, p, stream); break;
-    default: e = launch_fused_bf16(cfg->collision, p, stream); break;
+    case kF64: e = launch_fused_f64(p.collision, p, stream); break;
+    case kF32: e = launch_fused_f32(p.collision, p, stream); break;
+    case kF16: e = launch_fused_f16(p.collision, p, stream); break;
+    default: e = launch_fused_bf16(p.collision, p, stream); break;
   }
   if (e != cudaSuccess) {
     std::fprintf(stderr, "vplbm_step_noalloc: launch: %s\n", cudaGetErrorString(e));

@@ -404,10 +404,12 @@ template <class T>
 __device__ __forceinline__ Macro<T> macros(const StepParams& p, const T h[9], uint8_t m, int x,
                                            int y) {
   Macro<T> r;
-  r.drho = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
+  // sums and differences of opposite populations (the two-rate collision
+  // reuses them)
+  r.drho = h[0] + (((h[1] + h[3]) + (h[2] + h[4])) + ((h[5] + h[7]) + (h[6] + h[8])));
   r.rho = T(1) + r.drho;
-  const T jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
-  const T jy = (h[2] - h[4]) + (h[5] + h[6]) - (h[7] + h[8]);
+  const T jx = (h[1] - h[3]) + ((h[5] - h[7]) - (h[6] - h[8]));
+  const T jy = (h[2] - h[4]) + ((h[5] - h[7]) + (h[6] - h[8]));
   const Consts<T>& c = consts<T>(p);
   T usx = T(0), usy = T(0), a = T(0), kap = T(0);
   if (m) {
@@ -429,39 +431,54 @@ __device__ __forceinline__ Macro<T> macros(const StepParams& p, const T h[9], ui
 }
 
 // ---------------------------------------------------------------------------
-// Collision on offsets.
-// SRT (Eq. LatticeBoltz + Eq. Guo1):
-//   h* = h - omega (h - h_eq) + (1 - omega/2) w [3 (xi - u) + 9 (xi.u) xi] . F
-//   h_eq = w [drho + rho (3 xi.u + 4.5 (xi.u)^2 - 1.5 u.u)]
+// Collision on offsets, two-rate form.
+// The printed S relaxes the even moments (e, eps, p_xx, p_xy: symmetric under
+// xi -> -xi) at s+ = s_n and the odd ones (q_x, q_y) at s- = s_q; the rates of
+// rho, j_x and j_y do not change the result (rho = rho_eq, and j* = j + F for
+// any rate because m_eq uses the half-force velocity). Splitting each pair of
+// opposite populations into its even and odd parts, h+- = (h_a +- h_abar)/2,
+// Eq. equa_lbl_mrt with Eq. Guo2 is then, per pair,
+//   h*_a    = h_a    + P + Q,   h*_abar = h_abar + P - Q,
+//   P = -s+ (h+ - heq+) + (1 - s+/2) G+,   Q = -s- (h- - heq-) + (1 - s-/2) G-,
+// with heq+ = w (drho - 1.5 rho u.u + 4.5 rho (xi.u)^2), heq- = 3 w rho xi.u,
+// G+ = w (9 (xi.u)(xi.F) - 3 u.F), G- = 3 w xi.F (the even and odd parts of
+// Eq. Guo2's F_a), and for the rest population h*_0 = (1 - s+) h_0 + w_0 K,
+// K = s+ (drho - 1.5 rho u.u) - 3 (1 - s+/2) u.F. SRT with Eq. Guo1 is the
+// same with s+ = s- = 1/tau. This is the moment-space operator rearranged,
+// not an approximation of it.
 // ---------------------------------------------------------------------------
-template <class T, int A>
-__device__ __forceinline__ T srt_one(T h, T omega, T pre, T common, T rho, T ux, T uy, T Fx,
-                                     T Fy, T uF) {
-  const T xu = T(cx(A)) * ux + T(cy(A)) * uy;
-  const T xF = T(cx(A)) * Fx + T(cy(A)) * Fy;
-  const T heq = wgt<T>(A) * (common + rho * xu * (T(3) + T(4.5) * xu));
-  const T Fa = pre * wgt<T>(A) * (T(3) * (xF - uF) + T(9) * xu * xF);
-  return h - omega * (h - heq) + Fa;
+template <class T>
+__device__ __forceinline__ void trt_pair(T& ha, T& hb, T xu, T xF, T kw, T aw, T bw, T amw,
+                                         T bmw, T hsp, T hsm) {
+  const T s = ha + hb;
+  const T d = ha - hb;
+  const T rp = xu * (aw * xu + bw * xF) + kw;  // w (s+ heq+ + c+ G+)
+  const T rm = amw * xu + bmw * xF;            // w (s- heq- + c- G-)
+  const T P = rp - hsp * s;
+  const T Q = rm - hsm * d;
+  ha = ha + (P + Q);
+  hb = hb + (P - Q);
 }
 
 template <class T>
-__device__ __forceinline__ void collide_srt(const StepParams& p, T h[9], const Macro<T>& q) {
-  const T omega = consts<T>(p).omega, pre = consts<T>(p).srt_pre;
-  const T uu = q.ux * q.ux + q.uy * q.uy;
-  const T common = q.drho - T(1.5) * q.rho * uu;
-  const T uF = q.ux * q.Fx + q.uy * q.Fy;
-  h[0] = srt_one<T, 0>(h[0], omega, pre, common, q.rho, q.ux, q.uy, q.Fx, q.Fy, uF);
-  h[1] = srt_one<T, 1>(h[1], omega, pre, common, q.rho, q.ux, q.uy, q.Fx, q.Fy, uF);
-  h[2] = srt_one<T, 2>(h[2], omega, pre, common, q.rho, q.ux, q.uy, q.Fx, q.Fy, uF);
-  h[3] = srt_one<T, 3>(h[3], omega, pre, common, q.rho, q.ux, q.uy, q.Fx, q.Fy, uF);
-  h[4] = srt_one<T, 4>(h[4], omega, pre, common, q.rho, q.ux, q.uy, q.Fx, q.Fy, uF);
-  h[5] = srt_one<T, 5>(h[5], omega, pre, common, q.rho, q.ux, q.uy, q.Fx, q.Fy, uF);
-  h[6] = srt_one<T, 6>(h[6], omega, pre, common, q.rho, q.ux, q.uy, q.Fx, q.Fy, uF);
-  h[7] = srt_one<T, 7>(h[7], omega, pre, common, q.rho, q.ux, q.uy, q.Fx, q.Fy, uF);
-  h[8] = srt_one<T, 8>(h[8], omega, pre, common, q.rho, q.ux, q.uy, q.Fx, q.Fy, uF);
+__device__ __forceinline__ void collide_trt(const StepParams& p, T h[9], const Macro<T>& q) {
+  const Consts<T>& c = consts<T>(p);
+  const T ux = q.ux, uy = q.uy, Fx = q.Fx, Fy = q.Fy, rho = q.rho;
+  const T uu = ux * ux + uy * uy;
+  const T uF = ux * Fx + uy * Fy;
+  const T K = c.t_sp * (q.drho - T(1.5) * rho * uu) - c.t_c3p * uF;
+  const T k9 = K * T(1.0 / 9.0), k36 = K * T(1.0 / 36.0);
+  const T a9 = c.t_a[0] * rho, a36 = c.t_a[1] * rho;
+  const T am9 = c.t_am[0] * rho, am36 = c.t_am[1] * rho;
+  h[0] = c.t_1msp * h[0] + T(4.0 / 9.0) * K;
+  trt_pair<T>(h[1], h[3], ux, Fx, k9, a9, c.t_b[0], am9, c.t_bm[0], c.t_hsp, c.t_hsm);
+  trt_pair<T>(h[2], h[4], uy, Fy, k9, a9, c.t_b[0], am9, c.t_bm[0], c.t_hsp, c.t_hsm);
+  trt_pair<T>(h[5], h[7], ux + uy, Fx + Fy, k36, a36, c.t_b[1], am36, c.t_bm[1], c.t_hsp, c.t_hsm);
+  trt_pair<T>(h[6], h[8], uy - ux, Fy - Fx, k36, a36, c.t_b[1], am36, c.t_bm[1], c.t_hsp, c.t_hsm);
 }
 
-// MRT (Eq. equa_lbl_mrt with Lu forcing, Eq. Guo2), on the moments of h.
+// MRT (Eq. equa_lbl_mrt with Lu forcing, Eq. Guo2), on the moments of h, for
+// rates without the two-rate structure.
 // m = M h with M of Eq. eq1.7; since M w = (1, -2, 1, 0, ...), the equilibrium
 // moments of h are m_eq(rho, u) - M w. The forcing moments M F are
 // (0, 6 u.F, -6 u.F, F_x, -F_x, F_y, -F_y, 2 (u F_x - v F_y), u F_y + v F_x).
@@ -986,8 +1003,8 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
       nb[k] = sr ? round_bits(unsigned((long long)y * p.nx + (xb + k)), key) : 0u;
       if (GEN && xb + k >= p.nx) continue;  // past the last column: padding, stored as pulled
       const Macro<T> q = macros<T>(p, h[k], m[k], xb + k, y);
-      if (COLL == kSrt)
-        collide_srt<T>(p, h[k], q);
+      if (COLL == kTrt)
+        collide_trt<T>(p, h[k], q);
       else
         collide_mrt<T>(p, h[k], q);
       finish_node(q, m[k]);
@@ -1170,8 +1187,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks_per_sm(STORE))
     for (int w = tid; w < int(sizeof(StepParams) / sizeof(int)); w += kThreads) to[w] = __ldg(from + w);
   }
   __syncthreads();
-  if (sp.collision == kSrt)
-    step_tile<STORE, kSrt, MODE>(sp, gt.tile, sp.t + k);
+  if (sp.collision == kTrt)
+    step_tile<STORE, kTrt, MODE>(sp, gt.tile, sp.t + k);
   else
     step_tile<STORE, kMrt, MODE>(sp, gt.tile, sp.t + k);
 }

@@ -26,7 +26,7 @@ static cudaError_t launch_fused_coll(const StepParams& p, cudaStream_t st) {
 }
 
 cudaError_t VPLBM_FN(launch_fused_)(int coll, const StepParams& p, cudaStream_t st) {
-  return coll == kSrt ? launch_fused_coll<kSrt>(p, st) : launch_fused_coll<kMrt>(p, st);
+  return coll == kTrt ? launch_fused_coll<kTrt>(p, st) : launch_fused_coll<kMrt>(p, st);
 }
 
 cudaError_t VPLBM_FN(launch_group_)(const StepParams* d_params, const GroupTile* d_table,

@@ -7,7 +7,10 @@
 namespace vplbm {
 
 enum { kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
-enum { kSrt = 0, kMrt = 1 };
+// Collision kernels: kTrt, the two-rate form (SRT, and MRT whose even
+// moments relax at one rate and odd moments at another, as the printed S
+// does); kMrt, the moment-space form for any other rates.
+enum { kTrt = 0, kMrt = 1 };
 enum { kBcPeriodic = 0, kBcInletOutlet = 1, kBcFreeSlip = 2, kBcInletConvective = 3 };
 // Streaming schemes of the fused step: A/B buffers (pull from src, write dst),
 // or in-place AA-pattern streaming on one buffer, whose steps alternate
@@ -55,8 +58,13 @@ struct BodyState {
 // run at the FP64 rate).
 template <class T>
 struct Consts {
-  T omega, srt_pre;                       // 1/tau and 1 - 1/(2 tau)
   T s_e, s_eps, s_qx, s_qy, s_pxx, s_pxy;  // MRT rates
+  // two-rate form, s+ (even moments) and s- (odd moments), c+- = 1 - s+-/2:
+  T t_hsp, t_hsm;   // s+/2, s-/2
+  T t_1msp, t_sp;   // 1 - s+, s+
+  T t_c3p;          // 3 c+
+  T t_a[2], t_b[2];    // w 4.5 s+ and w 9 c+ for w = 1/9, 1/36
+  T t_am[2], t_bm[2];  // w 3 s- and w 3 c-
   T a_s, kappa_s;                         // 1/(2 eta) and (1/eta)/(1 + 1/(2 eta))
   T gx, gy;                               // body force per unit mass
   T heq_in[9];                            // inlet ghost f_eq(1, u_in) - w
@@ -93,7 +101,7 @@ struct StepParams {
   int ring_len;
   int reduce_mass;
   int stochastic;           // 16-bit stores: 1 = stochastic rounding, 0 = nearest even
-  int collision;            // kSrt | kMrt (read by the grouped kernel)
+  int collision;            // kTrt | kMrt (read by the grouped kernel)
 };
 
 __host__ __device__ constexpr int elem_bytes(int storage) {
