@@ -404,6 +404,21 @@ def run_gpu(args):
         rep = run_serving(args, n_requests=args.serve_requests, rate=args.serve_rate_bench,
                           quiet=True)
         extra["serving"] = rep
+        # the FP16-offset store against the plain FP32 store on the same
+        # requests: closed-loop capacity, then latency under Poisson arrivals,
+        # and each cylinder request's mean drag coefficient in the two forms
+        served = {}
+        for st in ("f32", "f16"):
+            cap = run_serving(args, n_requests=args.serve_requests_storage, rate=0.0, storage=st,
+                              quiet=True)
+            rep, res = run_serving(args, n_requests=args.serve_requests_storage,
+                                   rate=args.serve_rate_bench, storage=st, quiet=True,
+                                   want_results=True)
+            served[st] = res
+            extra[f"serving_{st}"] = {**rep, "capacity_solves_per_s": cap["solves_per_s"],
+                                      "capacity_mlups": cap["mlups"]}
+        extra["serving_f16_vs_f32_drag"] = drag_agreement(
+            args, served["f32"], served["f16"], n_requests=args.serve_requests_storage)
 
     peak, peak_src = hbm_peak()
     l2_bytes = getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0)
@@ -481,7 +496,7 @@ def run_serving_passes(args):
                       "serving": out}), flush=True)
 
 
-def drag_agreement(args, res32, res16):
+def drag_agreement(args, res32, res16, n_requests=None):
     """Mean drag coefficient (second half of each run) of every cylinder
     request served with FP16-offset storage against the same request served
     with FP32 storage; requests that diverged in either pass are left out.
@@ -493,7 +508,8 @@ def drag_agreement(args, res32, res16):
 
     from paper_1812_05401_gb300 import diag
     from paper_1812_05401_gb300 import inputs as I
-    reqs = {r.rid: r.workload for r in I.serving_mix(args.serve_requests, rate=1.0, seed=1234)}
+    reqs = {r.rid: r.workload for r in I.serving_mix(n_requests or args.serve_requests, rate=1.0,
+                                                        seed=1234)}
     a = {r.rid: r for r in res32 if not r.error}
     b = {r.rid: r for r in res16 if not r.error}
     rel, steady = [], []
@@ -681,6 +697,8 @@ def main():
     ap.add_argument("--oracle-rates", action="store_true",
                     help="time the FP64 oracle (CPU baseline) on every configuration, 1 thread and all cores")
     ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--serve-requests-storage", type=int, default=128,
+                    help="requests of each all-FP32 and all-FP16 serving pass in the default run")
     ap.add_argument("--serve-rate", type=float, default=0.0)
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--no-serving", dest="serve_in_bench", action="store_false",

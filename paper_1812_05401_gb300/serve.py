@@ -251,14 +251,22 @@ class Server:
 
     @staticmethod
     def report(results, makespan: float):
-        lat = np.array([r.latency for r in results]) if results else np.zeros(1)
-        updates = float(sum(r.nodes * r.steps for r in results))
+        """Throughput and latency of the served solves: those that finished
+        without an error. A solve that diverged or was stopped is counted in
+        `failed` and in the GPU work figure `mlups_all`, but not in
+        solves_per_s, the latency percentiles or `mlups`."""
+        ok = [r for r in results if not r.error]
+        lat = np.array([r.latency for r in ok]) if ok else np.full(1, np.nan)
+        updates = float(sum(r.nodes * r.steps for r in ok))
+        updates_all = float(sum(r.nodes * r.steps for r in results))
         return {
             "completed": len(results),
-            "failed": sum(1 for r in results if r.error),
+            "served": len(ok),
+            "failed": len(results) - len(ok),
             "makespan_s": round(makespan, 3),
-            "solves_per_s": round(len(results) / makespan, 3) if makespan > 0 else None,
+            "solves_per_s": round(len(ok) / makespan, 3) if makespan > 0 else None,
             "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
             "p99_latency_s": round(float(np.percentile(lat, 99)), 4),
             "mlups": round(updates / makespan / 1e6, 1) if makespan > 0 else None,
+            "mlups_all": round(updates_all / makespan / 1e6, 1) if makespan > 0 else None,
         }

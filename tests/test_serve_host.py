@@ -217,6 +217,22 @@ def test_report_percentiles():
     assert rep["mlups"] == 100 * 1000 * 100_000 / 20.0 / 1e6  # 500 MLUPS
 
 
+def test_report_counts_only_served_solves():
+    """A failed solve (diverged or stopped) is neither served throughput nor a
+    latency sample; its GPU work shows in mlups_all only."""
+    lat = np.linspace(0.1, 10.0, 100)
+    results = [S.Result(i, "r", 0.0, 0.0, float(x), 1000, 100_000, "f32", "srt",
+                        error="diverged" if i % 4 == 0 else None) for i, x in enumerate(lat)]
+    rep = S.Server.report(results, 20.0)
+    ok = lat[np.arange(100) % 4 != 0]
+    assert rep["completed"] == 100 and rep["served"] == 75 and rep["failed"] == 25
+    assert rep["solves_per_s"] == 75 / 20.0
+    assert rep["p50_latency_s"] == pytest.approx(np.percentile(ok, 50), abs=1e-4)
+    assert rep["p99_latency_s"] == pytest.approx(np.percentile(ok, 99), abs=1e-4)
+    assert rep["mlups"] == 75 * 1000 * 100_000 / 20.0 / 1e6
+    assert rep["mlups_all"] == 100 * 1000 * 100_000 / 20.0 / 1e6
+
+
 def test_deadlines_drop_waiting_requests_and_stop_running_ones(monkeypatch):
     """Fake clock, 1 ms per grouped step. "long" runs 3 rounds of 100 steps
     (0.3 s); "late" waits behind it for memory and its 0.15 s deadline passes
