@@ -1,28 +1,36 @@
-"""Wake statistics of the reduced-precision stores against the FP64 path.
+"""Wake statistics of every storage form against the FP64 oracle.
 
 Cylinder of D = 40 in a 1024 x 256 free-slip channel at Re = 100 (u = 0.05,
 MRT, Lambda = 3/16). Over tens of thousands of steps of an unsteady flow a
 pointwise comparison is meaningless, so the runs are compared through their
-statistics: mean drag C_Dave, RMS lift C_Lrms and Strouhal number St.
+statistics (Section 3.3): mean drag C_Dave, RMS lift C_Lrms and Strouhal
+number St.
 
-To compare the stationary shedding and not the precision-dependent time at
-which shedding starts, the FP64 path first develops the wake (60,000 steps
-from a 1e-4 seeded perturbation); every storage form then starts from that
-same state and runs 60,000 more steps (~14 shedding periods), all of which
-enter the statistics. The FP64 GPU path is the reference: it is held to the
-FP64 oracle within 1e-12 over 1000 steps in test_gpu_parity.
+The reference is the FP64 oracle's own run (tests/golden/c2_wake_statistics.json,
+written by tests/golden/c2_wake_statistics.py, which calls only the oracle):
+60,000 steps from the seeded initial state develop the wake, the next 60,000
+(about 14 shedding periods) are recorded. The FP64 GPU path repeats that run
+from the same initial state. Every other storage starts from the FP64 GPU
+path's state at step 60,000 and records the same window, so that the
+statistics compare the stationary shedding and not the precision-dependent
+time at which shedding starts.
 
-Tolerances (relative, C_Dave and St from the spectral peak):
-  FP32 storage                       1e-3 (measured 4.5e-4, 3.6e-4)
-  FP16 offsets, stochastic rounding  1e-3 (measured 6.5e-4, 8.7e-4)
-  BF16 offsets, stochastic rounding  1e-2 (measured 4.4e-3, 3.7e-3)
+Bars (relative, against the oracle):
+  FP64 storage                       1e-8 on C_Dave, C_Lrms and St
+  FP32 storage                       1e-3 on C_Dave and St
+  FP16 offsets, stochastic rounding  1e-3 on C_Dave and St
+  BF16 offsets, stochastic rounding  misses 1e-3 (8 significant bits): its
+      error is printed and held only to 1e-2, so that a change that makes it
+      worse is seen; the test's name says it misses the bar.
 With round-to-nearest-even the 16-bit forms do not reach 1e-3 on this flow:
 rounding f - w (~0.02) to 11 significant bits is about 20 times the viscous
 change of a population per step, and a deterministic rounding acts as a small
-systematic forcing (measured: FP16 C_Dave +4.5%, St +3%; BF16 C_Dave +8%,
-St -1.2%). Those bounds are the measured ones with margin. Stochastic
-rounding, the default for the 16-bit forms, removes the correlation.
+systematic forcing. Those tests document the effect with the FP64 GPU run as
+the reference and bounds that are the measured errors with margin.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -30,13 +38,12 @@ from paper_1812_05401_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-DEVELOP, MEASURE = 60_000, 60_000
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c2_wake_statistics.json")))
+DEVELOP, MEASURE = GOLDEN["develop_steps"], GOLDEN["measure_steps"]
 _cache = {}
 
 
-def _run(storage, rounding="nearest"):
-    if (storage, rounding) in _cache:
-        return _cache[(storage, rounding)]
+def _lib():
     import torch
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
@@ -44,13 +51,33 @@ def _run(storage, rounding="nearest"):
     B.build()
     from paper_1812_05401_gb300 import diag
     from paper_1812_05401_gb300 import vplbm as V
-    if "developed" not in _cache:
+    return V, diag
+
+
+def _fp64():
+    """The FP64 GPU run of the oracle's protocol: statistics of the window
+    and the state at its start."""
+    if "f64" not in _cache:
+        V, diag = _lib()
         w = I.c2_cylinder_re100()
         w.storage = "f64"
-        with V.Solver.from_workload(w, ring_len=16, reduce_mass=False) as s:
+        with V.Solver.from_workload(w, ring_len=MEASURE, reduce_mass=False) as s:
             s.step(DEVELOP)
             s.synchronize()
             _cache["developed"] = s.populations()
+            s.forces()  # the window's records only
+            s.step(MEASURE)
+            s.synchronize()
+            fx, fy, _ = s.forces()
+        _cache["f64"] = diag.wake_statistics(fx, fy, w.u_ref, w.l_ref, discard=0.0)
+    return _cache["f64"]
+
+
+def _run(storage, rounding="stochastic"):
+    if (storage, rounding) in _cache:
+        return _cache[(storage, rounding)]
+    _fp64()
+    V, diag = _lib()
     w = I.c2_cylinder_re100()
     w.storage = storage
     with V.Solver.from_workload(w, ring_len=MEASURE, reduce_mass=False,
@@ -64,30 +91,48 @@ def _run(storage, rounding="nearest"):
     return st
 
 
-def test_fp64_wake_is_periodic_shedding():
-    s = _run("f64")
-    assert 1.0 < s["C_D_ave"] < 3.0
-    assert 0.12 < s["St"] < 0.3
-    assert s["C_L_rms"] > 0.05  # shedding developed
-    assert s["St"] == pytest.approx(s["St_crossings"], rel=1e-2)
+def _rel(a, b):
+    return abs(a - b) / abs(b)
+
+
+def test_golden_is_periodic_shedding():
+    """The oracle's reference window is developed shedding (Re = 100)."""
+    assert 1.0 < GOLDEN["C_D_ave"] < 3.0
+    assert 0.12 < GOLDEN["St"] < 0.3
+    assert GOLDEN["C_L_rms"] > 0.05
+    assert GOLDEN["St"] == pytest.approx(GOLDEN["St_crossings"], rel=1e-2)
+
+
+def test_fp64_path_reproduces_oracle_statistics():
+    """The FP64 GPU path over the oracle's 120,000 steps: the same statistics
+    to 1e-8 (the two differ only in rounding order)."""
+    s = _fp64()
+    print("f64", s, "oracle", {k: GOLDEN[k] for k in ("C_D_ave", "C_L_rms", "St")})
+    for k in ("C_D_ave", "C_L_rms", "St"):
+        assert _rel(s[k], GOLDEN[k]) < 1e-8, k
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_storage_statistics_within_1e3_of_oracle(storage):
+    s = _run(storage)
+    err = {k: _rel(s[k], GOLDEN[k]) for k in ("C_D_ave", "C_L_rms", "St")}
+    print(storage, "relative error against the oracle", err)
+    assert err["C_D_ave"] < 1e-3
+    assert err["St"] < 1e-3
+
+
+def test_bf16_stochastic_misses_1e3_bar_reported():
+    s = _run("bf16")
+    err = {k: _rel(s[k], GOLDEN[k]) for k in ("C_D_ave", "C_L_rms", "St")}
+    print("bf16 relative error against the oracle (bar 1e-3, not met)", err)
+    assert err["C_D_ave"] < 1e-2 and err["St"] < 1e-2
 
 
 @pytest.mark.parametrize("storage,tol_cd,tol_st", [("f32", 1e-3, 1e-3), ("f16", 0.06, 0.05),
                                                    ("bf16", 0.12, 0.03)])
 def test_nearest_rounding_statistics(storage, tol_cd, tol_st):
-    ref = _run("f64")
+    ref = _fp64()
     s = _run(storage, "nearest")
     print(storage, "nearest", s, "ref", ref)
-    assert s["C_D_ave"] == pytest.approx(ref["C_D_ave"], rel=tol_cd)
-    assert s["St"] == pytest.approx(ref["St"], rel=tol_st)
-
-
-@pytest.mark.parametrize("storage,tol_cd,tol_st", [("f16", 1e-3, 1e-3), ("bf16", 1e-2, 1e-2)])
-def test_stochastic_rounding_statistics(storage, tol_cd, tol_st):
-    """16-bit offsets with stochastic rounding: the rounding errors no longer
-    correlate with the flow, so they average out of the statistics."""
-    ref = _run("f64")
-    s = _run(storage, "stochastic")
-    print(storage, "stochastic", s, "ref", ref)
     assert s["C_D_ave"] == pytest.approx(ref["C_D_ave"], rel=tol_cd)
     assert s["St"] == pytest.approx(ref["St"], rel=tol_st)
