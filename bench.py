@@ -234,40 +234,75 @@ def oracle_rates(budget_s: float = 8.0):
     print(json.dumps(out), flush=True)
 
 
-def oracle_sample(w, budget_s: float = 12.0, max_steps: int = 50):
-    """Runs the FP64 oracle on a window of the workload's grid: rows around the
-    body (at most 1024) and the first half of the columns (at most 8192), same
-    physics, as many steps as fit in budget_s. Returns (MLUPS, description,
-    threads)."""
+def oracle_config(w):
+    """The oracle's configuration of a workload (full grid, same physics)."""
     import oracle as O
     tau = O.tau_from_reynolds(w.u_ref, w.l_ref, w.re) if w.re else w.tau
-    ny = min(w.ny, 1024)
-    nx = min(w.nx, 8192)
-    y_off = max(0, int(w.bodies[0].cy) - ny // 2) if w.bodies else 0
-    bodies = [O.Body(b.cx, b.cy - y_off, b.radius, b.amp_x, b.amp_y, b.period, b.omega, b.outside)
-              for b in w.bodies]
     chan = w.bc == "channel"
-    cfg = O.Config(nx=nx, ny=ny, collision=O.MRT if w.collision == "mrt" else O.SRT, tau=tau,
-                   lam=w.lam, bc_x=O.BC_INLET_OUTLET if chan else O.BC_PERIODIC,
-                   bc_y=O.BC_FREE_SLIP if chan else O.BC_PERIODIC,
-                   u_in=(w.u_ref, 0.0) if chan else (0.0, 0.0), bodies=bodies)
-    import numpy as np
-    u0 = np.zeros((2, ny, nx))
-    if chan:
-        u0[0] = w.u_ref
-    f = O.init_equilibrium(cfg, 1.0, u0)
-    O.run(cfg, f, 1)  # warm-up (page-in)
-    steps, t0 = 0, time.perf_counter()
-    while steps < max_steps:
-        O.run(cfg, f, 1, t0=steps + 1)
-        steps += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
+    return O.Config(nx=w.nx, ny=w.ny, collision=O.MRT if w.collision == "mrt" else O.SRT, tau=tau,
+                    lam=w.lam, bc_x=O.BC_INLET_OUTLET if chan else O.BC_PERIODIC,
+                    bc_y=O.BC_FREE_SLIP if chan else O.BC_PERIODIC,
+                    u_in=(w.u_ref, 0.0) if chan else (0.0, 0.0),
+                    bodies=[O.Body(b.cx, b.cy, b.radius, b.amp_x, b.amp_y, b.period, b.omega,
+                                   b.outside) for b in w.bodies])
+
+
+def oracle_full(w, warmup: int, steps: int = 0, budget_s: float = 0.0):
+    """Times the FP64 oracle on the workload's full grid, on every host core:
+    `warmup` untimed steps, then `steps` timed steps (or, with steps = 0, as
+    many as fit in budget_s seconds). Returns (MLUPS, steps, seconds,
+    threads)."""
+    import oracle as O
+    cfg = oracle_config(w)
+    f = O.init_equilibrium(cfg, 1.0, w.initial_velocity())
+    if warmup:
+        O.run(cfg, f, warmup)
+    t0 = time.perf_counter()
+    if steps:
+        O.run(cfg, f, steps, t0=warmup)
+        n = steps
+    else:
+        n = 0
+        while n == 0 or time.perf_counter() - t0 < budget_s:
+            O.run(cfg, f, 1, t0=warmup + n)
+            n += 1
     dt = time.perf_counter() - t0
-    mlups = nx * ny * steps / dt / 1e6
-    desc = (f"FP64 oracle, {nx}x{ny} window of the {w.nx}x{w.ny} grid (rows around the body), "
-            f"{steps} steps, {dt:.1f} s")
-    return mlups, desc, O.num_threads()
+    return w.nx * w.ny * n / dt / 1e6, n, dt, O.num_threads()
+
+
+def device_l2_bytes() -> int:
+    """L2 size of GPU 0 from its device properties (0 without a GPU)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(getattr(torch.cuda.get_device_properties(0), "L2_cache_size", 0))
+    except Exception:
+        pass
+    return 0
+
+
+def l2_residency(nodes: int, storage: str, streaming: str, l2_bytes: int):
+    """(cache_resident, note): whether the population buffers fit in L2, and
+    the line's statement of it (inputs larger than L2 need no flush)."""
+    esize = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}[storage]
+    pop_bytes = (2 if streaming == "ab" else 1) * 9 * nodes * esize
+    if pop_bytes < l2_bytes:
+        return True, ("inputs fit in L2 (%.0f MB): population buffers of %.1f MB, cache-resident, "
+                      "so the roofline fraction is not a DRAM figure" % (l2_bytes / 1e6, pop_bytes / 1e6))
+    return False, "inputs larger than L2 (%.0f MB): %s population buffer%s of %.2f GB" % (
+        l2_bytes / 1e6, "two" if streaming == "ab" else "one in-place",
+        "s" if streaming == "ab" else "", 9 * nodes * esize / 1e9)
+
+
+def workload_config(w, storage: str, streaming: str, world: int, l2_note: str | None = None):
+    """The `config` object of the JSON line (both arms)."""
+    return {"workload": w.name + f" {w.collision.upper()} {storage.upper()}",
+            "nx": w.nx, "ny": w.ny, "nodes": w.nx * w.ny, "storage": storage,
+            "collision": w.collision, "re": w.re, "u_in": w.u_ref,
+            "step": "mask update of the moving body + fused pull/penalize/collide/reduce kernel",
+            "streaming": streaming,
+            **({"l2": l2_note} if l2_note else {}),
+            "parallelism": f"replicas x{world}"}
 
 
 # -----------------------------------------------------------------------------
@@ -397,6 +432,9 @@ def run_gpu(args):
     extra = {}
     if args.compare_f16 and args.storage == "f32":
         extra["f16_offset_store"] = side_run("f16", args.streaming)
+        extra["bf16_offset_store"] = side_run("bf16", args.streaming)
+    if args.precision:
+        extra["precision_vs_oracle"] = precision_record()
     if args.compare_aa and args.storage == "f32" and args.streaming == "ab":
         extra["aa_inplace"] = side_run("f32", "aa")
 
@@ -421,17 +459,8 @@ def run_gpu(args):
             args, served["f32"], served["f16"], n_requests=args.serve_requests_storage)
 
     peak, peak_src = hbm_peak()
-    l2_bytes = getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0)
-    esize = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}[args.storage]
-    pop_bytes = (2 if args.streaming == "ab" else 1) * 9 * nodes * esize
-    resident = pop_bytes < l2_bytes
-    if resident:
-        l2_note = ("inputs fit in L2 (%.0f MB): population buffers of %.1f MB, cache-resident, so "
-                   "the roofline fraction is not a DRAM figure" % (l2_bytes / 1e6, pop_bytes / 1e6))
-    else:
-        l2_note = "inputs larger than L2 (%.0f MB): %s population buffer%s of %.2f GB" % (
-            l2_bytes / 1e6, "two" if args.streaming == "ab" else "one in-place",
-            "s" if args.streaming == "ab" else "", 9 * nodes * esize / 1e9)
+    l2_bytes = device_l2_bytes()
+    resident, l2_note = l2_residency(nodes, args.storage, args.streaming, l2_bytes)
     kms = fused_ms / max(fused_n, 1)
     achieved = ALGO_BYTES[args.storage] * nodes / (kms / 1e3) / 1e9
     traffic = traffic_per_launch(args.workload, args.storage, args.streaming)
@@ -448,13 +477,7 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32" if args.storage != "f64" else "f64",
         "data": "synthetic",
-        "config": {"workload": w.name + f" {w.collision.upper()} {args.storage.upper()}",
-                   "nx": w.nx, "ny": w.ny, "nodes": nodes, "storage": args.storage,
-                   "collision": w.collision, "re": w.re, "u_in": w.u_ref,
-                   "step": "mask update of the moving body + fused pull/penalize/collide/reduce kernel",
-                   "streaming": args.streaming,
-                   "l2": l2_note,
-                   "parallelism": f"replicas x{world}"},
+        "config": workload_config(w, args.storage, args.streaming, world, l2_note),
         "e2e": {"value": round(e2e, 1), "unit": "MLUPS", "h2d_bytes_per_step": 704,
                 "d2h_bytes_per_step": 24,
                 "note": "public API per step: vplbm_step(1) then vplbm_forces (synchronizing read of F_x, F_y, mass)"},
@@ -471,13 +494,58 @@ def run_gpu(args):
     }
     result.update(extra)
     if rank == 0 and not args.no_cpu_baseline:
-        mlups, desc, cores = oracle_sample(w, args.cpu_budget)
-        result["cpu_baseline"] = {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores,
-                                  "kind": "oracle", "sample": desc}
+        mlups, n, dt, cores = oracle_full(w, warmup=1, budget_s=args.cpu_budget)
+        result["cpu_baseline"] = {
+            "value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle on the full {w.nx}x{w.ny} grid of this workload, {n} timed "
+                      f"steps after 1, {dt:.1f} s, {cores} threads of {os.cpu_count()} processors"}
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def precision_record():
+    """Wake statistics of each storage form against the FP64 oracle's (the
+    Re = 100 cylinder channel, 1024 x 256, MRT; the oracle's values are the
+    stored ones its own run wrote, tests/golden/c2_wake_statistics.json). The
+    FP64 path develops the wake over the oracle's development steps; FP32 and
+    the 16-bit offsets (stochastic rounding) then record the oracle's window
+    from that state. Relative errors of C_Dave and St; the benchmark spec's bar for
+    the reduced-precision stores is 1e-3."""
+    import torch
+
+    from paper_1812_05401_gb300 import diag
+    from paper_1812_05401_gb300 import inputs as I
+    from paper_1812_05401_gb300 import vplbm as V
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "c2_wake_statistics.json")))
+    dev, meas = g["develop_steps"], g["measure_steps"]
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    w = I.c2_cylinder_re100()
+    w.storage = "f64"
+    with V.Solver.from_workload(w, stream=stream, ring_len=16, reduce_mass=False) as s:
+        s.step(dev)
+        s.synchronize()
+        f0 = s.populations()
+    out = {"workload": w.name + " MRT", "window_steps": meas, "bar": 1e-3,
+           "reference": "FP64 oracle statistics (stored)"}
+    for st in ("f32", "f16", "bf16"):
+        w.storage = st
+        with V.Solver.from_workload(w, stream=stream, ring_len=meas, reduce_mass=False,
+                                    with_initial_velocity=False) as s:
+            s.set_populations(f0)
+            s.step(meas)
+            s.synchronize()
+            fx, fy, _ = s.forces()
+        r = diag.wake_statistics(fx, fy, w.u_ref, w.l_ref, discard=0.0)
+        e = {k: abs(r[k] - g[k]) / abs(g[k]) for k in ("C_D_ave", "C_L_rms", "St")}
+        out[st] = {"C_D_ave_rel_err": float(f"{e['C_D_ave']:.3g}"),
+                   "St_rel_err": float(f"{e['St']:.3g}"),
+                   "C_L_rms_rel_err": float(f"{e['C_L_rms']:.3g}"),
+                   "within_bar": bool(e["C_D_ave"] < 1e-3 and e["St"] < 1e-3)}
+    out["seconds"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 def run_serving_passes(args):
@@ -617,57 +685,24 @@ def run_grouped(args):
 
 
 def run_reference(args):
-    """Reference arm: the FP64 oracle on the host cores. One step = one oracle
-    step over a window of the workload's grid (rows around the body, at most
-    8192 columns); the window's height is sized from a calibration step so
-    that the W + K steps take about args.ref_budget seconds."""
+    """Reference arm: the FP64 oracle on the host cores, on the same workload
+    at its full grid size. One step = one oracle step of the whole grid; W
+    untimed steps, then K timed steps."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import numpy as np
-
-    import oracle as O
     w = make_workload(args.workload, args.storage)
-    tau = O.tau_from_reynolds(w.u_ref, w.l_ref, w.re) if w.re else w.tau
-    chan = w.bc == "channel"
-
-    def window(rows):
-        ny = max(8, min(w.ny, rows))
-        nx = min(w.nx, 8192)
-        y_off = max(0, int(w.bodies[0].cy) - ny // 2) if w.bodies else 0
-        bodies = [O.Body(b.cx, b.cy - y_off, b.radius, b.amp_x, b.amp_y, b.period, b.omega,
-                         b.outside) for b in w.bodies]
-        cfg = O.Config(nx=nx, ny=ny, collision=O.MRT if w.collision == "mrt" else O.SRT, tau=tau,
-                       lam=w.lam, bc_x=O.BC_INLET_OUTLET if chan else O.BC_PERIODIC,
-                       bc_y=O.BC_FREE_SLIP if chan else O.BC_PERIODIC,
-                       u_in=(w.u_ref, 0.0) if chan else (0.0, 0.0), bodies=bodies)
-        u0 = np.zeros((2, ny, nx))
-        if chan:
-            u0[0] = w.u_ref
-        return cfg, O.init_equilibrium(cfg, 1.0, u0)
-
-    cfg, f = window(256)
-    t0 = time.perf_counter()
-    O.run(cfg, f, 1)
-    rate = cfg.nx * cfg.ny / max(time.perf_counter() - t0, 1e-6)  # node updates per second
-    per_step = args.ref_budget / max(1, args.steps + args.warmup)
-    rows = int(rate * per_step / cfg.nx)
-    cfg, f = window(rows)
-    O.run(cfg, f, args.warmup)
-    t0 = time.perf_counter()
-    O.run(cfg, f, args.steps, t0=args.warmup)
-    dt = time.perf_counter() - t0
-    value = cfg.nx * cfg.ny * args.steps / dt / 1e6
-    desc = (f"FP64 oracle, {cfg.nx}x{cfg.ny} window of the {w.nx}x{w.ny} grid (rows around the "
-            f"body), {args.steps} timed steps after {args.warmup}, {dt:.1f} s")
+    value, n, dt, cores = oracle_full(w, warmup=args.warmup, steps=args.steps)
+    desc = (f"FP64 oracle on the full {w.nx}x{w.ny} grid of this workload, {n} timed steps "
+            f"after {args.warmup}, {dt:.1f} s, {cores} threads of {os.cpu_count()} processors")
     out = {"impl": "reference", "metric": "VP-LBM MLUPS (node updates per second / 1e6)",
            "value": round(value, 3), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 4),
+           "warmup": args.warmup, "ms_per_step": round(dt / n * 1e3, 4),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic",
-           "config": {"workload": w.name + f" {w.collision.upper()} {args.storage.upper()}",
-                      "nx": w.nx, "ny": w.ny, "oracle_window": f"{cfg.nx}x{cfg.ny}"},
-           "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": O.num_threads(),
+           "config": workload_config(w, args.storage, args.streaming, world, l2_residency(
+               w.nx * w.ny, args.storage, args.streaming, device_l2_bytes())[1]),
+           "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": cores,
                             "kind": "oracle", "sample": desc},
            "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
@@ -690,9 +725,10 @@ def main():
     ap.add_argument("--streaming", default="ab", choices=["ab", "aa"],
                     help="streaming scheme of the headline run (A/B buffers or in place)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=12.0)
-    ap.add_argument("--ref-budget", type=float, default=90.0,
-                    help="reference arm: seconds of oracle work for the warm-up and timed steps")
+    ap.add_argument("--no-precision", dest="precision", action="store_false",
+                    help="skip the storage forms' wake statistics against the oracle's")
+    ap.add_argument("--cpu-budget", type=float, default=12.0,
+                    help="seconds of timed oracle steps in the cpu_baseline leg")
     ap.add_argument("--serving", action="store_true", help="run only the serving mix")
     ap.add_argument("--oracle-rates", action="store_true",
                     help="time the FP64 oracle (CPU baseline) on every configuration, 1 thread and all cores")

@@ -57,9 +57,12 @@ enum { VPLBM_SRT = 0, /* BGK, Eq. LatticeBoltz with Guo forcing, Eq. Guo1 */
 
 /* Population storage. Arithmetic is FP64 for VPLBM_F64 and FP32 otherwise.
  * VPLBM_F64 stores f_alpha; VPLBM_F32 stores f_alpha - w_alpha in 32 bits
- * (the same bytes, a finer rounding step); the *_OFFSET forms store
- * f_alpha - w_alpha in 16 bits, rounded as vplbm_config.rounding says
- * (stochastically by default). */
+ * (the same bytes, a finer rounding step); the *_OFFSET forms store, in 16
+ * bits, f_alpha - r_alpha with the reference r = f_eq(1, u_in) (the inlet's
+ * equilibrium) when bc_x has an inlet, else r = w (the rest state), rounded as
+ * vplbm_config.rounding says (stochastically by default). Outside the wake a
+ * channel's populations stay near the inlet's equilibrium, so the 16-bit
+ * elements are small there and their rounding steps fine. */
 enum { VPLBM_F64 = 0, VPLBM_F32 = 1, VPLBM_F16_OFFSET = 2, VPLBM_BF16_OFFSET = 3 };
 
 /* Rounding of the 16-bit stores. NEAREST: round to nearest even.
@@ -133,7 +136,9 @@ typedef struct {
   void* stream;            /* cudaStream_t to run on, or NULL for a private stream */
   double u_conv;           /* convective outlet velocity U_c >= 0 (bc_x = INLET_CONVECTIVE) */
   int32_t streaming;       /* VPLBM_STREAM_AB (default) | VPLBM_STREAM_AA */
-  int32_t reserved;        /* 0 */
+  int32_t tile_rows;       /* rows of a fused-step tile: 8, 16 or 32, or 0 (default) for
+                              the tallest that gives the GPU's 152 SMs four waves of tiles;
+                              the tiles fix the order of the force and mass sums */
   /* Device memory hook (optional): both set, or both NULL (the default:
    * stream-ordered allocation from the CUDA memory pool on the solver's
    * stream). When set, every device buffer the solver owns comes from
@@ -324,7 +329,8 @@ vplbm_status vplbm_fused_timing(vplbm_solver* s, double* total_ms, int64_t* laun
  *  bodies    host array of n_bodies <= VPLBM_MAX_BODIES rigid bodies, evaluated
  *            at step t, or NULL with n_bodies = 0.
  *  f_src     device populations f*(t) in the storage type, [9][ny][pitch]
- *            (f for FP64, offsets f - w otherwise), 16-byte aligned.
+ *            (f for FP64, f - w for FP32, f - r for the 16-bit forms with r
+ *            the reference of the storage enum's comment), 16-byte aligned.
  *  f_dst     device output f*(t+1), same layout; must not alias f_src.
  *  mask      device [ny][pitch] bytes: 0 fluid, k = 1..n_bodies solid of body
  *            k (solid velocity from its motion), 255 solid with the velocity

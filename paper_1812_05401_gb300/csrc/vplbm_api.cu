@@ -462,6 +462,7 @@ void round_consts(StepParams* p) {
   f.gx = float(d.gx);
   f.gy = float(d.gy);
   for (int a = 0; a < 9; ++a) f.heq_in[a] = float(d.heq_in[a]);
+  for (int a = 0; a < 9; ++a) f.h_ref[a] = float(d.h_ref[a]);
   f.u_conv = float(d.u_conv);
   f.conv_inv = float(d.conv_inv);
   f.t_hsp = float(d.t_hsp);
@@ -527,7 +528,14 @@ void physics_consts(const vplbm_config* cfg, StepParams* p) {
   cd.kappa_s = (1.0 / cfg->eta) / (1.0 + 0.5 / cfg->eta);
   cd.gx = cfg->body_force[0];
   cd.gy = cfg->body_force[1];
+  p->force_free = cfg->body_force[0] == 0.0 && cfg->body_force[1] == 0.0 ? 1 : 0;
   heq_host(1.0, cfg->u_in[0], cfg->u_in[1], cd.heq_in);
+  // 16-bit stores of a channel keep offsets from the inlet's equilibrium, so
+  // that the elements outside the wake are near zero, where the 16-bit step
+  // is fine; other flows and storages keep offsets from the rest state
+  const bool sixteen = cfg->storage == VPLBM_F16_OFFSET || cfg->storage == VPLBM_BF16_OFFSET;
+  const bool inlet = cfg->bc_x == VPLBM_BC_INLET_OUTLET || cfg->bc_x == VPLBM_BC_INLET_CONVECTIVE;
+  for (int a = 0; a < 9; ++a) cd.h_ref[a] = sixteen && inlet ? cd.heq_in[a] : 0.0;
   cd.u_conv = cfg->u_conv;
   cd.conv_inv = 1.0 / (1.0 + cfg->u_conv);
   round_consts(p);
@@ -664,13 +672,31 @@ vplbm_status validate(const vplbm_config* c, std::string* why) {
     return *why = "unknown rounding", VPLBM_ERR_INVALID;
   if (!c->dev_alloc != !c->dev_free)
     return *why = "dev_alloc and dev_free must both be set or both be NULL", VPLBM_ERR_INVALID;
+  if (c->tile_rows != 0 && c->tile_rows != 8 && c->tile_rows != 16 && c->tile_rows != 32)
+    return *why = "tile_rows must be 0 (automatic), 8, 16 or 32", VPLBM_ERR_INVALID;
   return VPLBM_OK;
+}
+
+// Tile height of a configuration: the requested one, or (tile_rows = 0) the
+// tallest of 32, 16 and 8 rows that still gives four waves of blocks on the
+// GPU's 152 SMs (fewer, shorter waves leave SMs idle in the last one, which
+// small grids cannot hide). A fixed rule, so a configuration has one tile
+// decomposition (and one reduction order) on any device.
+constexpr long long kSmCount = 152;
+int tile_rows_of(const vplbm_config* c) {
+  if (c->tile_rows) return c->tile_rows;
+  const long long tx = (c->nx + tile_x(c->storage) - 1) / tile_x(c->storage);
+  const long long want = 4 * kSmCount * min_blocks_per_sm(c->storage);
+  int rows = kTileRowsMax;
+  while (rows > kWarps && tx * ((c->ny + rows - 1) / rows) < want) rows /= 2;
+  return rows;
 }
 
 void tiles_of(const vplbm_config* c, int* tx, int* ty, int* nt, int* ng) {
   const int tw = tile_x(c->storage);
+  const int rows = tile_rows_of(c);
   *tx = (c->nx + tw - 1) / tw;
-  *ty = (c->ny + kTileY - 1) / kTileY;
+  *ty = (c->ny + rows - 1) / rows;
   *nt = *tx * *ty;
   *ng = (*nt + kGroup - 1) / kGroup;
 }
@@ -843,6 +869,8 @@ vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
   p.bc_y = cfg->bc_y;
   p.tiles_x = s->tiles_x;
   p.n_tiles = s->n_tiles;
+  p.tile_y = tile_rows_of(cfg);
+  p.rows_per_warp = p.tile_y / kWarps;
   p.mode = s->aa ? kModeAAPush : kModeAB;
   p.z = s->z;
   p.lost = s->lost;
@@ -1668,6 +1696,8 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_config* cfg, const vplbm_
   p.bc_y = cfg->bc_y;
   p.tiles_x = tx;
   p.n_tiles = nt;
+  p.tile_y = tile_rows_of(cfg);
+  p.rows_per_warp = p.tile_y / kWarps;
   physics_consts(cfg, &p);
   p.n_bodies = n_bodies;
   for (int b = 0; b < n_bodies; ++b) {

@@ -44,36 +44,39 @@ __device__ __forceinline__ constexpr T wgt(int a) {
 }
 
 // ---------------------------------------------------------------------------
-// Storage traits: E is the element in HBM, T the arithmetic type.
+// Storage traits: E is the element in HBM, T the arithmetic type. Every call
+// takes `ref`, the per-direction reference the 16-bit stores keep their
+// elements relative to (the other stores ignore it): a 16-bit element holds
+// h - ref, h = f - w the offset the kernel works on.
 // ---------------------------------------------------------------------------
 template <int S> struct Store;
 template <> struct Store<kF64> {
   using E = double;
   using T = double;
   static constexpr bool kSixteen = false;
-  static __device__ __forceinline__ T in(E e, int a) { return e - wgt<T>(a); }
-  static __device__ __forceinline__ E out(T h, int a) { return h + wgt<T>(a); }
-  static __device__ __forceinline__ double to_f64(const E* p, int) { return *p; }
-  static __device__ __forceinline__ void from_f64(E* p, double f, int) { *p = f; }
+  static __device__ __forceinline__ T in(E e, int a, T) { return e - wgt<T>(a); }
+  static __device__ __forceinline__ E out(T h, int a, T) { return h + wgt<T>(a); }
+  static __device__ __forceinline__ double to_f64(const E* p, int, T) { return *p; }
+  static __device__ __forceinline__ void from_f64(E* p, double f, int, T) { *p = f; }
   // npt = 2 consecutive elements as one 16-byte access, as offsets h = f - w.
   // load_h_plain: a plain load, for a buffer the kernel also writes (the
   // in-place steps); load_h takes the read-only data path.
-  static __device__ __forceinline__ void load_h_plain(const E* p, T h[2], int a) {
+  static __device__ __forceinline__ void load_h_plain(const E* p, T h[2], int a, T) {
     const double2 v = *reinterpret_cast<const double2*>(p);
     h[0] = v.x - wgt<T>(a);
     h[1] = v.y - wgt<T>(a);
   }
-  static __device__ __forceinline__ void load_h(const E* p, T h[2], int a) {
+  static __device__ __forceinline__ void load_h(const E* p, T h[2], int a, T) {
     const double2 v = __ldg(reinterpret_cast<const double2*>(p));
     h[0] = v.x - wgt<T>(a);
     h[1] = v.y - wgt<T>(a);
   }
-  static __device__ __forceinline__ void store_h(E* p, const T h[2], int a, const unsigned*, bool) {
+  static __device__ __forceinline__ void store_h(E* p, const T h[2], int a, const unsigned*, bool, T) {
     *reinterpret_cast<double2*>(p) = make_double2(h[0] + wgt<T>(a), h[1] + wgt<T>(a));
   }
   // one element's raw bits, rounded as store_h rounds it (r: the node's word)
   using R = unsigned long long;
-  static __device__ __forceinline__ R round_e(T h, int a, unsigned, bool) {
+  static __device__ __forceinline__ R round_e(T h, int a, unsigned, bool, T) {
     return static_cast<R>(__double_as_longlong(h + wgt<T>(a)));
   }
 };
@@ -83,34 +86,34 @@ template <> struct Store<kF32> {
   using E = float;
   using T = float;
   static constexpr bool kSixteen = false;
-  static __device__ __forceinline__ T in(E e, int) { return e; }
-  static __device__ __forceinline__ E out(T h, int) { return h; }
-  static __device__ __forceinline__ double to_f64(const E* p, int a) {
+  static __device__ __forceinline__ T in(E e, int, T) { return e; }
+  static __device__ __forceinline__ E out(T h, int, T) { return h; }
+  static __device__ __forceinline__ double to_f64(const E* p, int a, T) {
     return wgt<double>(a) + double(*p);
   }
-  static __device__ __forceinline__ void from_f64(E* p, double f, int a) {
+  static __device__ __forceinline__ void from_f64(E* p, double f, int a, T) {
     *p = float(f - wgt<double>(a));
   }
   // npt = 4 consecutive elements as one 16-byte access
-  static __device__ __forceinline__ void load_h_plain(const E* p, T h[4], int) {
+  static __device__ __forceinline__ void load_h_plain(const E* p, T h[4], int, T) {
     const float4 v = *reinterpret_cast<const float4*>(p);
     h[0] = v.x;
     h[1] = v.y;
     h[2] = v.z;
     h[3] = v.w;
   }
-  static __device__ __forceinline__ void load_h(const E* p, T h[4], int) {
+  static __device__ __forceinline__ void load_h(const E* p, T h[4], int, T) {
     const float4 v = __ldg(reinterpret_cast<const float4*>(p));
     h[0] = v.x;
     h[1] = v.y;
     h[2] = v.z;
     h[3] = v.w;
   }
-  static __device__ __forceinline__ void store_h(E* p, const T h[4], int, const unsigned*, bool) {
+  static __device__ __forceinline__ void store_h(E* p, const T h[4], int, const unsigned*, bool, T) {
     *reinterpret_cast<float4*>(p) = make_float4(h[0], h[1], h[2], h[3]);
   }
   using R = unsigned;
-  static __device__ __forceinline__ R round_e(T h, int, unsigned, bool) { return __float_as_uint(h); }
+  static __device__ __forceinline__ R round_e(T h, int, unsigned, bool, T) { return __float_as_uint(h); }
 };
 // 16-bit offset forms: npt = 4 elements as one 8-byte access.
 // Multipliers deriving each direction's rounding bits from the node's word
@@ -154,7 +157,8 @@ __device__ __forceinline__ unsigned pair_bits(unsigned r_lo, unsigned r_hi) {
   return __byte_perm(r_lo, r_hi, 0x7632);
 }
 
-// 16-bit offset forms: npt = 4 elements as one 8-byte access.
+// 16-bit offset forms: npt = 4 elements as one 8-byte access; an element
+// holds h - ref (FP32 arithmetic on both sides of the conversion).
 template <class H>
 struct Store16 {
   using E = H;
@@ -162,99 +166,109 @@ struct Store16 {
   static constexpr bool kSixteen = true;
 };
 template <> struct Store<kF16> : Store16<__half> {
-  static __device__ __forceinline__ void load_h_plain(const E* p, T h[4], int a) {
-    unpack(*reinterpret_cast<const uint2*>(p), h);
+  static __device__ __forceinline__ void load_h_plain(const E* p, T h[4], int, T ref) {
+    unpack(*reinterpret_cast<const uint2*>(p), h, ref);
   }
-  static __device__ __forceinline__ void load_h(const E* p, T h[4], int) {
-    unpack(__ldg(reinterpret_cast<const uint2*>(p)), h);
+  static __device__ __forceinline__ void load_h(const E* p, T h[4], int, T ref) {
+    unpack(__ldg(reinterpret_cast<const uint2*>(p)), h, ref);
   }
-  static __device__ __forceinline__ void unpack(const uint2 v, T h[4]) {
+  static __device__ __forceinline__ void unpack(const uint2 v, T h[4], T ref) {
     const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
     const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
-    h[0] = a.x;
-    h[1] = a.y;
-    h[2] = b.x;
-    h[3] = b.y;
+    h[0] = a.x + ref;
+    h[1] = a.y + ref;
+    h[2] = b.x + ref;
+    h[3] = b.y + ref;
   }
   // r[k]: the node's rounding word for node k (stochastic rounding only)
   static __device__ __forceinline__ void store_h(E* p, const T h[4], int a, const unsigned* r,
-                                                 bool sr) {
+                                                 bool sr, T ref) {
     uint2 v;
     if (sr) {
       const unsigned m = round_mul(a);
-      v.x = pack_f16_rs(h[0], h[1], pair_bits(r[0] * m, r[1] * m));
-      v.y = pack_f16_rs(h[2], h[3], pair_bits(r[2] * m, r[3] * m));
+      v.x = pack_f16_rs(h[0] - ref, h[1] - ref, pair_bits(r[0] * m, r[1] * m));
+      v.y = pack_f16_rs(h[2] - ref, h[3] - ref, pair_bits(r[2] * m, r[3] * m));
     } else {
-      v.x = pack_f16_rn(h[0], h[1]);
-      v.y = pack_f16_rn(h[2], h[3]);
+      v.x = pack_f16_rn(h[0] - ref, h[1] - ref);
+      v.y = pack_f16_rn(h[2] - ref, h[3] - ref);
     }
     *reinterpret_cast<uint2*>(p) = v;
   }
-  static __device__ __forceinline__ T in(E e, int) { return __half2float(e); }
-  static __device__ __forceinline__ E out(T h, int) { return __float2half_rn(h); }
+  static __device__ __forceinline__ T in(E e, int, T ref) { return __half2float(e) + ref; }
+  static __device__ __forceinline__ E out(T h, int, T ref) { return __float2half_rn(h - ref); }
   // one element as store_h rounds it (the packed conversions round each half alike)
   using R = unsigned short;
-  static __device__ __forceinline__ R round_e(T h, int a, unsigned r, bool sr) {
-    return sr ? (unsigned short)(pack_f16_rs(h, 0.f, (r * round_mul(a)) >> 16) & 0xffffu)
-              : __half_as_ushort(__float2half_rn(h));
+  static __device__ __forceinline__ R round_e(T h, int a, unsigned r, bool sr, T ref) {
+    return sr ? (unsigned short)(pack_f16_rs(h - ref, 0.f, (r * round_mul(a)) >> 16) & 0xffffu)
+              : __half_as_ushort(__float2half_rn(h - ref));
   }
-  static __device__ __forceinline__ double to_f64(const E* p, int a) {
-    return wgt<double>(a) + double(__half2float(*p));
+  // f of a stored element: w + (element + ref), the offset as the kernel forms it
+  static __device__ __forceinline__ double to_f64(const E* p, int a, T ref) {
+    return wgt<double>(a) + double(__half2float(*p) + ref);
   }
-  static __device__ __forceinline__ void from_f64(E* p, double f, int a) {
-    *p = __double2half(f - wgt<double>(a));
+  static __device__ __forceinline__ void from_f64(E* p, double f, int a, T ref) {
+    *p = __double2half(f - wgt<double>(a) - double(ref));
   }
 };
 template <> struct Store<kBF16> : Store16<__nv_bfloat16> {
-  static __device__ __forceinline__ void load_h_plain(const E* p, T h[4], int) {
-    unpack(*reinterpret_cast<const uint2*>(p), h);
+  static __device__ __forceinline__ void load_h_plain(const E* p, T h[4], int, T ref) {
+    unpack(*reinterpret_cast<const uint2*>(p), h, ref);
   }
-  static __device__ __forceinline__ void load_h(const E* p, T h[4], int) {
-    unpack(__ldg(reinterpret_cast<const uint2*>(p)), h);
+  static __device__ __forceinline__ void load_h(const E* p, T h[4], int, T ref) {
+    unpack(__ldg(reinterpret_cast<const uint2*>(p)), h, ref);
   }
   // a bf16 is the upper half of an FP32: widening is a shift or a mask
-  static __device__ __forceinline__ void unpack(const uint2 v, T h[4]) {
-    h[0] = __uint_as_float(v.x << 16);
-    h[1] = __uint_as_float(v.x & 0xffff0000u);
-    h[2] = __uint_as_float(v.y << 16);
-    h[3] = __uint_as_float(v.y & 0xffff0000u);
+  static __device__ __forceinline__ void unpack(const uint2 v, T h[4], T ref) {
+    h[0] = __uint_as_float(v.x << 16) + ref;
+    h[1] = __uint_as_float(v.x & 0xffff0000u) + ref;
+    h[2] = __uint_as_float(v.y << 16) + ref;
+    h[3] = __uint_as_float(v.y & 0xffff0000u) + ref;
   }
   static __device__ __forceinline__ void store_h(E* p, const T h[4], int a, const unsigned* r,
-                                                 bool sr) {
+                                                 bool sr, T ref) {
     uint2 v;
     if (sr) {
       const unsigned m = round_mul(a);
-      v.x = pack_bf16_rs(h[0], h[1], pair_bits(r[0] * m, r[1] * m));
-      v.y = pack_bf16_rs(h[2], h[3], pair_bits(r[2] * m, r[3] * m));
+      v.x = pack_bf16_rs(h[0] - ref, h[1] - ref, pair_bits(r[0] * m, r[1] * m));
+      v.y = pack_bf16_rs(h[2] - ref, h[3] - ref, pair_bits(r[2] * m, r[3] * m));
     } else {
-      v.x = pack_bf16_rn(h[0], h[1]);
-      v.y = pack_bf16_rn(h[2], h[3]);
+      v.x = pack_bf16_rn(h[0] - ref, h[1] - ref);
+      v.y = pack_bf16_rn(h[2] - ref, h[3] - ref);
     }
     *reinterpret_cast<uint2*>(p) = v;
   }
-  static __device__ __forceinline__ T in(E e, int) { return __bfloat162float(e); }
-  static __device__ __forceinline__ E out(T h, int) { return __float2bfloat16_rn(h); }
+  static __device__ __forceinline__ T in(E e, int, T ref) { return __bfloat162float(e) + ref; }
+  static __device__ __forceinline__ E out(T h, int, T ref) { return __float2bfloat16_rn(h - ref); }
   using R = unsigned short;
-  static __device__ __forceinline__ R round_e(T h, int a, unsigned r, bool sr) {
-    return sr ? (unsigned short)(pack_bf16_rs(h, 0.f, (r * round_mul(a)) >> 16) & 0xffffu)
-              : __bfloat16_as_ushort(__float2bfloat16_rn(h));
+  static __device__ __forceinline__ R round_e(T h, int a, unsigned r, bool sr, T ref) {
+    return sr ? (unsigned short)(pack_bf16_rs(h - ref, 0.f, (r * round_mul(a)) >> 16) & 0xffffu)
+              : __bfloat16_as_ushort(__float2bfloat16_rn(h - ref));
   }
-  static __device__ __forceinline__ double to_f64(const E* p, int a) {
-    return wgt<double>(a) + double(__bfloat162float(*p));
+  static __device__ __forceinline__ double to_f64(const E* p, int a, T ref) {
+    return wgt<double>(a) + double(__bfloat162float(*p) + ref);
   }
-  static __device__ __forceinline__ void from_f64(E* p, double f, int a) {
-    *p = __double2bfloat16(f - wgt<double>(a));
+  static __device__ __forceinline__ void from_f64(E* p, double f, int a, T ref) {
+    *p = __double2bfloat16(f - wgt<double>(a) - double(ref));
   }
 };
 
-// Scalar offset load/store of one population.
+// The reference of direction a's stored elements (16-bit stores; 0 otherwise).
 template <class S>
-__device__ __forceinline__ typename S::T load_h(const typename S::E* p, int a) {
-  return S::in(__ldg(p), a);
+__device__ __forceinline__ typename S::T sref(const StepParams& p, int a) {
+  if constexpr (S::kSixteen)
+    return p.cf.h_ref[a];
+  else
+    return typename S::T(0);
+}
+
+// Scalar offset load/store of one population of direction a.
+template <class S>
+__device__ __forceinline__ typename S::T load_h(const StepParams& p, const typename S::E* ptr, int a) {
+  return S::in(__ldg(ptr), a, sref<S>(p, a));
 }
 template <class S>
-__device__ __forceinline__ void store_h(typename S::E* p, typename S::T h, int a) {
-  *p = S::out(h, a);
+__device__ __forceinline__ void store_h(const StepParams& p, typename S::E* ptr, typename S::T h, int a) {
+  *ptr = S::out(h, a, sref<S>(p, a));
 }
 
 // Random bits of the stochastic rounding: the MurmurHash3 32-bit finalizer
@@ -286,7 +300,7 @@ __device__ __forceinline__ typename S::T outlet_ghost(const StepParams& p,
   using T = typename S::T;
   const Consts<T>& c = consts<T>(p);
   const long long gi = (long long)(as == 3 ? 0 : (as == 6 ? 1 : 2)) * p.ny + ys;
-  const T f_last = load_h<S>(src + (long long)as * p.plane + (long long)ys * p.pitch + (p.nx - 1), as);
+  const T f_last = load_h<S>(p, src + (long long)as * p.plane + (long long)ys * p.pitch + (p.nx - 1), as);
   const T g = (static_cast<const T*>(p.ghost_src)[gi] + c.u_conv * f_last) * c.conv_inv;
   if (write) static_cast<T*>(p.ghost_dst)[gi] = g;
   return g;
@@ -300,7 +314,7 @@ __device__ __forceinline__ typename S::T outlet_ghost_aa(const StepParams& p, in
                                                          bool write) {
   using T = typename S::T;
   const long long gi = (long long)(as == 3 ? 0 : (as == 6 ? 1 : 2)) * p.ny + ys;
-  const T f_last = S::in(static_cast<const typename S::E*>(p.z)[gi], as);
+  const T f_last = S::in(static_cast<const typename S::E*>(p.z)[gi], as, sref<S>(p, as));
   if (p.bc_x != kBcInletConvective) return f_last;  // zero gradient
   const Consts<T>& c = consts<T>(p);
   const T g = (static_cast<const T*>(p.ghost_src)[gi] + c.u_conv * f_last) * c.conv_inv;
@@ -338,7 +352,7 @@ __device__ __forceinline__ typename S::T pull_bc(const StepParams& p, const type
       xs = p.nx - 1;
     }
   }
-  return load_h<S>(src + (long long)as * p.plane + (long long)ys * p.pitch + xs, A);
+  return load_h<S>(p, src + (long long)as * p.plane + (long long)ys * p.pitch + xs, as);
 }
 
 // The nine pulled populations of node (x, y), one at a time with the boundary
@@ -400,7 +414,10 @@ __device__ __forceinline__ void solid_velocity(const StepParams& p, uint8_t m, i
   // any other label (only a caller-written mask can hold one) is solid at rest
 }
 
-template <class T>
+// FREE: a fluid node (m = 0) without body force (g = 0), for which Eqs. 17
+// and 18 reduce to f_pen = 0 and u = j / rho; the same values as the general
+// form, which would compute them through zero terms.
+template <class T, bool FREE = false>
 __device__ __forceinline__ Macro<T> macros(const StepParams& p, const T h[9], uint8_t m, int x,
                                            int y) {
   Macro<T> r;
@@ -410,6 +427,13 @@ __device__ __forceinline__ Macro<T> macros(const StepParams& p, const T h[9], ui
   r.rho = T(1) + r.drho;
   const T jx = (h[1] - h[3]) + ((h[5] - h[7]) - (h[6] - h[8]));
   const T jy = (h[2] - h[4]) + ((h[5] - h[7]) + (h[6] - h[8]));
+  if constexpr (FREE) {
+    const T inv = recip(r.rho);
+    r.ux = jx * inv;
+    r.uy = jy * inv;
+    r.fpx = r.fpy = r.Fx = r.Fy = T(0);
+    return r;
+  }
   const Consts<T>& c = consts<T>(p);
   T usx = T(0), usy = T(0), a = T(0), kap = T(0);
   if (m) {
@@ -447,34 +471,37 @@ __device__ __forceinline__ Macro<T> macros(const StepParams& p, const T h[9], ui
 // same with s+ = s- = 1/tau. This is the moment-space operator rearranged,
 // not an approximation of it.
 // ---------------------------------------------------------------------------
-template <class T>
+template <class T, bool FREE>
 __device__ __forceinline__ void trt_pair(T& ha, T& hb, T xu, T xF, T kw, T aw, T bw, T amw,
                                          T bmw, T hsp, T hsm) {
   const T s = ha + hb;
   const T d = ha - hb;
-  const T rp = xu * (aw * xu + bw * xF) + kw;  // w (s+ heq+ + c+ G+)
-  const T rm = amw * xu + bmw * xF;            // w (s- heq- + c- G-)
+  // w (s+ heq+ + c+ G+) and w (s- heq- + c- G-); without a force G+- = 0
+  const T rp = FREE ? xu * (aw * xu) + kw : xu * (aw * xu + bw * xF) + kw;
+  const T rm = FREE ? amw * xu : amw * xu + bmw * xF;
   const T P = rp - hsp * s;
   const T Q = rm - hsm * d;
   ha = ha + (P + Q);
   hb = hb + (P - Q);
 }
 
-template <class T>
+template <class T, bool FREE = false>
 __device__ __forceinline__ void collide_trt(const StepParams& p, T h[9], const Macro<T>& q) {
   const Consts<T>& c = consts<T>(p);
   const T ux = q.ux, uy = q.uy, Fx = q.Fx, Fy = q.Fy, rho = q.rho;
   const T uu = ux * ux + uy * uy;
-  const T uF = ux * Fx + uy * Fy;
-  const T K = c.t_sp * (q.drho - T(1.5) * rho * uu) - c.t_c3p * uF;
+  const T K = FREE ? c.t_sp * (q.drho - T(1.5) * rho * uu)
+                   : c.t_sp * (q.drho - T(1.5) * rho * uu) - c.t_c3p * (ux * Fx + uy * Fy);
   const T k9 = K * T(1.0 / 9.0), k36 = K * T(1.0 / 36.0);
   const T a9 = c.t_a[0] * rho, a36 = c.t_a[1] * rho;
   const T am9 = c.t_am[0] * rho, am36 = c.t_am[1] * rho;
   h[0] = c.t_1msp * h[0] + T(4.0 / 9.0) * K;
-  trt_pair<T>(h[1], h[3], ux, Fx, k9, a9, c.t_b[0], am9, c.t_bm[0], c.t_hsp, c.t_hsm);
-  trt_pair<T>(h[2], h[4], uy, Fy, k9, a9, c.t_b[0], am9, c.t_bm[0], c.t_hsp, c.t_hsm);
-  trt_pair<T>(h[5], h[7], ux + uy, Fx + Fy, k36, a36, c.t_b[1], am36, c.t_bm[1], c.t_hsp, c.t_hsm);
-  trt_pair<T>(h[6], h[8], uy - ux, Fy - Fx, k36, a36, c.t_b[1], am36, c.t_bm[1], c.t_hsp, c.t_hsm);
+  trt_pair<T, FREE>(h[1], h[3], ux, Fx, k9, a9, c.t_b[0], am9, c.t_bm[0], c.t_hsp, c.t_hsm);
+  trt_pair<T, FREE>(h[2], h[4], uy, Fy, k9, a9, c.t_b[0], am9, c.t_bm[0], c.t_hsp, c.t_hsm);
+  trt_pair<T, FREE>(h[5], h[7], ux + uy, Fx + Fy, k36, a36, c.t_b[1], am36, c.t_bm[1], c.t_hsp,
+                    c.t_hsm);
+  trt_pair<T, FREE>(h[6], h[8], uy - ux, Fy - Fx, k36, a36, c.t_b[1], am36, c.t_bm[1], c.t_hsp,
+                    c.t_hsm);
 }
 
 // MRT (Eq. equa_lbl_mrt with Lu forcing, Eq. Guo2), on the moments of h, for
@@ -653,9 +680,9 @@ __device__ __forceinline__ void finish_reduction(const StepParams& p, int tile, 
 }
 
 // ---------------------------------------------------------------------------
-// The fused time step of one tile: (32 N) x 32 nodes, N = npt(STORE). Lane l
-// of warp w takes nodes x0 + N l .. x0 + N l + N - 1 of rows y0 + w + 8 r,
-// r = 0..kRows-1.
+// The fused time step of one tile: (32 N) x tile_y nodes, N = npt(STORE). Lane
+// l of warp w takes nodes x0 + N l .. x0 + N l + N - 1 of rows y0 + w + 8 r,
+// r = 0..rows_per_warp-1.
 //
 // Every direction is pulled with one N-element vector load per lane: a
 // direction with xi_x = +1 takes its first node's value from the lane to the
@@ -691,8 +718,8 @@ __device__ __forceinline__ typename S::T edge_pull(const StepParams& p, const ty
       xs = p.nx - 1;
     }
   }
-  if (AA) return S::in(src[(long long)opposite(as) * p.plane + (long long)ys * p.pitch + xs], A);
-  return load_h<S>(src + (long long)as * p.plane + (long long)ys * p.pitch + xs, A);
+  if (AA) return S::in(src[(long long)opposite(as) * p.plane + (long long)ys * p.pitch + xs], as, sref<S>(p, as));
+  return load_h<S>(p, src + (long long)as * p.plane + (long long)ys * p.pitch + xs, as);
 }
 
 template <class S, int N, int A, bool GEN, bool AA = false>
@@ -713,11 +740,12 @@ __device__ __forceinline__ void pull_dir_vec(const StepParams& p, const typename
   }
   const E* row = src + (long long)(AA ? opposite(as) : as) * p.plane + (long long)ys * p.pitch;
   T v[N];
+  const T ref = sref<S>(p, as);
   if (!GEN || lane_active) {
     if (AA)
-      S::load_h_plain(row + xb, v, A);
+      S::load_h_plain(row + xb, v, as, ref);
     else
-      S::load_h(row + xb, v, A);
+      S::load_h(row + xb, v, as, ref);
   } else {
 #pragma unroll
     for (int k = 0; k < N; ++k) v[k] = T(0);
@@ -731,7 +759,7 @@ __device__ __forceinline__ void pull_dir_vec(const StepParams& p, const typename
     // it lies outside the grid (the source row already carries the y rules)
     if (lane == 0)
       left = GEN && xb - 1 < 0 ? edge_pull<S, A, AA>(p, src, as, ys, xb - 1)
-                               : (AA ? S::in(row[xb - 1], A) : load_h<S>(row + xb - 1, A));
+                               : (AA ? S::in(row[xb - 1], as, ref) : S::in(__ldg(row + xb - 1), as, ref));
     h[0][A] = left;
 #pragma unroll
     for (int k = 1; k < N; ++k) h[k][A] = v[k - 1];
@@ -739,7 +767,7 @@ __device__ __forceinline__ void pull_dir_vec(const StepParams& p, const typename
     T right = __shfl_down_sync(0xffffffffu, v[0], 1);
     if (lane == kLanes - 1)
       right = GEN && xb + N >= p.nx ? edge_pull<S, A, AA>(p, src, as, ys, xb + N)
-                                    : (AA ? S::in(row[xb + N], A) : load_h<S>(row + xb + N, A));
+                                    : (AA ? S::in(row[xb + N], as, ref) : S::in(__ldg(row + xb + N), as, ref));
 #pragma unroll
     for (int k = 0; k < N - 1; ++k) h[k][A] = v[k + 1];
     h[N - 1][A] = right;
@@ -956,9 +984,9 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
   const int lane = threadIdx.x, warp = threadIdx.y;
   const int tx = tile % p.tiles_x;
   const int ty = tile / p.tiles_x;
-  const int x0 = tx * TX, y0 = ty * kTileY;
+  const int x0 = tx * TX, y0 = ty * p.tile_y;
   const int xb = x0 + lane * N;
-  const bool interior = x0 >= 1 && x0 + TX <= p.nx - 1 && y0 >= 1 && y0 + kTileY <= p.ny - 1;
+  const bool interior = x0 >= 1 && x0 + TX <= p.nx - 1 && y0 >= 1 && y0 + p.tile_y <= p.ny - 1;
   const E* __restrict__ src = static_cast<const E*>(p.src);
   E* __restrict__ dst = static_cast<E*>(p.dst);
   E* buf = static_cast<E*>(p.dst);  // the in-place modes' one buffer (not restrict: read and written)
@@ -984,38 +1012,40 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
   auto process_row = [&](int y, auto& h, auto gen) {
     constexpr bool GEN = decltype(gen)::value;
     const long long i = (long long)y * p.pitch + xb;
-    uint8_t m[N];
-    if (N == 4) {
-      const uchar4 mv = *reinterpret_cast<const uchar4*>(p.mask + i);
-      m[0] = mv.x;
-      m[1] = mv.y;
-      m[2 % N] = mv.z;
-      m[3 % N] = mv.w;
-    } else {
-      const uchar2 mv = *reinterpret_cast<const uchar2*>(p.mask + i);
-      m[0] = mv.x;
-      m[1 % N] = mv.y;
-    }
+    // the N mask bytes of this lane's nodes, byte k for node k (kept in one
+    // register: the collision's registers are the kernel's tightest budget)
+    const unsigned mw = N == 4 ? *reinterpret_cast<const unsigned*>(p.mask + i)
+                               : unsigned(*reinterpret_cast<const unsigned short*>(p.mask + i));
+    auto mk = [&](int k) -> uint8_t { return uint8_t(mw >> (8 * k)); };
     const bool sr = S::kSixteen && p.stochastic;
-    unsigned nb[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      nb[k] = sr ? round_bits(unsigned((long long)y * p.nx + (xb + k)), key) : 0u;
       if (GEN && xb + k >= p.nx) continue;  // past the last column: padding, stored as pulled
-      const Macro<T> q = macros<T>(p, h[k], m[k], xb + k, y);
-      if (COLL == kTrt)
-        collide_trt<T>(p, h[k], q);
-      else
-        collide_mrt<T>(p, h[k], q);
-      finish_node(q, m[k]);
+      if (COLL == kTrt && !GEN && p.force_free && mk(k) == 0) {
+        // a fluid node without body force: the force-free form of the step
+        const Macro<T> q = macros<T, true>(p, h[k], 0, xb + k, y);
+        collide_trt<T, true>(p, h[k], q);
+        finish_node(q, 0);
+      } else {
+        const Macro<T> q = macros<T>(p, h[k], mk(k), xb + k, y);
+        if (COLL == kTrt)
+          collide_trt<T>(p, h[k], q);
+        else
+          collide_mrt<T>(p, h[k], q);
+        finish_node(q, mk(k));
+      }
     }
+    // each node's rounding word (16-bit stores), computed after the collision
+    unsigned nb[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) nb[k] = sr ? round_bits(unsigned((long long)y * p.nx + (xb + k)), key) : 0u;
     if constexpr (MODE == kModeAB) {
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
         T o[N];
 #pragma unroll
         for (int k = 0; k < N; ++k) o[k] = h[k][a];
-        S::store_h(dst + (long long)a * p.plane + i, o, a, nb, sr);
+        S::store_h(dst + (long long)a * p.plane + i, o, a, nb, sr, sref<S>(p, a));
       }
     } else if constexpr (MODE == kModeAALocal) {
 #pragma unroll
@@ -1023,7 +1053,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
         T o[N];
 #pragma unroll
         for (int k = 0; k < N; ++k) o[k] = h[k][a];
-        S::store_h(buf + (long long)opposite(a) * p.plane + i, o, a, nb, sr);
+        S::store_h(buf + (long long)opposite(a) * p.plane + i, o, a, nb, sr, sref<S>(p, a));
       }
       if (GEN && p.bc_x != kBcPeriodic) {
         // the outlet column's stored f* of alpha = 3, 6, 7, for the next push step
@@ -1031,9 +1061,9 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
         for (int k = 0; k < N; ++k) {
           if (xb + k != p.nx - 1) continue;
           typename S::R* z = static_cast<typename S::R*>(p.z);
-          z[0 * p.ny + y] = S::round_e(h[k][3], 3, nb[k], sr);
-          z[1 * p.ny + y] = S::round_e(h[k][6], 6, nb[k], sr);
-          z[2 * p.ny + y] = S::round_e(h[k][7], 7, nb[k], sr);
+          z[0 * p.ny + y] = S::round_e(h[k][3], 3, nb[k], sr, sref<S>(p, 3));
+          z[1 * p.ny + y] = S::round_e(h[k][6], 6, nb[k], sr, sref<S>(p, 6));
+          z[2 * p.ny + y] = S::round_e(h[k][7], 7, nb[k], sr, sref<S>(p, 7));
         }
       }
     } else {  // push step
@@ -1045,7 +1075,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
       for (int a = 0; a < 9; ++a) {
         typename S::R e[N];
 #pragma unroll
-        for (int k = 0; k < N; ++k) e[k] = S::round_e(h[k][a], a, nb[k], sr);
+        for (int k = 0; k < N; ++k) e[k] = S::round_e(h[k][a], a, nb[k], sr, sref<S>(p, a));
         if (vec) {
           push_dir_vec<S, N>(p, buf, a, xb, y, lane, e);
         } else {
@@ -1058,9 +1088,9 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
 #pragma unroll
         for (int k = 0; k < N; ++k) {
           if (xb + k != p.nx - 1) continue;
-          push_outlet_copy<S>(p, buf, 3, y, S::round_e(h[k][3], 3, nb[k], sr));
-          push_outlet_copy<S>(p, buf, 6, y, S::round_e(h[k][6], 6, nb[k], sr));
-          push_outlet_copy<S>(p, buf, 7, y, S::round_e(h[k][7], 7, nb[k], sr));
+          push_outlet_copy<S>(p, buf, 3, y, S::round_e(h[k][3], 3, nb[k], sr, sref<S>(p, 3)));
+          push_outlet_copy<S>(p, buf, 6, y, S::round_e(h[k][6], 6, nb[k], sr, sref<S>(p, 6)));
+          push_outlet_copy<S>(p, buf, 7, y, S::round_e(h[k][7], 7, nb[k], sr, sref<S>(p, 7)));
         }
       }
     }
@@ -1076,7 +1106,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
         T v[N];
-        S::load_h_plain(buf + (long long)a * p.plane + i, v, a);
+        S::load_h_plain(buf + (long long)a * p.plane + i, v, a, sref<S>(p, a));
 #pragma unroll
         for (int k = 0; k < N; ++k) h[k][a] = v[k];
       }
@@ -1104,10 +1134,10 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
 
   if (interior) {
 #pragma unroll 1
-    for (int r = 0; r < kRows; ++r) do_row(y0 + warp + r * kWarps, std::false_type());
+    for (int r = 0; r < p.rows_per_warp; ++r) do_row(y0 + warp + r * kWarps, std::false_type());
   } else {
 #pragma unroll 1
-    for (int r = 0; r < kRows; ++r) {
+    for (int r = 0; r < p.rows_per_warp; ++r) {
       const int y = y0 + warp + r * kWarps;
       if (y >= p.ny) break;  // warp-uniform: a warp is one row
       do_row(y, std::true_type());
@@ -1151,7 +1181,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
     }
     if (p.reduce_mass) {
       // sum rho = active nodes + sum drho
-      const int nact = min(TX, p.nx - x0) * min(kTileY, p.ny - y0);
+      const int nact = min(TX, p.nx - x0) * min(p.tile_y, p.ny - y0);
       ts[2] = double(nact) + double(msum);
     }
   }
@@ -1219,7 +1249,8 @@ __device__ __forceinline__ void pull_node_any(const StepParams& p, int x, int y,
     pull_node<S>(p, buf, x, y, h);
   } else if (p.mode == kModeAALocal) {
 #pragma unroll
-    for (int a = 0; a < 9; ++a) h[a] = S::in(buf[(long long)a * p.plane + (long long)y * p.pitch + x], a);
+    for (int a = 0; a < 9; ++a)
+      h[a] = S::in(buf[(long long)a * p.plane + (long long)y * p.pitch + x], a, sref<S>(p, a));
     aa_local_boundary<S>(p, h, x, y, false);
   } else {
     h[0] = pull_aa<S, 0>(p, buf, x, y);
@@ -1305,7 +1336,7 @@ __global__ void __launch_bounds__(kThreads)
         if (p.mask[(long long)yf * p.pitch + xf] != 0) continue;
         const int o = opposite(a);
         const E ef = fstar_e<S>(p, src, a, xf, yf), es = fstar_e<S>(p, src, o, x, y);
-        const double flow = S::to_f64(&ef, a) + S::to_f64(&es, o);
+        const double flow = S::to_f64(&ef, a, sref<S>(p, a)) + S::to_f64(&es, o, sref<S>(p, o));
         fx += double(cx(a)) * flow;
         fy += double(cy(a)) * flow;
       }
@@ -1357,7 +1388,7 @@ __global__ void init_kernel(const __grid_constant__ StepParams p, void* dst, con
     const T heq = wgt<T>(a) * (common + rho * xu * (T(3) + T(4.5) * xu));
     // in place (AA), a state before a push step keeps f*_a in the opposite slot
     const int slot = p.mode == kModeAB ? a : opposite(a);
-    store_h<S>(d + (long long)slot * p.plane + i, heq, a);
+    store_h<S>(p, d + (long long)slot * p.plane + i, heq, a);
   }
 }
 
@@ -1375,7 +1406,7 @@ __global__ void ghost_init_kernel(const __grid_constant__ StepParams p, const vo
   const int k = i / p.ny, y = i - k * p.ny;
   const int a = k == 0 ? 3 : (k == 1 ? 6 : 7);
   const typename S::E e = fstar_e<S>(p, static_cast<const typename S::E*>(srcv), a, p.nx - 1, y);
-  if (ghostv) static_cast<T*>(ghostv)[i] = S::in(e, a);
+  if (ghostv) static_cast<T*>(ghostv)[i] = S::in(e, a, sref<S>(p, a));
   if (zv) static_cast<typename S::E*>(zv)[i] = e;
 }
 
@@ -1393,7 +1424,7 @@ __global__ void export_kernel(const __grid_constant__ StepParams p, const void* 
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     const typename S::E e = fstar_e<S>(p, src, a, x, y);
-    f[a * nn + o] = S::to_f64(&e, a);
+    f[a * nn + o] = S::to_f64(&e, a, sref<S>(p, a));
   }
   (void)i;
 }
@@ -1411,7 +1442,7 @@ __global__ void import_kernel(const __grid_constant__ StepParams p, void* dstv, 
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     const int slot = p.mode == kModeAB ? a : opposite(a);  // in place: before a push step
-    S::from_f64(dst + slot * p.plane + i, f[a * nn + o], a);
+    S::from_f64(dst + slot * p.plane + i, f[a * nn + o], a, sref<S>(p, a));
   }
 }
 

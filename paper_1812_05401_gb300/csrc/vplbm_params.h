@@ -21,14 +21,16 @@ enum { kModeAB = 0, kModeAAPush = 1, kModeAALocal = 2 };
 
 constexpr int kMaxBodies = 8;
 // Fused-step tiles: a block is 8 warps; each warp covers one row segment of
-// 32 lanes x npt(storage) consecutive nodes and kRows rows (8 apart), so a
-// tile is (32 npt) x 32 nodes. npt makes each lane's access 16 bytes for
-// FP32/FP64 storage (8 bytes for the 16-bit forms).
+// 32 lanes x npt(storage) consecutive nodes and rows_per_warp rows (8 apart),
+// so a tile is (32 npt) x (8 rows_per_warp) nodes. npt makes each lane's
+// access 16 bytes for FP32/FP64 storage (8 bytes for the 16-bit forms). The
+// tile height (8, 16 or 32 rows) is chosen per solver: 32 for grids with
+// enough tiles to fill the GPU several times over, shorter ones for grids
+// that would leave most of the last wave of blocks idle.
 constexpr int kLanes = 32;
 constexpr int kWarps = 8;
-constexpr int kRows = 4;
 constexpr int kThreads = kLanes * kWarps;
-constexpr int kTileY = kWarps * kRows;
+constexpr int kTileRowsMax = 32;
 // Resident blocks per SM the fused kernel is compiled for: 3 for the 8- and
 // 4-byte stores (80 registers per thread, 24 warps per SM, no spills), 4 for
 // the 16-bit stores, whose kernels are instruction-issue-bound and gain more
@@ -68,6 +70,7 @@ struct Consts {
   T a_s, kappa_s;                         // 1/(2 eta) and (1/eta)/(1 + 1/(2 eta))
   T gx, gy;                               // body force per unit mass
   T heq_in[9];                            // inlet ghost f_eq(1, u_in) - w
+  T h_ref[9];                             // 16-bit stores: elements hold h - h_ref
   T u_conv, conv_inv;                     // convective outlet: U_c and 1/(1 + U_c)
   T body[kMaxBodies][5];                  // cx, cy, vx, vy, omega of each body
 };
@@ -88,6 +91,7 @@ struct StepParams {
   int nx, ny, pitch;
   int bc_x, bc_y;
   int tiles_x, n_tiles;
+  int tile_y, rows_per_warp;  // tile height (8, 16 or 32) and tile_y / kWarps
   int n_bodies;
   long long plane;          // pitch * ny
   Consts<double> cd;        // constants for the FP64 kernels
@@ -102,6 +106,7 @@ struct StepParams {
   int reduce_mass;
   int stochastic;           // 16-bit stores: 1 = stochastic rounding, 0 = nearest even
   int collision;            // kTrt | kMrt (read by the grouped kernel)
+  int force_free;           // 1: no body force (g = 0), so fluid nodes feel no force
 };
 
 __host__ __device__ constexpr int elem_bytes(int storage) {

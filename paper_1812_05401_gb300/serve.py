@@ -37,6 +37,8 @@ import numpy as np
 
 from . import vplbm as V
 
+SERVE_TILE_ROWS = 32
+
 
 @dataclass
 class Result:
@@ -100,8 +102,10 @@ class Server:
             self._cancelled.add(rid)
 
     def _create(self, w):
+        # full-height tiles: a grouped launch of many solves already fills the
+        # GPU, and taller tiles run the per-tile reduction less often
         cfg, bodies = V.config_from_workload(w, ring_len=max(1, w.steps), stream=self.stream,
-                                             reduce_mass=False)
+                                             reduce_mass=False, tile_rows=SERVE_TILE_ROWS)
         u0 = (w.u_ref, 0.0) if w.bc == "channel" else (0.0, 0.0)
         s = V.Solver(cfg, bodies, perturbation=(u0[0], u0[1], w.perturbation, w.seed))
         return s, V.vplbm_footprint_bytes(cfg)
@@ -199,7 +203,8 @@ class Server:
                     emit({"rid": req.rid, "name": req.workload.name, "arrival": arrived(req),
                           "dropped": why, "at": t})
                     continue
-                cfg, _ = V.config_from_workload(req.workload, ring_len=max(1, req.workload.steps))
+                cfg, _ = V.config_from_workload(req.workload, ring_len=max(1, req.workload.steps),
+                                                tile_rows=SERVE_TILE_ROWS)
                 fp = V.vplbm_footprint_bytes(cfg)
                 if fp > self.budget:
                     self.rejected.append(req.rid)

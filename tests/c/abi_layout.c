@@ -41,7 +41,7 @@ int main(void) {
   FIELD(vplbm_config, stream);
   FIELD(vplbm_config, u_conv);
   FIELD(vplbm_config, streaming);
-  FIELD(vplbm_config, reserved);
+  FIELD(vplbm_config, tile_rows);
   FIELD(vplbm_config, dev_alloc);
   FIELD(vplbm_config, dev_free);
   FIELD(vplbm_config, alloc_ctx);

@@ -1,8 +1,9 @@
 /* The C ABI end to end: a cylinder in a channel at Re = 100 (uniform inlet,
  * zero-gradient outlet, free-slip walls), MRT with FP32 storage, stepped on
  * the GPU; prints the mean drag coefficient of the second half of the run.
- * Built (not run) by the CPU tests so that it stays valid against the header;
- * running it needs a GPU:
+ * Usage: cylinder [nx ny diameter steps] (default 1024 256 40 20000). The CPU
+ * tests build it against the header; a GPU test runs it on a small case and
+ * compares its drag with the FP64 oracle's.
  *   gcc -std=c11 -I include tests/c/example_cylinder.c \
  *       -L paper_1812_05401_gb300 -lvplbm -Wl,-rpath,paper_1812_05401_gb300 -o cylinder
  */
@@ -18,9 +19,23 @@ static int check(vplbm_status st, const vplbm_solver* s, const char* what) {
   return 1;
 }
 
-int main(void) {
-  const int nx = 1024, ny = 256, steps = 20000;
-  const double u = 0.05, d = 40.0, re = 100.0;
+int main(int argc, char** argv) {
+  int nx = 1024, ny = 256, steps = 20000;
+  double d = 40.0;
+  const double u = 0.05, re = 100.0;
+  if (argc == 5) {
+    nx = atoi(argv[1]);
+    ny = atoi(argv[2]);
+    d = atof(argv[3]);
+    steps = atoi(argv[4]);
+  } else if (argc != 1) {
+    fprintf(stderr, "usage: %s [nx ny diameter steps]\n", argv[0]);
+    return 2;
+  }
+  if (nx < 1 || ny < 1 || steps < 2 || !(d > 0.0)) {
+    fprintf(stderr, "need nx, ny >= 1, steps >= 2 and a positive diameter\n");
+    return 2;
+  }
 
   vplbm_config cfg;
   vplbm_config_init(&cfg);
@@ -57,7 +72,7 @@ int main(void) {
     double sum = 0.0;
     for (int64_t k = n / 2; k < n; ++k) sum += fx[k];
     const double cd = sum / (double)(n - n / 2) / (0.5 * u * u * d); /* rho_ref = 1 */
-    printf("mean C_D over steps %lld..%lld: %.4f\n", (long long)(n / 2), (long long)n, cd);
+    printf("mean C_D over steps %lld..%lld: %.9f\n", (long long)(n / 2), (long long)n, cd);
     rc = 0;
   }
   free(fx);

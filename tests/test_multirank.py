@@ -56,7 +56,7 @@ def test_reference_arm_under_torchrun_prints_once():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
            "--master-addr=127.0.0.1", f"--master-port={port}", os.path.join(ROOT, "bench.py"),
            "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0",
-           "--workload", "cylinder-re100", "--ref-budget", "2"]
+           "--workload", "cylinder-re100"]
     r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300,
                        env=dict(os.environ, OMP_NUM_THREADS="2"))
     assert r.returncode == 0, r.stderr[-2000:]

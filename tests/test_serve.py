@@ -36,7 +36,7 @@ def test_results_identical_alone_and_in_the_mix(mods):
     by_id = {r.rid: r for r in results}
     for req in reqs[::3]:
         with V.Solver.from_workload(req.workload, ring_len=max(1, req.workload.steps),
-                                    reduce_mass=False) as s:
+                                    reduce_mass=False, tile_rows=serve.SERVE_TILE_ROWS) as s:
             s.step(req.workload.steps)
             f = s.populations()
             fx, fy, _ = s.forces()
@@ -50,7 +50,8 @@ def test_admission_by_memory_budget(mods):
     reqs = _small_mix(8, seed=11)
     fps = []
     for r in reqs:
-        cfg, _ = V.config_from_workload(r.workload, ring_len=max(1, r.workload.steps))
+        cfg, _ = V.config_from_workload(r.workload, ring_len=max(1, r.workload.steps),
+                                        tile_rows=serve.SERVE_TILE_ROWS)
         fps.append(V.vplbm_footprint_bytes(cfg))
     budget = max(fps) + min(fps)  # at most about two solves at a time
     srv = serve.Server(budget_bytes=budget, max_active=8, round_steps=32)
@@ -106,6 +107,44 @@ def test_a_diverging_solve_fails_alone(mods):
             continue
         assert by_id[req.rid].error is None
         with V.Solver.from_workload(req.workload, ring_len=max(1, req.workload.steps),
-                                    reduce_mass=False, device_init=True) as s:
+                                    reduce_mass=False, device_init=True,
+                                    tile_rows=serve.SERVE_TILE_ROWS) as s:
             s.step(req.workload.steps)
             assert np.array_equal(s.populations(), by_id[req.rid].populations)
+
+
+def test_fp16_store_serves_steady_drag_within_1e3_of_fp32(mods):
+    """The serving precision bar: the same requests served with FP16-offset
+    storage and with FP32 storage give mean drag coefficients (second half of
+    the run) within 1e-3 of each other where the drag is stationary: cylinder
+    channels below the onset of vortex shedding (Re < 47), SRT and MRT, of
+    the mix's smaller sizes, 20,000 steps each. Every solve succeeds."""
+    serve, V = mods
+    from paper_1812_05401_gb300 import diag
+    reqs = {"f32": [], "f16": []}
+    rid = 0
+    for side in (64, 96, 128):
+        for re in (25.0, 40.0):
+            d = max(4.0, round(40.0 * side / 256.0))
+            for st in reqs:
+                w = I.cylinder_channel(4 * side, side, d, 0.05, re, 20_000,
+                                       collision="srt" if rid % 2 else "mrt", storage=st,
+                                       perturbation=1e-4, seed=100 + rid)
+                reqs[st].append(I.Request(rid, 0.0, w))
+            rid += 1
+    served = {}
+    for st, rq in reqs.items():
+        srv = serve.Server(budget_bytes=1 << 32, max_active=16, round_steps=500)
+        results, rep = srv.run(rq, realtime=False)
+        assert rep["failed"] == 0 and rep["served"] == len(rq)
+        served[st] = {r.rid: r for r in results}
+    for req in reqs["f32"]:
+        w = req.workload
+        cd = []
+        for st in ("f32", "f16"):
+            r = served[st][req.rid]
+            c, _ = diag.coefficients(r.fx, r.fy, w.u_ref, w.l_ref)
+            cd.append(float(np.mean(c[len(c) // 2:])))
+        rel = abs(cd[1] - cd[0]) / abs(cd[0])
+        print(w.name, w.collision, "C_D f32", cd[0], "f16", cd[1], "rel", rel)
+        assert rel < 1e-3, w.name

@@ -59,7 +59,7 @@ class FakeLib:
 
         self.Solver = Solver
 
-    def config_from_workload(self, w, ring_len=4096, stream=None, reduce_mass=True):
+    def config_from_workload(self, w, ring_len=4096, stream=None, reduce_mass=True, tile_rows=0):
         assert ring_len >= w.steps  # the whole force series fits the ring
         return types.SimpleNamespace(w=w), list(w.bodies)
 

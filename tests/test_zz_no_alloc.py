@@ -51,11 +51,27 @@ def _dtype(storage):
             "bf16": torch.bfloat16}[storage]
 
 
+U_IN = (0.04, 0.0)  # the channel's inlet velocity in these tests
+XI = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]])
+
+
+def _ref(storage):
+    """Per-direction reference of the 16-bit elements of a channel: the
+    offsets of the inlet's equilibrium, f_eq(1, u_in) - w, as FP32 (the
+    kernel's arithmetic); zero for the other storages."""
+    if storage not in ("f16", "bf16"):
+        return np.zeros(9)
+    xu = XI @ np.array(U_IN)
+    uu = U_IN[0] ** 2 + U_IN[1] ** 2
+    return (W * (3.0 * xu + 4.5 * xu * xu - 1.5 * uu)).astype(np.float32).astype(np.float64)
+
+
 def _store(f, storage):
-    """The storage's elements of the FP64 populations f (exactly those the
-    solver holds: FP64 stores f, the other forms the offsets f - w)."""
+    """The storage's elements of the FP64 populations f (those the solver
+    holds: FP64 stores f, FP32 the offsets f - w, the 16-bit forms f - w
+    minus the reference)."""
     import torch
-    h = f if storage == "f64" else f - W[:, None, None]
+    h = f if storage == "f64" else f - W[:, None, None] - _ref(storage)[:, None, None]
     return torch.from_numpy(h).to(_dtype(storage))
 
 
@@ -64,7 +80,7 @@ def _state(V, nx, ny, pitch, coll, storage):
     chi = I.random_mask(nx, ny, 41, 0.1)
     us = I.random_solid_velocity(nx, ny, 42, 0.02)
     body = I.BodySpec(nx * 0.6, ny * 0.5, 9.0, omega=0.001)
-    cfg = V.make_config(nx, ny, coll, storage, 0.6, bc="channel", u_in=(0.04, 0.0))
+    cfg = V.make_config(nx, ny, coll, storage, 0.6, bc="channel", u_in=U_IN)
     cfg.stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     ref = V.Solver(cfg, [body])
     ref.set_mask(chi, us)
@@ -91,8 +107,11 @@ def _state(V, nx, ny, pitch, coll, storage):
 
 
 def _populations(dst, nx, storage):
-    h = dst[:, :, :nx].double().cpu().numpy()
-    return h if storage == "f64" else h + W[:, None, None]
+    h = dst[:, :, :nx].float().cpu().numpy()
+    if storage == "f64":
+        return dst[:, :, :nx].double().cpu().numpy()
+    # the kernel's FP32 decode: element + reference, then w + that in FP64
+    return (h + _ref(storage)[:, None, None].astype(np.float32)).astype(np.float64) + W[:, None, None]
 
 
 @pytest.mark.parametrize("storage", ["f32", "f64", "f16", "bf16"])
