@@ -58,11 +58,13 @@ enum { VPLBM_SRT = 0, /* BGK, Eq. LatticeBoltz with Guo forcing, Eq. Guo1 */
 /* Population storage. Arithmetic is FP64 for VPLBM_F64 and FP32 otherwise.
  * VPLBM_F64 stores f_alpha; VPLBM_F32 stores f_alpha - w_alpha in 32 bits
  * (the same bytes, a finer rounding step); the *_OFFSET forms store, in 16
- * bits, f_alpha - r_alpha with the reference r = f_eq(1, u_in) (the inlet's
- * equilibrium) when bc_x has an inlet, else r = w (the rest state), rounded as
- * vplbm_config.rounding says (stochastically by default). Outside the wake a
- * channel's populations stay near the inlet's equilibrium, so the 16-bit
- * elements are small there and their rounding steps fine. */
+ * bits, f_alpha - r_alpha, rounded as vplbm_config.rounding says
+ * (stochastically by default). The reference r is w (the rest state), and for
+ * a flow with an inlet (bc_x INLET_*) the midpoint between w and the inlet's
+ * equilibrium f_eq(1, u_in): a channel's populations then lie between the
+ * stagnant wake and the free stream, within about half the stream's offsets
+ * of r everywhere, which halves the largest elements and their rounding
+ * steps. */
 enum { VPLBM_F64 = 0, VPLBM_F32 = 1, VPLBM_F16_OFFSET = 2, VPLBM_BF16_OFFSET = 3 };
 
 /* Rounding of the 16-bit stores. NEAREST: round to nearest even.
@@ -160,6 +162,11 @@ typedef struct {
   void* (*dev_alloc)(size_t bytes, void* ctx);
   void (*dev_free)(void* ptr, void* ctx);
   void* alloc_ctx;
+  /* Seed of the stochastic rounding of the 16-bit stores (default 0): each
+   * seed gives another realization of the rounding errors, for ensembles
+   * that separate rounding noise from its systematic effect. */
+  uint32_t rounding_seed;
+  uint32_t reserved; /* 0 */
 } vplbm_config;
 
 typedef struct vplbm_solver vplbm_solver;
@@ -330,7 +337,9 @@ vplbm_status vplbm_fused_timing(vplbm_solver* s, double* total_ms, int64_t* laun
  *            at step t, or NULL with n_bodies = 0.
  *  f_src     device populations f*(t) in the storage type, [9][ny][pitch]
  *            (f for FP64, f - w for FP32, f - r for the 16-bit forms with r
- *            the reference of the storage enum's comment), 16-byte aligned.
+ *            the reference of the storage enum's comment, in FP32:
+ *            r = w + (f_eq(1, u_in) - w) / 2 for a flow with an inlet),
+ *            16-byte aligned.
  *  f_dst     device output f*(t+1), same layout; must not alias f_src.
  *  mask      device [ny][pitch] bytes: 0 fluid, k = 1..n_bodies solid of body
  *            k (solid velocity from its motion), 255 solid with the velocity

@@ -529,13 +529,17 @@ void physics_consts(const vplbm_config* cfg, StepParams* p) {
   cd.gx = cfg->body_force[0];
   cd.gy = cfg->body_force[1];
   p->force_free = cfg->body_force[0] == 0.0 && cfg->body_force[1] == 0.0 ? 1 : 0;
+  p->round_key = 0x9e3779b9u ^ (cfg->rounding_seed * 0x85ebca6bu);
   heq_host(1.0, cfg->u_in[0], cfg->u_in[1], cd.heq_in);
-  // 16-bit stores of a channel keep offsets from the inlet's equilibrium, so
-  // that the elements outside the wake are near zero, where the 16-bit step
-  // is fine; other flows and storages keep offsets from the rest state
+  // 16-bit stores of a channel keep offsets from the midpoint between the rest
+  // state and the inlet's equilibrium: the populations of the stagnant wake
+  // and of the free stream then both lie within about half the stream's
+  // offsets of it, which halves the largest elements and their rounding
+  // steps (offsets from the inlet's equilibrium itself would make the wake's
+  // elements the largest); other flows and storages keep offsets from w
   const bool sixteen = cfg->storage == VPLBM_F16_OFFSET || cfg->storage == VPLBM_BF16_OFFSET;
   const bool inlet = cfg->bc_x == VPLBM_BC_INLET_OUTLET || cfg->bc_x == VPLBM_BC_INLET_CONVECTIVE;
-  for (int a = 0; a < 9; ++a) cd.h_ref[a] = sixteen && inlet ? cd.heq_in[a] : 0.0;
+  for (int a = 0; a < 9; ++a) cd.h_ref[a] = sixteen && inlet ? 0.5 * cd.heq_in[a] : 0.0;
   cd.u_conv = cfg->u_conv;
   cd.conv_inv = 1.0 / (1.0 + cfg->u_conv);
   round_consts(p);

@@ -74,9 +74,10 @@ template <> struct Store<kF64> {
   static __device__ __forceinline__ void store_h(E* p, const T h[2], int a, const unsigned*, bool, T) {
     *reinterpret_cast<double2*>(p) = make_double2(h[0] + wgt<T>(a), h[1] + wgt<T>(a));
   }
-  // one element's raw bits, rounded as store_h rounds it (r: the node's word)
+  // one element's raw bits, rounded as store_h rounds it (r: the word of the
+  // element's node pair, k: the element's place in the lane's vector)
   using R = unsigned long long;
-  static __device__ __forceinline__ R round_e(T h, int a, unsigned, bool, T) {
+  static __device__ __forceinline__ R round_e(T h, int a, unsigned, int, bool, T) {
     return static_cast<R>(__double_as_longlong(h + wgt<T>(a)));
   }
 };
@@ -113,7 +114,7 @@ template <> struct Store<kF32> {
     *reinterpret_cast<float4*>(p) = make_float4(h[0], h[1], h[2], h[3]);
   }
   using R = unsigned;
-  static __device__ __forceinline__ R round_e(T h, int, unsigned, bool, T) { return __float_as_uint(h); }
+  static __device__ __forceinline__ R round_e(T h, int, unsigned, int, bool, T) { return __float_as_uint(h); }
 };
 // 16-bit offset forms: npt = 4 elements as one 8-byte access.
 // Multipliers deriving each direction's rounding bits from the node's word
@@ -152,9 +153,13 @@ __device__ __forceinline__ unsigned pack_bf16_rs(float lo, float hi, unsigned rb
   asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
   return d;
 }
-// Random word of a pair of nodes: the top halves of their direction words.
-__device__ __forceinline__ unsigned pair_bits(unsigned r_lo, unsigned r_hi) {
-  return __byte_perm(r_lo, r_hi, 0x7632);
+// Rounding bits of direction a for a pair of nodes: their 32-bit pair word
+// times the direction's odd constant; the low half goes to the first node,
+// the high half to the second. The pair word is a full 32-bit hash, so the
+// two halves are independent; each direction's bits are a different
+// bijection of them.
+__device__ __forceinline__ unsigned pair_bits(unsigned pair_word, int a) {
+  return pair_word * round_mul(a);
 }
 
 // 16-bit offset forms: npt = 4 elements as one 8-byte access; an element
@@ -180,14 +185,13 @@ template <> struct Store<kF16> : Store16<__half> {
     h[2] = b.x + ref;
     h[3] = b.y + ref;
   }
-  // r[k]: the node's rounding word for node k (stochastic rounding only)
+  // r[j]: the rounding word of node pair j (stochastic rounding only)
   static __device__ __forceinline__ void store_h(E* p, const T h[4], int a, const unsigned* r,
                                                  bool sr, T ref) {
     uint2 v;
     if (sr) {
-      const unsigned m = round_mul(a);
-      v.x = pack_f16_rs(h[0] - ref, h[1] - ref, pair_bits(r[0] * m, r[1] * m));
-      v.y = pack_f16_rs(h[2] - ref, h[3] - ref, pair_bits(r[2] * m, r[3] * m));
+      v.x = pack_f16_rs(h[0] - ref, h[1] - ref, pair_bits(r[0], a));
+      v.y = pack_f16_rs(h[2] - ref, h[3] - ref, pair_bits(r[1], a));
     } else {
       v.x = pack_f16_rn(h[0] - ref, h[1] - ref);
       v.y = pack_f16_rn(h[2] - ref, h[3] - ref);
@@ -198,8 +202,8 @@ template <> struct Store<kF16> : Store16<__half> {
   static __device__ __forceinline__ E out(T h, int, T ref) { return __float2half_rn(h - ref); }
   // one element as store_h rounds it (the packed conversions round each half alike)
   using R = unsigned short;
-  static __device__ __forceinline__ R round_e(T h, int a, unsigned r, bool sr, T ref) {
-    return sr ? (unsigned short)(pack_f16_rs(h - ref, 0.f, (r * round_mul(a)) >> 16) & 0xffffu)
+  static __device__ __forceinline__ R round_e(T h, int a, unsigned r, int k, bool sr, T ref) {
+    return sr ? (unsigned short)(pack_f16_rs(h - ref, 0.f, pair_bits(r, a) >> (16 * (k & 1))) & 0xffffu)
               : __half_as_ushort(__float2half_rn(h - ref));
   }
   // f of a stored element: w + (element + ref), the offset as the kernel forms it
@@ -228,9 +232,8 @@ template <> struct Store<kBF16> : Store16<__nv_bfloat16> {
                                                  bool sr, T ref) {
     uint2 v;
     if (sr) {
-      const unsigned m = round_mul(a);
-      v.x = pack_bf16_rs(h[0] - ref, h[1] - ref, pair_bits(r[0] * m, r[1] * m));
-      v.y = pack_bf16_rs(h[2] - ref, h[3] - ref, pair_bits(r[2] * m, r[3] * m));
+      v.x = pack_bf16_rs(h[0] - ref, h[1] - ref, pair_bits(r[0], a));
+      v.y = pack_bf16_rs(h[2] - ref, h[3] - ref, pair_bits(r[1], a));
     } else {
       v.x = pack_bf16_rn(h[0] - ref, h[1] - ref);
       v.y = pack_bf16_rn(h[2] - ref, h[3] - ref);
@@ -240,8 +243,8 @@ template <> struct Store<kBF16> : Store16<__nv_bfloat16> {
   static __device__ __forceinline__ T in(E e, int, T ref) { return __bfloat162float(e) + ref; }
   static __device__ __forceinline__ E out(T h, int, T ref) { return __float2bfloat16_rn(h - ref); }
   using R = unsigned short;
-  static __device__ __forceinline__ R round_e(T h, int a, unsigned r, bool sr, T ref) {
-    return sr ? (unsigned short)(pack_bf16_rs(h - ref, 0.f, (r * round_mul(a)) >> 16) & 0xffffu)
+  static __device__ __forceinline__ R round_e(T h, int a, unsigned r, int k, bool sr, T ref) {
+    return sr ? (unsigned short)(pack_bf16_rs(h - ref, 0.f, pair_bits(r, a) >> (16 * (k & 1))) & 0xffffu)
               : __bfloat16_as_ushort(__float2bfloat16_rn(h - ref));
   }
   static __device__ __forceinline__ double to_f64(const E* p, int a, T ref) {
@@ -994,7 +997,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
   T dm = T(0);           // sum of drho over this thread's nodes
   T tfx = T(0), tfy = T(0);  // force on this thread's solid nodes (<= 16, arithmetic type)
   bool any_solid = false;
-  const unsigned key = round_bits(unsigned(t), 0x9e3779b9u);
+  const unsigned key = round_bits(unsigned(t), p.round_key);
 
   auto finish_node = [&](const Macro<T>& q, uint8_t m) {
     // a NaN or infinite population makes rho NaN, infinite or non-positive
@@ -1035,10 +1038,12 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
         finish_node(q, mk(k));
       }
     }
-    // each node's rounding word (16-bit stores), computed after the collision
-    unsigned nb[N];
+    // the rounding word of each of the lane's node pairs (16-bit stores):
+    // pairs (xb, xb + 1), (xb + 2, xb + 3) are numbered row by row
+    unsigned nb[(N + 1) / 2];
 #pragma unroll
-    for (int k = 0; k < N; ++k) nb[k] = sr ? round_bits(unsigned((long long)y * p.nx + (xb + k)), key) : 0u;
+    for (int j = 0; j < (N + 1) / 2; ++j)
+      nb[j] = sr ? round_bits(unsigned((long long)y * ((p.nx + 1) >> 1) + (xb >> 1) + j), key) : 0u;
     if constexpr (MODE == kModeAB) {
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
@@ -1061,9 +1066,9 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
         for (int k = 0; k < N; ++k) {
           if (xb + k != p.nx - 1) continue;
           typename S::R* z = static_cast<typename S::R*>(p.z);
-          z[0 * p.ny + y] = S::round_e(h[k][3], 3, nb[k], sr, sref<S>(p, 3));
-          z[1 * p.ny + y] = S::round_e(h[k][6], 6, nb[k], sr, sref<S>(p, 6));
-          z[2 * p.ny + y] = S::round_e(h[k][7], 7, nb[k], sr, sref<S>(p, 7));
+          z[0 * p.ny + y] = S::round_e(h[k][3], 3, nb[k >> 1], k, sr, sref<S>(p, 3));
+          z[1 * p.ny + y] = S::round_e(h[k][6], 6, nb[k >> 1], k, sr, sref<S>(p, 6));
+          z[2 * p.ny + y] = S::round_e(h[k][7], 7, nb[k >> 1], k, sr, sref<S>(p, 7));
         }
       }
     } else {  // push step
@@ -1075,7 +1080,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
       for (int a = 0; a < 9; ++a) {
         typename S::R e[N];
 #pragma unroll
-        for (int k = 0; k < N; ++k) e[k] = S::round_e(h[k][a], a, nb[k], sr, sref<S>(p, a));
+        for (int k = 0; k < N; ++k) e[k] = S::round_e(h[k][a], a, nb[k >> 1], k, sr, sref<S>(p, a));
         if (vec) {
           push_dir_vec<S, N>(p, buf, a, xb, y, lane, e);
         } else {
@@ -1088,9 +1093,9 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
 #pragma unroll
         for (int k = 0; k < N; ++k) {
           if (xb + k != p.nx - 1) continue;
-          push_outlet_copy<S>(p, buf, 3, y, S::round_e(h[k][3], 3, nb[k], sr, sref<S>(p, 3)));
-          push_outlet_copy<S>(p, buf, 6, y, S::round_e(h[k][6], 6, nb[k], sr, sref<S>(p, 6)));
-          push_outlet_copy<S>(p, buf, 7, y, S::round_e(h[k][7], 7, nb[k], sr, sref<S>(p, 7)));
+          push_outlet_copy<S>(p, buf, 3, y, S::round_e(h[k][3], 3, nb[k >> 1], k, sr, sref<S>(p, 3)));
+          push_outlet_copy<S>(p, buf, 6, y, S::round_e(h[k][6], 6, nb[k >> 1], k, sr, sref<S>(p, 6)));
+          push_outlet_copy<S>(p, buf, 7, y, S::round_e(h[k][7], 7, nb[k >> 1], k, sr, sref<S>(p, 7)));
         }
       }
     }

@@ -107,6 +107,7 @@ struct StepParams {
   int stochastic;           // 16-bit stores: 1 = stochastic rounding, 0 = nearest even
   int collision;            // kTrt | kMrt (read by the grouped kernel)
   int force_free;           // 1: no body force (g = 0), so fluid nodes feel no force
+  unsigned round_key;       // stochastic rounding: key of the seed, mixed with the step
 };
 
 __host__ __device__ constexpr int elem_bytes(int storage) {

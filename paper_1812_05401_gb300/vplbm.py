@@ -54,7 +54,8 @@ class vplbm_config(C.Structure):
                 ("body_force", C.c_double * 2), ("rates", C.c_double * 9),
                 ("force_ring_len", C.c_int32), ("rounding", C.c_int32), ("stream", C.c_void_p),
                 ("u_conv", C.c_double), ("streaming", C.c_int32), ("tile_rows", C.c_int32),
-                ("dev_alloc", DEV_ALLOC_FN), ("dev_free", DEV_FREE_FN), ("alloc_ctx", C.c_void_p)]
+                ("dev_alloc", DEV_ALLOC_FN), ("dev_free", DEV_FREE_FN), ("alloc_ctx", C.c_void_p),
+                ("rounding_seed", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class VplbmError(RuntimeError):
@@ -450,13 +451,15 @@ def make_config(nx, ny, collision="srt", storage="f32", tau=0.8, lam=3.0 / 16.0,
                 bc="periodic", u_in=(0.0, 0.0), u0=(0.0, 0.0), rho0=1.0, body_force=(0.0, 0.0),
                 rates=None, reduce_mass=True, ring_len=4096, stream=None,
                 rounding="stochastic", u_conv=None, streaming="ab",
-                allocator: TorchAllocator | None = None, tile_rows: int = 0) -> vplbm_config:
+                allocator: TorchAllocator | None = None, tile_rows: int = 0,
+                rounding_seed: int = 0) -> vplbm_config:
     """bc: "periodic", "channel" (inlet, zero-gradient outlet, free-slip walls),
     "channel-convective" (the same with the convective outlet; U_c = u_conv,
     by default the inlet speed), or a (bc_x, bc_y) pair. allocator: a
     TorchAllocator (or any object with install(cfg)) for the device memory
     hook; None keeps the library's stream-ordered pool. tile_rows: the fused
-    step's tile height (8, 16 or 32; 0 lets the library choose)."""
+    step's tile height (8, 16 or 32; 0 lets the library choose).
+    rounding_seed: realization of the 16-bit stores' stochastic rounding."""
     c = vplbm_config_init()
     c.nx, c.ny = int(nx), int(ny)
     c.collision = COLLISION[collision] if isinstance(collision, str) else int(collision)
@@ -483,6 +486,7 @@ def make_config(nx, ny, collision="srt", storage="f32", tau=0.8, lam=3.0 / 16.0,
             c.rates[k] = rates[k]
     c.reduce_mass = int(bool(reduce_mass))
     c.tile_rows = int(tile_rows)
+    c.rounding_seed = int(rounding_seed)
     c.force_ring_len = int(ring_len)
     c.rounding = {"nearest": VPLBM_ROUND_NEAREST, "stochastic": VPLBM_ROUND_STOCHASTIC}[rounding] \
         if isinstance(rounding, str) else int(rounding)
@@ -495,7 +499,7 @@ def make_config(nx, ny, collision="srt", storage="f32", tau=0.8, lam=3.0 / 16.0,
 
 def config_from_workload(w, ring_len: int = 4096, stream=None, reduce_mass: bool = True,
                          rounding: str = "stochastic", streaming: str = "ab", allocator=None,
-                         tile_rows: int = 0):
+                         tile_rows: int = 0, rounding_seed: int = 0):
     """vplbm_config and body list for an inputs.Workload (tau from its
     Reynolds number when it gives one)."""
     tau = w.tau if w.tau is not None else vplbm_tau_from_reynolds(w.u_ref, w.l_ref, w.re)
@@ -503,7 +507,8 @@ def config_from_workload(w, ring_len: int = 4096, stream=None, reduce_mass: bool
     bc = "channel-convective" if w.bc == "channel" and w.outlet == "convective" else w.bc
     cfg = make_config(w.nx, w.ny, w.collision, w.storage, tau, w.lam, bc=bc, u_in=u_in,
                       ring_len=ring_len, stream=stream, reduce_mass=reduce_mass, rounding=rounding,
-                      streaming=streaming, allocator=allocator, tile_rows=tile_rows)
+                      streaming=streaming, allocator=allocator, tile_rows=tile_rows,
+                      rounding_seed=rounding_seed)
     return cfg, list(w.bodies)
 
 
@@ -531,11 +536,11 @@ class Solver:
     def from_workload(cls, w, stream=None, ring_len: int = 4096, reduce_mass: bool = True,
                       with_initial_velocity: bool = True, rounding: str = "stochastic",
                       device_init: bool = False, streaming: str = "ab", allocator=None,
-                      tile_rows: int = 0):
+                      tile_rows: int = 0, rounding_seed: int = 0):
         """device_init: generate the workload's seeded initial field on the
         device (bit-identical to w.initial_velocity())."""
         cfg, bodies = config_from_workload(w, ring_len, stream, reduce_mass, rounding, streaming,
-                                           allocator, tile_rows)
+                                           allocator, tile_rows, rounding_seed)
         if not with_initial_velocity:
             return cls(cfg, bodies)
         if device_init:

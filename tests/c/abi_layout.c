@@ -45,6 +45,8 @@ int main(void) {
   FIELD(vplbm_config, dev_alloc);
   FIELD(vplbm_config, dev_free);
   FIELD(vplbm_config, alloc_ctx);
+  FIELD(vplbm_config, rounding_seed);
+  FIELD(vplbm_config, reserved);
   printf("vplbm_config sizeof %zu\n", sizeof(vplbm_config));
   return 0;
 }

@@ -13,16 +13,26 @@ paper's momentum exchange over the mask's fluid-to-solid links; statistics over 
 force record shows the shedding saturated by step 200,000), St from the lift
 spectrum.
 
-Measured (FP32, 500,000-step run, window 250k-500k): C_Dave = 1.544 (+6.5%),
-C_Lrms = 0.98 (+17%), St = 0.2345 (+6.6%). Drag and Strouhal number are both
-a few percent above the paper's, as the 10% blockage of the free-slip walls
-at +-5D would produce; the paper's values sit on the unconfined experiments.
-The outlet is a candidate too. The two force measures differ by the rate of
-change of the solid region's momentum (a one-step balance the oracle pins),
-whose mean vanishes in a periodic state: their C_Dave agree closely.
-Bounds: 8% on C_Dave and St, 20% on C_Lrms (the RMS lift is the most
-sensitive to the outlet and force definitions), for both measures; 1% between
-the two measures' C_Dave and St.
+Reproduced (FP32, 400,000 steps, window 200k-400k): convective outlet
+C_Dave = 1.553, C_Lrms = 0.935, St = 0.2356; zero-gradient outlet 1.541,
+0.970, 0.2342. Against the paper: +7.1%, +11%, +7.1% (convective). Controlled
+runs, one change at a time (same steps and window), bound the cause:
+  another perturbation seed        C_Dave -0.2%, C_Lrms -0.8%, St  0.0%
+  channel height 20D (5% blockage) C_Dave -0.7%, C_Lrms -1.0%, St -0.5%
+  half resolution (D = 100)        C_Dave +0.7%, C_Lrms  0.0%, St -0.2%
+  MRT, Lambda = 3/16               C_Dave -0.4%, C_Lrms -0.5%, St +0.2%
+  centre on a node row             C_Dave +0.1%, C_Lrms -0.7%, St -0.1%
+  eta = 1e-5                       C_Dave  0.0%, C_Lrms  0.0%, St  0.0%
+  window 400k-800k                 C_Dave +0.15%, C_Lrms -0.3%, St +0.3%
+  FP64 vs FP32 over 100k steps     C_Dave 2.6e-4, C_Lrms 2e-4, St 1.3e-4
+None moves the statistics by more than 1%, so neither blockage, resolution,
+the collision operator, the mask position, eta, the window nor precision
+explains the 7-11% gap; the paper's own numbers come from the same 30D x 10D
+domain. Untested candidates: the inlet (an equilibrium ghost at rho = 1 here)
+and the symmetry plane (half-way here). The gap is stated as open.
+Bounds: the reproduced values within 1% (C_Dave, St) and 3% (C_Lrms), which
+covers the seed-to-seed spread; both force measures; 1% between the two
+measures' C_Dave and St.
 """
 import json
 import os
@@ -35,6 +45,10 @@ PAPER = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
                                     "paper_constants.json")))["cylinder_re500"]
 
 pytestmark = pytest.mark.gpu
+
+
+REPRODUCED = {"convective": {"C_D_ave": 1.553, "C_L_rms": 0.935, "St": 0.2356},
+              "zero-gradient": {"C_D_ave": 1.541, "C_L_rms": 0.970, "St": 0.2342}}
 
 
 @pytest.mark.parametrize("outlet", ["convective", "zero-gradient"])
@@ -61,9 +75,11 @@ def test_table2_cylinder_re500(outlet):
     me = diag.wake_statistics(mx, my, U, D, discard=0.5)
     print(f"Table 2 reproduction ({outlet} outlet), penalization integral:", st)
     print(f"Table 2 reproduction ({outlet} outlet), momentum exchange:", me)
+    rep = REPRODUCED[outlet]
+    print("against the paper:", {k: st[k] / PAPER[k] - 1.0 for k in ("C_D_ave", "C_L_rms", "St")})
     for r in (st, me):
-        assert r["C_D_ave"] == pytest.approx(PAPER["C_D_ave"], rel=0.08)
-        assert r["St"] == pytest.approx(PAPER["St"], rel=0.08)
-        assert r["C_L_rms"] == pytest.approx(PAPER["C_L_rms"], rel=0.20)
+        assert r["C_D_ave"] == pytest.approx(rep["C_D_ave"], rel=0.01)
+        assert r["St"] == pytest.approx(rep["St"], rel=0.01)
+        assert r["C_L_rms"] == pytest.approx(rep["C_L_rms"], rel=0.03)
     assert me["C_D_ave"] == pytest.approx(st["C_D_ave"], rel=0.01)
     assert me["St"] == pytest.approx(st["St"], rel=0.01)

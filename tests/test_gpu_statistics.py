@@ -18,10 +18,12 @@ time at which shedding starts.
 Bars (relative, against the oracle):
   FP64 storage                       1e-8 on C_Dave, C_Lrms and St
   FP32 storage                       1e-3 on C_Dave and St
-  FP16 offsets, stochastic rounding  1e-3 on C_Dave and St
-  BF16 offsets, stochastic rounding  misses 1e-3 (8 significant bits): its
-      error is printed and held only to 1e-2, so that a change that makes it
-      worse is seen; the test's name says it misses the bar.
+  FP16 offsets, stochastic rounding  1e-3 on C_Dave and St, for each of four
+      realizations of the rounding (rounding_seed 0..3) and their mean
+  BF16 offsets, stochastic rounding  misses 1e-3 (8 significant bits): the
+      errors of the four realizations are printed and held only to 1e-2, so
+      that a change that makes them worse is seen; the test's name says it
+      misses the bar.
 With round-to-nearest-even the 16-bit forms do not reach 1e-3 on this flow:
 rounding f - w (~0.02) to 11 significant bits is about 20 times the viscous
 change of a population per step, and a deterministic rounding acts as a small
@@ -73,21 +75,22 @@ def _fp64():
     return _cache["f64"]
 
 
-def _run(storage, rounding="stochastic"):
-    if (storage, rounding) in _cache:
-        return _cache[(storage, rounding)]
+def _run(storage, rounding="stochastic", seed=0):
+    if (storage, rounding, seed) in _cache:
+        return _cache[(storage, rounding, seed)]
     _fp64()
     V, diag = _lib()
     w = I.c2_cylinder_re100()
     w.storage = storage
     with V.Solver.from_workload(w, ring_len=MEASURE, reduce_mass=False,
-                                with_initial_velocity=False, rounding=rounding) as s:
+                                with_initial_velocity=False, rounding=rounding,
+                                rounding_seed=seed) as s:
         s.set_populations(_cache["developed"])
         s.step(MEASURE)
         s.synchronize()
         fx, fy, _ = s.forces()
     st = diag.wake_statistics(fx, fy, w.u_ref, w.l_ref, discard=0.0)
-    _cache[(storage, rounding)] = st
+    _cache[(storage, rounding, seed)] = st
     return st
 
 
@@ -112,20 +115,41 @@ def test_fp64_path_reproduces_oracle_statistics():
         assert _rel(s[k], GOLDEN[k]) < 1e-8, k
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
-def test_storage_statistics_within_1e3_of_oracle(storage):
-    s = _run(storage)
+SEEDS = (0, 1, 2, 3)
+
+
+def _errors(storage, seeds):
+    """Signed relative errors against the oracle, per realization and of the
+    realizations' mean statistics."""
+    runs = [_run(storage, seed=sd) for sd in seeds]
+    out = {"runs": [{k: (r[k] - GOLDEN[k]) / GOLDEN[k] for k in ("C_D_ave", "C_L_rms", "St")}
+                    for r in runs]}
+    out["mean"] = {k: (np.mean([r[k] for r in runs]) - GOLDEN[k]) / GOLDEN[k]
+                   for k in ("C_D_ave", "C_L_rms", "St")}
+    return out
+
+
+def test_fp32_statistics_within_1e3_of_oracle():
+    s = _run("f32")
     err = {k: _rel(s[k], GOLDEN[k]) for k in ("C_D_ave", "C_L_rms", "St")}
-    print(storage, "relative error against the oracle", err)
+    print("f32 relative error against the oracle", err)
     assert err["C_D_ave"] < 1e-3
     assert err["St"] < 1e-3
 
 
+def test_fp16_statistics_within_1e3_of_oracle():
+    e = _errors("f16", SEEDS)
+    print("f16 relative errors against the oracle, per rounding seed", e["runs"], "mean", e["mean"])
+    for r in e["runs"] + [e["mean"]]:
+        assert abs(r["C_D_ave"]) < 1e-3 and abs(r["St"]) < 1e-3
+
+
 def test_bf16_stochastic_misses_1e3_bar_reported():
-    s = _run("bf16")
-    err = {k: _rel(s[k], GOLDEN[k]) for k in ("C_D_ave", "C_L_rms", "St")}
-    print("bf16 relative error against the oracle (bar 1e-3, not met)", err)
-    assert err["C_D_ave"] < 1e-2 and err["St"] < 1e-2
+    e = _errors("bf16", SEEDS)
+    print("bf16 relative errors against the oracle (bar 1e-3, not met), per rounding seed",
+          e["runs"], "mean", e["mean"])
+    for r in e["runs"]:
+        assert abs(r["C_D_ave"]) < 1e-2 and abs(r["St"]) < 1e-2
 
 
 @pytest.mark.parametrize("storage,tol_cd,tol_st", [("f32", 1e-3, 1e-3), ("f16", 0.06, 0.05),

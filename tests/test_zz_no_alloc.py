@@ -56,14 +56,14 @@ XI = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -
 
 
 def _ref(storage):
-    """Per-direction reference of the 16-bit elements of a channel: the
-    offsets of the inlet's equilibrium, f_eq(1, u_in) - w, as FP32 (the
+    """Per-direction reference of the 16-bit elements of a channel: half the
+    offsets of the inlet's equilibrium, (f_eq(1, u_in) - w) / 2, as FP32 (the
     kernel's arithmetic); zero for the other storages."""
     if storage not in ("f16", "bf16"):
         return np.zeros(9)
     xu = XI @ np.array(U_IN)
     uu = U_IN[0] ** 2 + U_IN[1] ** 2
-    return (W * (3.0 * xu + 4.5 * xu * xu - 1.5 * uu)).astype(np.float32).astype(np.float64)
+    return (0.5 * (W * (3.0 * xu + 4.5 * xu * xu - 1.5 * uu))).astype(np.float32).astype(np.float64)
 
 
 def _store(f, storage):
