@@ -25,10 +25,12 @@ Bars (relative, against the oracle):
       that a change that makes them worse is seen; the test's name says it
       misses the bar.
 With round-to-nearest-even the 16-bit forms do not reach 1e-3 on this flow:
-rounding f - w (~0.02) to 11 significant bits is about 20 times the viscous
-change of a population per step, and a deterministic rounding acts as a small
-systematic forcing. Those tests document the effect with the FP64 GPU run as
-the reference and bounds that are the measured errors with margin.
+the rounding step of an element (~0.01) at 11 significant bits is about ten
+times the viscous change of a population per step, and a deterministic
+rounding acts as a small systematic forcing. Those tests document the effect
+with the FP64 GPU run as the reference and bounds that are the measured
+errors with margin (FP16: C_Dave +0.9%, St +0.6%; BF16: C_Dave 0.0%, St
+-5.8%, and the RMS lift halved).
 """
 import json
 import os
@@ -152,8 +154,8 @@ def test_bf16_stochastic_misses_1e3_bar_reported():
         assert abs(r["C_D_ave"]) < 1e-2 and abs(r["St"]) < 1e-2
 
 
-@pytest.mark.parametrize("storage,tol_cd,tol_st", [("f32", 1e-3, 1e-3), ("f16", 0.06, 0.05),
-                                                   ("bf16", 0.12, 0.03)])
+@pytest.mark.parametrize("storage,tol_cd,tol_st", [("f32", 1e-3, 1e-3), ("f16", 0.02, 0.015),
+                                                   ("bf16", 0.02, 0.08)])
 def test_nearest_rounding_statistics(storage, tol_cd, tol_st):
     ref = _fp64()
     s = _run(storage, "nearest")
