@@ -35,6 +35,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+CPU_WARMUP, CPU_STEPS = 5, 20  # the cpu_baseline leg's oracle sample (full grid)
 ALGO_BYTES = {"f32": 73.0, "f16": 37.0, "bf16": 37.0, "f64": 145.0}  # per node update, u8 mask
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_SOURCES = ["paper_1812_05401_gb300/csrc/vplbm_device.cuh", "paper_1812_05401_gb300/csrc/vplbm_params.h",
@@ -200,30 +201,25 @@ def make_workload(name: str, storage: str):
 def oracle_rates(budget_s: float = 8.0):
     """The FP64 oracle's rate on the host cores for each configuration at its
     full grid size (C1 Couette, C2 and C3 cylinders, C5 moving cylinder), with
-    one thread and with every core: a timed sample of up to budget_s seconds
-    per measurement (after one untimed step). Prints one JSON line."""
+    one thread and with every core: after one untimed step (which also sizes
+    the sample), the steps that fit in about budget_s seconds, timed as one
+    call (as the cpu_baseline leg and the reference arm time it). Prints one
+    JSON line."""
     import oracle as O
     from paper_1812_05401_gb300 import inputs as I
     out = {"kind": "oracle", "nproc": os.cpu_count(), "budget_s_per_rate": budget_s, "configs": {}}
     for name, w in (("C1", I.c1_circular_couette()), ("C2", I.c2_cylinder_re100()),
                     ("C3", I.c3_cylinder_re1000("f32")), ("C5", I.c5_moving_cylinder("f32"))):
-        tau = O.tau_from_reynolds(w.u_ref, w.l_ref, w.re) if w.re else w.tau
-        chan = w.bc == "channel"
-        cfg = O.Config(nx=w.nx, ny=w.ny, collision=O.MRT if w.collision == "mrt" else O.SRT,
-                       tau=tau, lam=w.lam, bc_x=O.BC_INLET_OUTLET if chan else O.BC_PERIODIC,
-                       bc_y=O.BC_FREE_SLIP if chan else O.BC_PERIODIC,
-                       u_in=(w.u_ref, 0.0) if chan else (0.0, 0.0),
-                       bodies=[O.Body(b.cx, b.cy, b.radius, b.amp_x, b.amp_y, b.period, b.omega,
-                                      b.outside) for b in w.bodies])
+        cfg = oracle_config(w)
         f = O.init_equilibrium(cfg, 1.0, None)
         rates = {}
         for threads in (1, 0):
             O.set_num_threads(threads)
+            t0 = time.perf_counter()
             O.run(cfg, f, 1)
-            steps, t0 = 0, time.perf_counter()
-            while time.perf_counter() - t0 < budget_s:
-                O.run(cfg, f, 1, t0=steps + 1)
-                steps += 1
+            steps = max(2, int(budget_s / max(time.perf_counter() - t0, 1e-6)))
+            t0 = time.perf_counter()
+            O.run(cfg, f, steps, t0=1)
             dt = time.perf_counter() - t0
             rates["1_thread" if threads == 1 else f"{O.num_threads()}_threads"] = {
                 "mlups": round(w.nx * w.ny * steps / dt / 1e6, 3), "steps": steps,
@@ -247,27 +243,19 @@ def oracle_config(w):
                                    b.outside) for b in w.bodies])
 
 
-def oracle_full(w, warmup: int, steps: int = 0, budget_s: float = 0.0):
+def oracle_full(w, warmup: int, steps: int):
     """Times the FP64 oracle on the workload's full grid, on every host core:
-    `warmup` untimed steps, then `steps` timed steps (or, with steps = 0, as
-    many as fit in budget_s seconds). Returns (MLUPS, steps, seconds,
-    threads)."""
+    `warmup` untimed steps, then `steps` timed steps in one call. Returns
+    (MLUPS, steps, seconds, threads)."""
     import oracle as O
     cfg = oracle_config(w)
     f = O.init_equilibrium(cfg, 1.0, w.initial_velocity())
     if warmup:
         O.run(cfg, f, warmup)
     t0 = time.perf_counter()
-    if steps:
-        O.run(cfg, f, steps, t0=warmup)
-        n = steps
-    else:
-        n = 0
-        while n == 0 or time.perf_counter() - t0 < budget_s:
-            O.run(cfg, f, 1, t0=warmup + n)
-            n += 1
+    O.run(cfg, f, steps, t0=warmup)
     dt = time.perf_counter() - t0
-    return w.nx * w.ny * n / dt / 1e6, n, dt, O.num_threads()
+    return w.nx * w.ny * steps / dt / 1e6, steps, dt, O.num_threads()
 
 
 def device_l2_bytes() -> int:
@@ -494,11 +482,13 @@ def run_gpu(args):
     }
     result.update(extra)
     if rank == 0 and not args.no_cpu_baseline:
-        mlups, n, dt, cores = oracle_full(w, warmup=1, budget_s=args.cpu_budget)
+        # the reference arm's sample at the driver's --steps 20 --warmup 5
+        mlups, n, dt, cores = oracle_full(w, warmup=CPU_WARMUP, steps=CPU_STEPS)
         result["cpu_baseline"] = {
             "value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": f"FP64 oracle on the full {w.nx}x{w.ny} grid of this workload, {n} timed "
-                      f"steps after 1, {dt:.1f} s, {cores} threads of {os.cpu_count()} processors"}
+                      f"steps after {CPU_WARMUP}, {dt:.1f} s, {cores} threads of {os.cpu_count()} "
+                      f"processors"}
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
@@ -727,8 +717,6 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", dest="precision", action="store_false",
                     help="skip the storage forms' wake statistics against the oracle's")
-    ap.add_argument("--cpu-budget", type=float, default=12.0,
-                    help="seconds of timed oracle steps in the cpu_baseline leg")
     ap.add_argument("--serving", action="store_true", help="run only the serving mix")
     ap.add_argument("--oracle-rates", action="store_true",
                     help="time the FP64 oracle (CPU baseline) on every configuration, 1 thread and all cores")
