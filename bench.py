@@ -631,12 +631,14 @@ def run_grouped(args):
     """Grouped-launch throughput by grid size (the serving kernel): for each
     side s, a batch of k cylinder channels of 4s x s nodes (k s.t. the batch
     holds ~16M nodes; diameter 40 s / 256, Re 200, FP32, SRT and MRT
-    alternating) advanced by vplbm_group_step; CUDA events around `steps`
-    grouped steps after 20 untimed ones. Prints one JSON line."""
+    alternating, the server's tile height) advanced by vplbm_group_step; CUDA
+    events around `steps` grouped steps after 20 untimed ones. Prints one JSON
+    line."""
     import torch
 
     from paper_1812_05401_gb300 import inputs as I
     from paper_1812_05401_gb300 import vplbm as V
+    from paper_1812_05401_gb300.serve import SERVE_TILE_ROWS
     stream = torch.cuda.Stream()
     rows = []
     for side in args.grouped:
@@ -648,7 +650,8 @@ def run_grouped(args):
                 w = I.cylinder_channel(nx, ny, max(4.0, round(40 * side / 256)), 0.05, 200.0, 0,
                                        storage="f32", seed=i + 1)
                 w.collision = "mrt" if i % 2 else "srt"
-                solvers.append(V.Solver.from_workload(w, stream=stream, ring_len=args.steps + 32))
+                solvers.append(V.Solver.from_workload(w, stream=stream, ring_len=args.steps + 32,
+                                                      tile_rows=SERVE_TILE_ROWS))
             hs = [x.h for x in solvers]
             V.vplbm_group_step(hs, [20] * k)
             torch.cuda.synchronize()

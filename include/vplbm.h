@@ -61,10 +61,12 @@ enum { VPLBM_SRT = 0, /* BGK, Eq. LatticeBoltz with Guo forcing, Eq. Guo1 */
  * bits, f_alpha - r_alpha, rounded as vplbm_config.rounding says
  * (stochastically by default). The reference r is w (the rest state), and for
  * a flow with an inlet (bc_x INLET_*) the midpoint between w and the inlet's
- * equilibrium f_eq(1, u_in): a channel's populations then lie between the
- * stagnant wake and the free stream, within about half the stream's offsets
- * of r everywhere, which halves the largest elements and their rounding
- * steps. */
+ * equilibrium f_eq(1, u_in), taking the part of f_eq(1, u_in) - w that is
+ * even in xi_y (all of it for an inlet along x; a population and its mirror
+ * image at a free-slip wall then share one reference): a channel's
+ * populations lie between the stagnant wake and the free stream, within
+ * about half the stream's offsets of r everywhere, which halves the largest
+ * elements and their rounding steps. */
 enum { VPLBM_F64 = 0, VPLBM_F32 = 1, VPLBM_F16_OFFSET = 2, VPLBM_BF16_OFFSET = 3 };
 
 /* Rounding of the 16-bit stores. NEAREST: round to nearest even.

@@ -447,6 +447,28 @@ void heq_host(double rho, double ux, double uy, double out[9]) {
   }
 }
 
+// The sums through which a store's reference enters the two-rate collision
+// on stored elements (zero without a reference), from the reference as the
+// kernels hold it.
+template <class T>
+void ref_sums(Consts<T>& c, const double sp, const double sm) {
+  static const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  static const int pa[4] = {1, 2, 5, 6}, pb[4] = {3, 4, 7, 8};
+  double r[9], sum = 0.0, sx = 0.0;
+  for (int a = 0; a < 9; ++a) {
+    r[a] = double(c.h_ref[a]);
+    sum += r[a];
+    sx += ex[a] * r[a];
+  }
+  c.r_sum = T(sum);
+  c.r_x = T(sx);
+  for (int k = 0; k < 4; ++k) {
+    c.r_p[k] = T(-0.5 * sp * (r[pa[k]] + r[pb[k]]));
+    c.r_m[k] = T(-0.5 * sm * (r[pa[k]] - r[pb[k]]));
+  }
+  c.r_0 = T(-sp * r[0]);
+}
+
 // Float copies of the FP64 constants.
 void round_consts(StepParams* p) {
   Consts<double>& d = p->cd;
@@ -476,6 +498,7 @@ void round_consts(StepParams* p) {
     f.t_am[k] = float(d.t_am[k]);
     f.t_bm[k] = float(d.t_bm[k]);
   }
+  ref_sums(f, d.t_sp, 2.0 * d.t_hsm);
 }
 
 // Collision and forcing constants of a configuration (FP64, then their float
@@ -536,10 +559,16 @@ void physics_consts(const vplbm_config* cfg, StepParams* p) {
   // and of the free stream then both lie within about half the stream's
   // offsets of it, which halves the largest elements and their rounding
   // steps (offsets from the inlet's equilibrium itself would make the wake's
-  // elements the largest); other flows and storages keep offsets from w
+  // elements the largest); other flows and storages keep offsets from w.
+  // The reference takes the part of f_eq(1, u_in) - w that is even in xi_y
+  // (all of it for an inlet along x), so that a population and its mirror
+  // image at a free-slip wall share one reference.
+  static const int my[9] = {0, 1, 4, 3, 2, 8, 7, 6, 5};
   const bool sixteen = cfg->storage == VPLBM_F16_OFFSET || cfg->storage == VPLBM_BF16_OFFSET;
   const bool inlet = cfg->bc_x == VPLBM_BC_INLET_OUTLET || cfg->bc_x == VPLBM_BC_INLET_CONVECTIVE;
-  for (int a = 0; a < 9; ++a) cd.h_ref[a] = sixteen && inlet ? 0.5 * cd.heq_in[a] : 0.0;
+  for (int a = 0; a < 9; ++a)
+    cd.h_ref[a] = sixteen && inlet ? 0.25 * (cd.heq_in[a] + cd.heq_in[my[a]]) : 0.0;
+  ref_sums(cd, sp, sm);
   cd.u_conv = cfg->u_conv;
   cd.conv_inv = 1.0 / (1.0 + cfg->u_conv);
   round_consts(p);

@@ -44,10 +44,12 @@ __device__ __forceinline__ constexpr T wgt(int a) {
 }
 
 // ---------------------------------------------------------------------------
-// Storage traits: E is the element in HBM, T the arithmetic type. Every call
-// takes `ref`, the per-direction reference the 16-bit stores keep their
-// elements relative to (the other stores ignore it): a 16-bit element holds
-// h - ref, h = f - w the offset the kernel works on.
+// Storage traits: E is the element in HBM, T the arithmetic type, h = f - w
+// the offset of a population. A 16-bit element holds h - ref, ref a
+// per-direction reference (zero for the other stores, which hold h). The
+// fused step works on the elements' values e = h - ref as they are (load_h,
+// store_h, round_e, in_e: no reference), its collision taking ref through
+// constant sums; in, out, to_f64 and from_f64 convert to and from h and f.
 // ---------------------------------------------------------------------------
 template <int S> struct Store;
 template <> struct Store<kF64> {
@@ -55,29 +57,30 @@ template <> struct Store<kF64> {
   using T = double;
   static constexpr bool kSixteen = false;
   static __device__ __forceinline__ T in(E e, int a, T) { return e - wgt<T>(a); }
+  static __device__ __forceinline__ T in_e(E e, int a) { return e - wgt<T>(a); }
   static __device__ __forceinline__ E out(T h, int a, T) { return h + wgt<T>(a); }
   static __device__ __forceinline__ double to_f64(const E* p, int, T) { return *p; }
   static __device__ __forceinline__ void from_f64(E* p, double f, int, T) { *p = f; }
   // npt = 2 consecutive elements as one 16-byte access, as offsets h = f - w.
   // load_h_plain: a plain load, for a buffer the kernel also writes (the
   // in-place steps); load_h takes the read-only data path.
-  static __device__ __forceinline__ void load_h_plain(const E* p, T h[2], int a, T) {
+  static __device__ __forceinline__ void load_h_plain(const E* p, T h[2], int a) {
     const double2 v = *reinterpret_cast<const double2*>(p);
     h[0] = v.x - wgt<T>(a);
     h[1] = v.y - wgt<T>(a);
   }
-  static __device__ __forceinline__ void load_h(const E* p, T h[2], int a, T) {
+  static __device__ __forceinline__ void load_h(const E* p, T h[2], int a) {
     const double2 v = __ldg(reinterpret_cast<const double2*>(p));
     h[0] = v.x - wgt<T>(a);
     h[1] = v.y - wgt<T>(a);
   }
-  static __device__ __forceinline__ void store_h(E* p, const T h[2], int a, const unsigned*, bool, T) {
+  static __device__ __forceinline__ void store_h(E* p, const T h[2], int a, const unsigned*, bool) {
     *reinterpret_cast<double2*>(p) = make_double2(h[0] + wgt<T>(a), h[1] + wgt<T>(a));
   }
   // one element's raw bits, rounded as store_h rounds it (r: the word of the
   // element's node pair, k: the element's place in the lane's vector)
   using R = unsigned long long;
-  static __device__ __forceinline__ R round_e(T h, int a, unsigned, int, bool, T) {
+  static __device__ __forceinline__ R round_e(T h, int a, unsigned, int, bool) {
     return static_cast<R>(__double_as_longlong(h + wgt<T>(a)));
   }
 };
@@ -88,6 +91,7 @@ template <> struct Store<kF32> {
   using T = float;
   static constexpr bool kSixteen = false;
   static __device__ __forceinline__ T in(E e, int, T) { return e; }
+  static __device__ __forceinline__ T in_e(E e, int) { return e; }
   static __device__ __forceinline__ E out(T h, int, T) { return h; }
   static __device__ __forceinline__ double to_f64(const E* p, int a, T) {
     return wgt<double>(a) + double(*p);
@@ -96,25 +100,25 @@ template <> struct Store<kF32> {
     *p = float(f - wgt<double>(a));
   }
   // npt = 4 consecutive elements as one 16-byte access
-  static __device__ __forceinline__ void load_h_plain(const E* p, T h[4], int, T) {
+  static __device__ __forceinline__ void load_h_plain(const E* p, T h[4], int) {
     const float4 v = *reinterpret_cast<const float4*>(p);
     h[0] = v.x;
     h[1] = v.y;
     h[2] = v.z;
     h[3] = v.w;
   }
-  static __device__ __forceinline__ void load_h(const E* p, T h[4], int, T) {
+  static __device__ __forceinline__ void load_h(const E* p, T h[4], int) {
     const float4 v = __ldg(reinterpret_cast<const float4*>(p));
     h[0] = v.x;
     h[1] = v.y;
     h[2] = v.z;
     h[3] = v.w;
   }
-  static __device__ __forceinline__ void store_h(E* p, const T h[4], int, const unsigned*, bool, T) {
+  static __device__ __forceinline__ void store_h(E* p, const T h[4], int, const unsigned*, bool) {
     *reinterpret_cast<float4*>(p) = make_float4(h[0], h[1], h[2], h[3]);
   }
   using R = unsigned;
-  static __device__ __forceinline__ R round_e(T h, int, unsigned, int, bool, T) { return __float_as_uint(h); }
+  static __device__ __forceinline__ R round_e(T h, int, unsigned, int, bool) { return __float_as_uint(h); }
 };
 // 16-bit offset forms: npt = 4 elements as one 8-byte access.
 // Multipliers deriving each direction's rounding bits from the node's word
@@ -171,40 +175,41 @@ struct Store16 {
   static constexpr bool kSixteen = true;
 };
 template <> struct Store<kF16> : Store16<__half> {
-  static __device__ __forceinline__ void load_h_plain(const E* p, T h[4], int, T ref) {
-    unpack(*reinterpret_cast<const uint2*>(p), h, ref);
+  static __device__ __forceinline__ void load_h_plain(const E* p, T e[4], int) {
+    unpack(*reinterpret_cast<const uint2*>(p), e);
   }
-  static __device__ __forceinline__ void load_h(const E* p, T h[4], int, T ref) {
-    unpack(__ldg(reinterpret_cast<const uint2*>(p)), h, ref);
+  static __device__ __forceinline__ void load_h(const E* p, T e[4], int) {
+    unpack(__ldg(reinterpret_cast<const uint2*>(p)), e);
   }
-  static __device__ __forceinline__ void unpack(const uint2 v, T h[4], T ref) {
+  static __device__ __forceinline__ void unpack(const uint2 v, T e[4]) {
     const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
     const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
-    h[0] = a.x + ref;
-    h[1] = a.y + ref;
-    h[2] = b.x + ref;
-    h[3] = b.y + ref;
+    e[0] = a.x;
+    e[1] = a.y;
+    e[2] = b.x;
+    e[3] = b.y;
   }
   // r[j]: the rounding word of node pair j (stochastic rounding only)
-  static __device__ __forceinline__ void store_h(E* p, const T h[4], int a, const unsigned* r,
-                                                 bool sr, T ref) {
+  static __device__ __forceinline__ void store_h(E* p, const T e[4], int a, const unsigned* r,
+                                                 bool sr) {
     uint2 v;
     if (sr) {
-      v.x = pack_f16_rs(h[0] - ref, h[1] - ref, pair_bits(r[0], a));
-      v.y = pack_f16_rs(h[2] - ref, h[3] - ref, pair_bits(r[1], a));
+      v.x = pack_f16_rs(e[0], e[1], pair_bits(r[0], a));
+      v.y = pack_f16_rs(e[2], e[3], pair_bits(r[1], a));
     } else {
-      v.x = pack_f16_rn(h[0] - ref, h[1] - ref);
-      v.y = pack_f16_rn(h[2] - ref, h[3] - ref);
+      v.x = pack_f16_rn(e[0], e[1]);
+      v.y = pack_f16_rn(e[2], e[3]);
     }
     *reinterpret_cast<uint2*>(p) = v;
   }
+  static __device__ __forceinline__ T in_e(E e, int) { return __half2float(e); }
   static __device__ __forceinline__ T in(E e, int, T ref) { return __half2float(e) + ref; }
   static __device__ __forceinline__ E out(T h, int, T ref) { return __float2half_rn(h - ref); }
   // one element as store_h rounds it (the packed conversions round each half alike)
   using R = unsigned short;
-  static __device__ __forceinline__ R round_e(T h, int a, unsigned r, int k, bool sr, T ref) {
-    return sr ? (unsigned short)(pack_f16_rs(h - ref, 0.f, pair_bits(r, a) >> (16 * (k & 1))) & 0xffffu)
-              : __half_as_ushort(__float2half_rn(h - ref));
+  static __device__ __forceinline__ R round_e(T e, int a, unsigned r, int k, bool sr) {
+    return sr ? (unsigned short)(pack_f16_rs(e, 0.f, pair_bits(r, a) >> (16 * (k & 1))) & 0xffffu)
+              : __half_as_ushort(__float2half_rn(e));
   }
   // f of a stored element: w + (element + ref), the offset as the kernel forms it
   static __device__ __forceinline__ double to_f64(const E* p, int a, T ref) {
@@ -215,37 +220,38 @@ template <> struct Store<kF16> : Store16<__half> {
   }
 };
 template <> struct Store<kBF16> : Store16<__nv_bfloat16> {
-  static __device__ __forceinline__ void load_h_plain(const E* p, T h[4], int, T ref) {
-    unpack(*reinterpret_cast<const uint2*>(p), h, ref);
+  static __device__ __forceinline__ void load_h_plain(const E* p, T e[4], int) {
+    unpack(*reinterpret_cast<const uint2*>(p), e);
   }
-  static __device__ __forceinline__ void load_h(const E* p, T h[4], int, T ref) {
-    unpack(__ldg(reinterpret_cast<const uint2*>(p)), h, ref);
+  static __device__ __forceinline__ void load_h(const E* p, T e[4], int) {
+    unpack(__ldg(reinterpret_cast<const uint2*>(p)), e);
   }
   // a bf16 is the upper half of an FP32: widening is a shift or a mask
-  static __device__ __forceinline__ void unpack(const uint2 v, T h[4], T ref) {
-    h[0] = __uint_as_float(v.x << 16) + ref;
-    h[1] = __uint_as_float(v.x & 0xffff0000u) + ref;
-    h[2] = __uint_as_float(v.y << 16) + ref;
-    h[3] = __uint_as_float(v.y & 0xffff0000u) + ref;
+  static __device__ __forceinline__ void unpack(const uint2 v, T e[4]) {
+    e[0] = __uint_as_float(v.x << 16);
+    e[1] = __uint_as_float(v.x & 0xffff0000u);
+    e[2] = __uint_as_float(v.y << 16);
+    e[3] = __uint_as_float(v.y & 0xffff0000u);
   }
-  static __device__ __forceinline__ void store_h(E* p, const T h[4], int a, const unsigned* r,
-                                                 bool sr, T ref) {
+  static __device__ __forceinline__ void store_h(E* p, const T e[4], int a, const unsigned* r,
+                                                 bool sr) {
     uint2 v;
     if (sr) {
-      v.x = pack_bf16_rs(h[0] - ref, h[1] - ref, pair_bits(r[0], a));
-      v.y = pack_bf16_rs(h[2] - ref, h[3] - ref, pair_bits(r[1], a));
+      v.x = pack_bf16_rs(e[0], e[1], pair_bits(r[0], a));
+      v.y = pack_bf16_rs(e[2], e[3], pair_bits(r[1], a));
     } else {
-      v.x = pack_bf16_rn(h[0] - ref, h[1] - ref);
-      v.y = pack_bf16_rn(h[2] - ref, h[3] - ref);
+      v.x = pack_bf16_rn(e[0], e[1]);
+      v.y = pack_bf16_rn(e[2], e[3]);
     }
     *reinterpret_cast<uint2*>(p) = v;
   }
+  static __device__ __forceinline__ T in_e(E e, int) { return __bfloat162float(e); }
   static __device__ __forceinline__ T in(E e, int, T ref) { return __bfloat162float(e) + ref; }
   static __device__ __forceinline__ E out(T h, int, T ref) { return __float2bfloat16_rn(h - ref); }
   using R = unsigned short;
-  static __device__ __forceinline__ R round_e(T h, int a, unsigned r, int k, bool sr, T ref) {
-    return sr ? (unsigned short)(pack_bf16_rs(h - ref, 0.f, pair_bits(r, a) >> (16 * (k & 1))) & 0xffffu)
-              : __bfloat16_as_ushort(__float2bfloat16_rn(h - ref));
+  static __device__ __forceinline__ R round_e(T e, int a, unsigned r, int k, bool sr) {
+    return sr ? (unsigned short)(pack_bf16_rs(e, 0.f, pair_bits(r, a) >> (16 * (k & 1))) & 0xffffu)
+              : __bfloat16_as_ushort(__float2bfloat16_rn(e));
   }
   static __device__ __forceinline__ double to_f64(const E* p, int a, T ref) {
     return wgt<double>(a) + double(__bfloat162float(*p) + ref);
@@ -312,17 +318,21 @@ __device__ __forceinline__ typename S::T outlet_ghost(const StepParams& p,
 // The same ghost value in the in-place (AA) push step, whose store no longer
 // holds the last column intact (the neighbours' pushes overwrite it): the
 // stored f*(nx - 1) comes from the side copy z that the local step wrote.
-template <class S>
+// ESP: the value as an element (offset minus the reference) instead of an
+// offset; the convective state itself is always kept as offsets.
+template <class S, bool ESP = false>
 __device__ __forceinline__ typename S::T outlet_ghost_aa(const StepParams& p, int as, int ys,
                                                          bool write) {
   using T = typename S::T;
   const long long gi = (long long)(as == 3 ? 0 : (as == 6 ? 1 : 2)) * p.ny + ys;
-  const T f_last = S::in(static_cast<const typename S::E*>(p.z)[gi], as, sref<S>(p, as));
-  if (p.bc_x != kBcInletConvective) return f_last;  // zero gradient
+  const typename S::E ze = static_cast<const typename S::E*>(p.z)[gi];
+  if (p.bc_x != kBcInletConvective)  // zero gradient
+    return ESP ? S::in_e(ze, as) : S::in(ze, as, sref<S>(p, as));
+  const T f_last = S::in(ze, as, sref<S>(p, as));
   const Consts<T>& c = consts<T>(p);
   const T g = (static_cast<const T*>(p.ghost_src)[gi] + c.u_conv * f_last) * c.conv_inv;
   if (write && p.ghost_dst) static_cast<T*>(p.ghost_dst)[gi] = g;
-  return g;
+  return ESP ? g - sref<S>(p, as) : g;
 }
 
 // ---------------------------------------------------------------------------
@@ -420,16 +430,22 @@ __device__ __forceinline__ void solid_velocity(const StepParams& p, uint8_t m, i
 // FREE: a fluid node (m = 0) without body force (g = 0), for which Eqs. 17
 // and 18 reduce to f_pen = 0 and u = j / rho; the same values as the general
 // form, which would compute them through zero terms.
-template <class T, bool FREE = false>
+// REF: h holds the elements e = h - h_ref of a 16-bit store; the reference
+// enters as its sum and x moment (its y moment is zero: h_ref is even in
+// xi_y).
+template <class T, bool FREE = false, bool REF = false>
 __device__ __forceinline__ Macro<T> macros(const StepParams& p, const T h[9], uint8_t m, int x,
                                            int y) {
   Macro<T> r;
+  const Consts<T>& c = consts<T>(p);
   // sums and differences of opposite populations (the two-rate collision
   // reuses them)
   r.drho = h[0] + (((h[1] + h[3]) + (h[2] + h[4])) + ((h[5] + h[7]) + (h[6] + h[8])));
+  if constexpr (REF) r.drho = r.drho + c.r_sum;
   r.rho = T(1) + r.drho;
-  const T jx = (h[1] - h[3]) + ((h[5] - h[7]) - (h[6] - h[8]));
+  T jx = (h[1] - h[3]) + ((h[5] - h[7]) - (h[6] - h[8]));
   const T jy = (h[2] - h[4]) + ((h[5] - h[7]) + (h[6] - h[8]));
+  if constexpr (REF) jx = jx + c.r_x;
   if constexpr (FREE) {
     const T inv = recip(r.rho);
     r.ux = jx * inv;
@@ -437,7 +453,6 @@ __device__ __forceinline__ Macro<T> macros(const StepParams& p, const T h[9], ui
     r.fpx = r.fpy = r.Fx = r.Fy = T(0);
     return r;
   }
-  const Consts<T>& c = consts<T>(p);
   T usx = T(0), usy = T(0), a = T(0), kap = T(0);
   if (m) {
     a = c.a_s;
@@ -473,38 +488,60 @@ __device__ __forceinline__ Macro<T> macros(const StepParams& p, const T h[9], ui
 // K = s+ (drho - 1.5 rho u.u) - 3 (1 - s+/2) u.F. SRT with Eq. Guo1 is the
 // same with s+ = s- = 1/tau. This is the moment-space operator rearranged,
 // not an approximation of it.
+// On the elements e = h - r of a 16-bit store (REF) the update of a pair is
+// the same, e*_a = e_a + P + Q: the pair's sum and difference carry the
+// reference's r_a + r_abar and r_a - r_abar, which enter P and Q as the
+// constants r_p = -(s+/2)(r_a + r_abar) and r_m = -(s-/2)(r_a - r_abar), and
+// e*_0 = (1 - s+) e_0 + w_0 K - s+ r_0.
 // ---------------------------------------------------------------------------
-template <class T, bool FREE>
+template <class T, bool FREE, bool REF>
 __device__ __forceinline__ void trt_pair(T& ha, T& hb, T xu, T xF, T kw, T aw, T bw, T amw,
-                                         T bmw, T hsp, T hsm) {
+                                         T bmw, T hsp, T hsm, T rq) {
   const T s = ha + hb;
   const T d = ha - hb;
   // w (s+ heq+ + c+ G+) and w (s- heq- + c- G-); without a force G+- = 0
+  // (kw holds the pair's r_p, rq its r_m)
   const T rp = FREE ? xu * (aw * xu) + kw : xu * (aw * xu + bw * xF) + kw;
-  const T rm = FREE ? amw * xu : amw * xu + bmw * xF;
+  T rm;
+  if constexpr (REF)
+    rm = FREE ? amw * xu + rq : amw * xu + (bmw * xF + rq);
+  else
+    rm = FREE ? amw * xu : amw * xu + bmw * xF;
   const T P = rp - hsp * s;
   const T Q = rm - hsm * d;
   ha = ha + (P + Q);
   hb = hb + (P - Q);
 }
 
-template <class T, bool FREE = false>
+template <class T, bool FREE = false, bool REF = false>
 __device__ __forceinline__ void collide_trt(const StepParams& p, T h[9], const Macro<T>& q) {
   const Consts<T>& c = consts<T>(p);
   const T ux = q.ux, uy = q.uy, Fx = q.Fx, Fy = q.Fy, rho = q.rho;
   const T uu = ux * ux + uy * uy;
   const T K = FREE ? c.t_sp * (q.drho - T(1.5) * rho * uu)
                    : c.t_sp * (q.drho - T(1.5) * rho * uu) - c.t_c3p * (ux * Fx + uy * Fy);
-  const T k9 = K * T(1.0 / 9.0), k36 = K * T(1.0 / 36.0);
   const T a9 = c.t_a[0] * rho, a36 = c.t_a[1] * rho;
   const T am9 = c.t_am[0] * rho, am36 = c.t_am[1] * rho;
-  h[0] = c.t_1msp * h[0] + T(4.0 / 9.0) * K;
-  trt_pair<T, FREE>(h[1], h[3], ux, Fx, k9, a9, c.t_b[0], am9, c.t_bm[0], c.t_hsp, c.t_hsm);
-  trt_pair<T, FREE>(h[2], h[4], uy, Fy, k9, a9, c.t_b[0], am9, c.t_bm[0], c.t_hsp, c.t_hsm);
-  trt_pair<T, FREE>(h[5], h[7], ux + uy, Fx + Fy, k36, a36, c.t_b[1], am36, c.t_bm[1], c.t_hsp,
-                    c.t_hsm);
-  trt_pair<T, FREE>(h[6], h[8], uy - ux, Fy - Fx, k36, a36, c.t_b[1], am36, c.t_bm[1], c.t_hsp,
-                    c.t_hsm);
+  T k13, k24, k57, k68;
+  if constexpr (REF) {
+    k13 = K * T(1.0 / 9.0) + c.r_p[0];
+    k24 = K * T(1.0 / 9.0) + c.r_p[1];
+    k57 = K * T(1.0 / 36.0) + c.r_p[2];
+    k68 = K * T(1.0 / 36.0) + c.r_p[3];
+    h[0] = c.t_1msp * h[0] + (T(4.0 / 9.0) * K + c.r_0);
+  } else {
+    k13 = k24 = K * T(1.0 / 9.0);
+    k57 = k68 = K * T(1.0 / 36.0);
+    h[0] = c.t_1msp * h[0] + T(4.0 / 9.0) * K;
+  }
+  trt_pair<T, FREE, REF>(h[1], h[3], ux, Fx, k13, a9, c.t_b[0], am9, c.t_bm[0], c.t_hsp, c.t_hsm,
+                         c.r_m[0]);
+  trt_pair<T, FREE, REF>(h[2], h[4], uy, Fy, k24, a9, c.t_b[0], am9, c.t_bm[0], c.t_hsp, c.t_hsm,
+                         c.r_m[1]);
+  trt_pair<T, FREE, REF>(h[5], h[7], ux + uy, Fx + Fy, k57, a36, c.t_b[1], am36, c.t_bm[1],
+                         c.t_hsp, c.t_hsm, c.r_m[2]);
+  trt_pair<T, FREE, REF>(h[6], h[8], uy - ux, Fy - Fx, k68, a36, c.t_b[1], am36, c.t_bm[1],
+                         c.t_hsp, c.t_hsm, c.r_m[3]);
 }
 
 // MRT (Eq. equa_lbl_mrt with Lu forcing, Eq. Guo2), on the moments of h, for
@@ -701,28 +738,35 @@ __device__ __forceinline__ void finish_reduction(const StepParams& p, int tile, 
 // AA: the push step reads f*_as(xs, ys) from the opposite slot of the source
 // node (where the local step put it), with plain (coherent) loads, since the
 // kernel also writes this buffer.
-template <class S, int A, bool AA = false>
+// ESP: the value as an element of direction A (offset minus the reference),
+// as the fused step works on them; the reference is even in xi_y, so the
+// mirrored source as of a free-slip wall has A's reference.
+template <class S, int A, bool AA = false, bool ESP = false>
 __device__ __forceinline__ typename S::T edge_pull(const StepParams& p, const typename S::E* src,
                                                    int as, int ys, int xs) {
+  using T = typename S::T;
   if (xs < 0 || xs >= p.nx) {
     if (p.bc_x == kBcPeriodic) {
       xs %= p.nx;
       if (xs < 0) xs += p.nx;
     } else if (xs < 0) {  // inlet ghost column at f_eq(1, u_in)
-      const Consts<typename S::T>& c = consts<typename S::T>(p);
-      return as == A ? c.heq_in[A] : c.heq_in[mirror_y(A)];
+      const Consts<T>& c = consts<T>(p);
+      const T h = as == A ? c.heq_in[A] : c.heq_in[mirror_y(A)];
+      return ESP ? h - sref<S>(p, A) : h;
     } else if (AA) {
-      return outlet_ghost_aa<S>(p, as, ys, xs == p.nx);
+      return outlet_ghost_aa<S, ESP>(p, as, ys, xs == p.nx);
     } else if (p.bc_x == kBcInletConvective) {
       // xs == nx: the last column's own pull (the entry's one reader); beyond
       // it, the unused edge value of a lane past the last column
-      return outlet_ghost<S>(p, src, as, ys, xs == p.nx);
+      const T g = outlet_ghost<S>(p, src, as, ys, xs == p.nx);
+      return ESP ? g - sref<S>(p, A) : g;
     } else {  // zero-gradient outlet ghost column
       xs = p.nx - 1;
     }
   }
-  if (AA) return S::in(src[(long long)opposite(as) * p.plane + (long long)ys * p.pitch + xs], as, sref<S>(p, as));
-  return load_h<S>(p, src + (long long)as * p.plane + (long long)ys * p.pitch + xs, as);
+  const typename S::E e = AA ? src[(long long)opposite(as) * p.plane + (long long)ys * p.pitch + xs]
+                             : __ldg(src + (long long)as * p.plane + (long long)ys * p.pitch + xs);
+  return ESP ? S::in_e(e, as) : S::in(e, as, sref<S>(p, as));
 }
 
 template <class S, int N, int A, bool GEN, bool AA = false>
@@ -743,12 +787,11 @@ __device__ __forceinline__ void pull_dir_vec(const StepParams& p, const typename
   }
   const E* row = src + (long long)(AA ? opposite(as) : as) * p.plane + (long long)ys * p.pitch;
   T v[N];
-  const T ref = sref<S>(p, as);
   if (!GEN || lane_active) {
     if (AA)
-      S::load_h_plain(row + xb, v, as, ref);
+      S::load_h_plain(row + xb, v, as);
     else
-      S::load_h(row + xb, v, as, ref);
+      S::load_h(row + xb, v, as);
   } else {
 #pragma unroll
     for (int k = 0; k < N; ++k) v[k] = T(0);
@@ -761,16 +804,16 @@ __device__ __forceinline__ void pull_dir_vec(const StepParams& p, const typename
     // the edge lanes' extra value: through the x boundary rules only where
     // it lies outside the grid (the source row already carries the y rules)
     if (lane == 0)
-      left = GEN && xb - 1 < 0 ? edge_pull<S, A, AA>(p, src, as, ys, xb - 1)
-                               : (AA ? S::in(row[xb - 1], as, ref) : S::in(__ldg(row + xb - 1), as, ref));
+      left = GEN && xb - 1 < 0 ? edge_pull<S, A, AA, true>(p, src, as, ys, xb - 1)
+                               : S::in_e(AA ? row[xb - 1] : __ldg(row + xb - 1), as);
     h[0][A] = left;
 #pragma unroll
     for (int k = 1; k < N; ++k) h[k][A] = v[k - 1];
   } else {  // node k pulls from x + 1
     T right = __shfl_down_sync(0xffffffffu, v[0], 1);
     if (lane == kLanes - 1)
-      right = GEN && xb + N >= p.nx ? edge_pull<S, A, AA>(p, src, as, ys, xb + N)
-                                    : (AA ? S::in(row[xb + N], as, ref) : S::in(__ldg(row + xb + N), as, ref));
+      right = GEN && xb + N >= p.nx ? edge_pull<S, A, AA, true>(p, src, as, ys, xb + N)
+                                    : S::in_e(AA ? row[xb + N] : __ldg(row + xb + N), as);
 #pragma unroll
     for (int k = 0; k < N - 1; ++k) h[k][A] = v[k + 1];
     h[N - 1][A] = right;
@@ -778,7 +821,7 @@ __device__ __forceinline__ void pull_dir_vec(const StepParams& p, const typename
       // the domain's last column pulls from beyond it, through the x boundary
 #pragma unroll
       for (int k = 0; k < N; ++k)
-        if (xb + k == p.nx - 1) h[k][A] = edge_pull<S, A, AA>(p, src, as, ys, p.nx);
+        if (xb + k == p.nx - 1) h[k][A] = edge_pull<S, A, AA, true>(p, src, as, ys, p.nx);
     }
   }
 }
@@ -929,7 +972,8 @@ __device__ __forceinline__ void push_dir_vec(const StepParams& p, typename S::E*
 // ghost columns. Inlet: f_eq(1, u_in) for the directions entering at x = 0.
 // Outlet: h holds the ghost column's copy of f*(nx - 1) (pushed there by the
 // previous push step); the convective outlet advances its state from it.
-template <class S>
+// ESP: h holds elements (offsets minus the reference) instead of offsets.
+template <class S, bool ESP = false>
 __device__ __forceinline__ void aa_local_boundary(const StepParams& p, typename S::T h[9], int x,
                                                   int y, bool write) {
   using T = typename S::T;
@@ -948,12 +992,13 @@ __device__ __forceinline__ void aa_local_boundary(const StepParams& p, typename 
       }
     }
     if (cx(a) == 1) {
-      h[a] = c.heq_in[as];
+      h[a] = ESP ? c.heq_in[as] - sref<S>(p, a) : c.heq_in[as];
     } else if (p.bc_x == kBcInletConvective) {
       const long long gi = (long long)(as == 3 ? 0 : (as == 6 ? 1 : 2)) * p.ny + ys;
-      const T g = (static_cast<const T*>(p.ghost_src)[gi] + c.u_conv * h[a]) * c.conv_inv;
+      const T f_last = ESP ? h[a] + sref<S>(p, a) : h[a];
+      const T g = (static_cast<const T*>(p.ghost_src)[gi] + c.u_conv * f_last) * c.conv_inv;
       if (write) static_cast<T*>(p.ghost_dst)[gi] = g;
-      h[a] = g;
+      h[a] = ESP ? g - sref<S>(p, a) : g;
     }
   }
 }
@@ -1021,21 +1066,32 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
                                : unsigned(*reinterpret_cast<const unsigned short*>(p.mask + i));
     auto mk = [&](int k) -> uint8_t { return uint8_t(mw >> (8 * k)); };
     const bool sr = S::kSixteen && p.stochastic;
+    constexpr bool REF = S::kSixteen;  // h holds elements e = h - h_ref
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       if (GEN && xb + k >= p.nx) continue;  // past the last column: padding, stored as pulled
       if (COLL == kTrt && !GEN && p.force_free && mk(k) == 0) {
         // a fluid node without body force: the force-free form of the step
-        const Macro<T> q = macros<T, true>(p, h[k], 0, xb + k, y);
-        collide_trt<T, true>(p, h[k], q);
+        const Macro<T> q = macros<T, true, REF>(p, h[k], 0, xb + k, y);
+        collide_trt<T, true, REF>(p, h[k], q);
         finish_node(q, 0);
-      } else {
-        const Macro<T> q = macros<T>(p, h[k], mk(k), xb + k, y);
-        if (COLL == kTrt)
-          collide_trt<T>(p, h[k], q);
-        else
-          collide_mrt<T>(p, h[k], q);
+      } else if (COLL == kTrt) {
+        const Macro<T> q = macros<T, false, REF>(p, h[k], mk(k), xb + k, y);
+        collide_trt<T, false, REF>(p, h[k], q);
         finish_node(q, mk(k));
+      } else {
+        // the moment-space form works on offsets
+        if constexpr (REF) {
+#pragma unroll
+          for (int a = 0; a < 9; ++a) h[k][a] = h[k][a] + sref<S>(p, a);
+        }
+        const Macro<T> q = macros<T>(p, h[k], mk(k), xb + k, y);
+        collide_mrt<T>(p, h[k], q);
+        finish_node(q, mk(k));
+        if constexpr (REF) {
+#pragma unroll
+          for (int a = 0; a < 9; ++a) h[k][a] = h[k][a] - sref<S>(p, a);
+        }
       }
     }
     // the rounding word of each of the lane's node pairs (16-bit stores):
@@ -1050,7 +1106,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
         T o[N];
 #pragma unroll
         for (int k = 0; k < N; ++k) o[k] = h[k][a];
-        S::store_h(dst + (long long)a * p.plane + i, o, a, nb, sr, sref<S>(p, a));
+        S::store_h(dst + (long long)a * p.plane + i, o, a, nb, sr);
       }
     } else if constexpr (MODE == kModeAALocal) {
 #pragma unroll
@@ -1058,7 +1114,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
         T o[N];
 #pragma unroll
         for (int k = 0; k < N; ++k) o[k] = h[k][a];
-        S::store_h(buf + (long long)opposite(a) * p.plane + i, o, a, nb, sr, sref<S>(p, a));
+        S::store_h(buf + (long long)opposite(a) * p.plane + i, o, a, nb, sr);
       }
       if (GEN && p.bc_x != kBcPeriodic) {
         // the outlet column's stored f* of alpha = 3, 6, 7, for the next push step
@@ -1066,9 +1122,9 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
         for (int k = 0; k < N; ++k) {
           if (xb + k != p.nx - 1) continue;
           typename S::R* z = static_cast<typename S::R*>(p.z);
-          z[0 * p.ny + y] = S::round_e(h[k][3], 3, nb[k >> 1], k, sr, sref<S>(p, 3));
-          z[1 * p.ny + y] = S::round_e(h[k][6], 6, nb[k >> 1], k, sr, sref<S>(p, 6));
-          z[2 * p.ny + y] = S::round_e(h[k][7], 7, nb[k >> 1], k, sr, sref<S>(p, 7));
+          z[0 * p.ny + y] = S::round_e(h[k][3], 3, nb[k >> 1], k, sr);
+          z[1 * p.ny + y] = S::round_e(h[k][6], 6, nb[k >> 1], k, sr);
+          z[2 * p.ny + y] = S::round_e(h[k][7], 7, nb[k >> 1], k, sr);
         }
       }
     } else {  // push step
@@ -1080,7 +1136,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
       for (int a = 0; a < 9; ++a) {
         typename S::R e[N];
 #pragma unroll
-        for (int k = 0; k < N; ++k) e[k] = S::round_e(h[k][a], a, nb[k >> 1], k, sr, sref<S>(p, a));
+        for (int k = 0; k < N; ++k) e[k] = S::round_e(h[k][a], a, nb[k >> 1], k, sr);
         if (vec) {
           push_dir_vec<S, N>(p, buf, a, xb, y, lane, e);
         } else {
@@ -1093,9 +1149,9 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
 #pragma unroll
         for (int k = 0; k < N; ++k) {
           if (xb + k != p.nx - 1) continue;
-          push_outlet_copy<S>(p, buf, 3, y, S::round_e(h[k][3], 3, nb[k >> 1], k, sr, sref<S>(p, 3)));
-          push_outlet_copy<S>(p, buf, 6, y, S::round_e(h[k][6], 6, nb[k >> 1], k, sr, sref<S>(p, 6)));
-          push_outlet_copy<S>(p, buf, 7, y, S::round_e(h[k][7], 7, nb[k >> 1], k, sr, sref<S>(p, 7)));
+          push_outlet_copy<S>(p, buf, 3, y, S::round_e(h[k][3], 3, nb[k >> 1], k, sr));
+          push_outlet_copy<S>(p, buf, 6, y, S::round_e(h[k][6], 6, nb[k >> 1], k, sr));
+          push_outlet_copy<S>(p, buf, 7, y, S::round_e(h[k][7], 7, nb[k >> 1], k, sr));
         }
       }
     }
@@ -1111,14 +1167,14 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
         T v[N];
-        S::load_h_plain(buf + (long long)a * p.plane + i, v, a, sref<S>(p, a));
+        S::load_h_plain(buf + (long long)a * p.plane + i, v, a);
 #pragma unroll
         for (int k = 0; k < N; ++k) h[k][a] = v[k];
       }
       if (GEN) {
 #pragma unroll
         for (int k = 0; k < N; ++k)
-          if (xb + k < p.nx) aa_local_boundary<S>(p, h[k], xb + k, y, true);
+          if (xb + k < p.nx) aa_local_boundary<S, true>(p, h[k], xb + k, y, true);
       }
     } else {
       constexpr bool AA = MODE == kModeAAPush;
