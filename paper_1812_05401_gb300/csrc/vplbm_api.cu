@@ -447,26 +447,15 @@ void heq_host(double rho, double ux, double uy, double out[9]) {
   }
 }
 
-// The sums through which a store's reference enters the two-rate collision
-// on stored elements (zero without a reference), from the reference as the
-// kernels hold it.
+// Pair sums and differences of a store's reference (zero without one), from
+// the reference as the kernels hold it.
 template <class T>
-void ref_sums(Consts<T>& c, const double sp, const double sm) {
-  static const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+void ref_sums(Consts<T>& c) {
   static const int pa[4] = {1, 2, 5, 6}, pb[4] = {3, 4, 7, 8};
-  double r[9], sum = 0.0, sx = 0.0;
-  for (int a = 0; a < 9; ++a) {
-    r[a] = double(c.h_ref[a]);
-    sum += r[a];
-    sx += ex[a] * r[a];
-  }
-  c.r_sum = T(sum);
-  c.r_x = T(sx);
   for (int k = 0; k < 4; ++k) {
-    c.r_p[k] = T(-0.5 * sp * (r[pa[k]] + r[pb[k]]));
-    c.r_m[k] = T(-0.5 * sm * (r[pa[k]] - r[pb[k]]));
+    c.r_s[k] = T(double(c.h_ref[pa[k]]) + double(c.h_ref[pb[k]]));
+    c.r_d[k] = T(double(c.h_ref[pa[k]]) - double(c.h_ref[pb[k]]));
   }
-  c.r_0 = T(-sp * r[0]);
 }
 
 // Float copies of the FP64 constants.
@@ -498,7 +487,7 @@ void round_consts(StepParams* p) {
     f.t_am[k] = float(d.t_am[k]);
     f.t_bm[k] = float(d.t_bm[k]);
   }
-  ref_sums(f, d.t_sp, 2.0 * d.t_hsm);
+  ref_sums(f);
 }
 
 // Collision and forcing constants of a configuration (FP64, then their float
@@ -568,7 +557,22 @@ void physics_consts(const vplbm_config* cfg, StepParams* p) {
   const bool inlet = cfg->bc_x == VPLBM_BC_INLET_OUTLET || cfg->bc_x == VPLBM_BC_INLET_CONVECTIVE;
   for (int a = 0; a < 9; ++a)
     cd.h_ref[a] = sixteen && inlet ? 0.25 * (cd.heq_in[a] + cd.heq_in[my[a]]) : 0.0;
-  ref_sums(cd, sp, sm);
+  // The reference is rounded to multiples of 2^-28 (of 2^-21 of its largest
+  // magnitude, for references above 2^-7), so that it, its pair sums and
+  // differences, and element + reference for every FP16 element (a multiple
+  // of 2^-24) whose sum stays below 2^-4 are exact in FP32: the kernels decode
+  // stored elements without rounding, and no rounding error of a constant
+  // repeats at every node and step (stochastic rounding carries such a
+  // repeated error forward, like a small body force, instead of absorbing it).
+  double rmax = 0.0;
+  for (int a = 0; a < 9; ++a) rmax = std::max(rmax, std::fabs(cd.h_ref[a]));
+  if (rmax > 0.0) {
+    int ex;
+    std::frexp(rmax, &ex);  // rmax < 2^ex
+    const double grid = std::ldexp(1.0, std::max(-28, ex - 21));
+    for (int a = 0; a < 9; ++a) cd.h_ref[a] = std::nearbyint(cd.h_ref[a] / grid) * grid;
+  }
+  ref_sums(cd);
   cd.u_conv = cfg->u_conv;
   cd.conv_inv = 1.0 / (1.0 + cfg->u_conv);
   round_consts(p);

@@ -427,12 +427,29 @@ __device__ __forceinline__ void solid_velocity(const StepParams& p, uint8_t m, i
   // any other label (only a caller-written mask can hold one) is solid at rest
 }
 
+// Sum and difference of the offsets of the opposite pair k ((1,3), (2,4),
+// (5,7), (6,8)) whose values the kernel holds in ha, hb: offsets themselves,
+// or (REF) the elements e = h - h_ref of a 16-bit store, decoded here with
+// the pair's reference sum and difference (exact in FP32).
+template <class T, bool REF>
+__device__ __forceinline__ T pair_s(const Consts<T>& c, T ha, T hb, int k) {
+  if constexpr (REF)
+    return (ha + hb) + c.r_s[k];
+  else
+    return ha + hb;
+}
+template <class T, bool REF>
+__device__ __forceinline__ T pair_d(const Consts<T>& c, T ha, T hb, int k) {
+  if constexpr (REF)
+    return (ha - hb) + c.r_d[k];
+  else
+    return ha - hb;
+}
+
 // FREE: a fluid node (m = 0) without body force (g = 0), for which Eqs. 17
 // and 18 reduce to f_pen = 0 and u = j / rho; the same values as the general
 // form, which would compute them through zero terms.
-// REF: h holds the elements e = h - h_ref of a 16-bit store; the reference
-// enters as its sum and x moment (its y moment is zero: h_ref is even in
-// xi_y).
+// REF: h holds the elements e = h - h_ref of a 16-bit store.
 template <class T, bool FREE = false, bool REF = false>
 __device__ __forceinline__ Macro<T> macros(const StepParams& p, const T h[9], uint8_t m, int x,
                                            int y) {
@@ -440,12 +457,15 @@ __device__ __forceinline__ Macro<T> macros(const StepParams& p, const T h[9], ui
   const Consts<T>& c = consts<T>(p);
   // sums and differences of opposite populations (the two-rate collision
   // reuses them)
-  r.drho = h[0] + (((h[1] + h[3]) + (h[2] + h[4])) + ((h[5] + h[7]) + (h[6] + h[8])));
-  if constexpr (REF) r.drho = r.drho + c.r_sum;
+  const T h0 = REF ? h[0] + c.h_ref[0] : h[0];
+  const T s13 = pair_s<T, REF>(c, h[1], h[3], 0), s24 = pair_s<T, REF>(c, h[2], h[4], 1);
+  const T s57 = pair_s<T, REF>(c, h[5], h[7], 2), s68 = pair_s<T, REF>(c, h[6], h[8], 3);
+  const T d13 = pair_d<T, REF>(c, h[1], h[3], 0), d24 = pair_d<T, REF>(c, h[2], h[4], 1);
+  const T d57 = pair_d<T, REF>(c, h[5], h[7], 2), d68 = pair_d<T, REF>(c, h[6], h[8], 3);
+  r.drho = h0 + ((s13 + s24) + (s57 + s68));
   r.rho = T(1) + r.drho;
-  T jx = (h[1] - h[3]) + ((h[5] - h[7]) - (h[6] - h[8]));
-  const T jy = (h[2] - h[4]) + ((h[5] - h[7]) + (h[6] - h[8]));
-  if constexpr (REF) jx = jx + c.r_x;
+  const T jx = d13 + (d57 - d68);
+  const T jy = d24 + (d57 + d68);
   if constexpr (FREE) {
     const T inv = recip(r.rho);
     r.ux = jx * inv;
@@ -488,25 +508,16 @@ __device__ __forceinline__ Macro<T> macros(const StepParams& p, const T h[9], ui
 // K = s+ (drho - 1.5 rho u.u) - 3 (1 - s+/2) u.F. SRT with Eq. Guo1 is the
 // same with s+ = s- = 1/tau. This is the moment-space operator rearranged,
 // not an approximation of it.
-// On the elements e = h - r of a 16-bit store (REF) the update of a pair is
-// the same, e*_a = e_a + P + Q: the pair's sum and difference carry the
-// reference's r_a + r_abar and r_a - r_abar, which enter P and Q as the
-// constants r_p = -(s+/2)(r_a + r_abar) and r_m = -(s-/2)(r_a - r_abar), and
-// e*_0 = (1 - s+) e_0 + w_0 K - s+ r_0.
+// On the elements e = h - r of a 16-bit store (REF) the update is the same,
+// e*_a = e_a + P + Q, with s and d decoded from the elements (pair_s, pair_d),
+// and e*_0 = (1 - s+) (e_0 + r_0) + w_0 K - r_0.
 // ---------------------------------------------------------------------------
-template <class T, bool FREE, bool REF>
-__device__ __forceinline__ void trt_pair(T& ha, T& hb, T xu, T xF, T kw, T aw, T bw, T amw,
-                                         T bmw, T hsp, T hsm, T rq) {
-  const T s = ha + hb;
-  const T d = ha - hb;
+template <class T, bool FREE>
+__device__ __forceinline__ void trt_pair(T& ha, T& hb, T s, T d, T xu, T xF, T kw, T aw, T bw,
+                                         T amw, T bmw, T hsp, T hsm) {
   // w (s+ heq+ + c+ G+) and w (s- heq- + c- G-); without a force G+- = 0
-  // (kw holds the pair's r_p, rq its r_m)
   const T rp = FREE ? xu * (aw * xu) + kw : xu * (aw * xu + bw * xF) + kw;
-  T rm;
-  if constexpr (REF)
-    rm = FREE ? amw * xu + rq : amw * xu + (bmw * xF + rq);
-  else
-    rm = FREE ? amw * xu : amw * xu + bmw * xF;
+  const T rm = FREE ? amw * xu : amw * xu + bmw * xF;
   const T P = rp - hsp * s;
   const T Q = rm - hsm * d;
   ha = ha + (P + Q);
@@ -520,28 +531,26 @@ __device__ __forceinline__ void collide_trt(const StepParams& p, T h[9], const M
   const T uu = ux * ux + uy * uy;
   const T K = FREE ? c.t_sp * (q.drho - T(1.5) * rho * uu)
                    : c.t_sp * (q.drho - T(1.5) * rho * uu) - c.t_c3p * (ux * Fx + uy * Fy);
+  const T k9 = K * T(1.0 / 9.0), k36 = K * T(1.0 / 36.0);
   const T a9 = c.t_a[0] * rho, a36 = c.t_a[1] * rho;
   const T am9 = c.t_am[0] * rho, am36 = c.t_am[1] * rho;
-  T k13, k24, k57, k68;
-  if constexpr (REF) {
-    k13 = K * T(1.0 / 9.0) + c.r_p[0];
-    k24 = K * T(1.0 / 9.0) + c.r_p[1];
-    k57 = K * T(1.0 / 36.0) + c.r_p[2];
-    k68 = K * T(1.0 / 36.0) + c.r_p[3];
-    h[0] = c.t_1msp * h[0] + (T(4.0 / 9.0) * K + c.r_0);
-  } else {
-    k13 = k24 = K * T(1.0 / 9.0);
-    k57 = k68 = K * T(1.0 / 36.0);
+  // the pair sums and differences as macros() formed them
+  const T s13 = pair_s<T, REF>(c, h[1], h[3], 0), s24 = pair_s<T, REF>(c, h[2], h[4], 1);
+  const T s57 = pair_s<T, REF>(c, h[5], h[7], 2), s68 = pair_s<T, REF>(c, h[6], h[8], 3);
+  const T d13 = pair_d<T, REF>(c, h[1], h[3], 0), d24 = pair_d<T, REF>(c, h[2], h[4], 1);
+  const T d57 = pair_d<T, REF>(c, h[5], h[7], 2), d68 = pair_d<T, REF>(c, h[6], h[8], 3);
+  if constexpr (REF)
+    h[0] = c.t_1msp * (h[0] + c.h_ref[0]) + (T(4.0 / 9.0) * K - c.h_ref[0]);
+  else
     h[0] = c.t_1msp * h[0] + T(4.0 / 9.0) * K;
-  }
-  trt_pair<T, FREE, REF>(h[1], h[3], ux, Fx, k13, a9, c.t_b[0], am9, c.t_bm[0], c.t_hsp, c.t_hsm,
-                         c.r_m[0]);
-  trt_pair<T, FREE, REF>(h[2], h[4], uy, Fy, k24, a9, c.t_b[0], am9, c.t_bm[0], c.t_hsp, c.t_hsm,
-                         c.r_m[1]);
-  trt_pair<T, FREE, REF>(h[5], h[7], ux + uy, Fx + Fy, k57, a36, c.t_b[1], am36, c.t_bm[1],
-                         c.t_hsp, c.t_hsm, c.r_m[2]);
-  trt_pair<T, FREE, REF>(h[6], h[8], uy - ux, Fy - Fx, k68, a36, c.t_b[1], am36, c.t_bm[1],
-                         c.t_hsp, c.t_hsm, c.r_m[3]);
+  trt_pair<T, FREE>(h[1], h[3], s13, d13, ux, Fx, k9, a9, c.t_b[0], am9, c.t_bm[0], c.t_hsp,
+                    c.t_hsm);
+  trt_pair<T, FREE>(h[2], h[4], s24, d24, uy, Fy, k9, a9, c.t_b[0], am9, c.t_bm[0], c.t_hsp,
+                    c.t_hsm);
+  trt_pair<T, FREE>(h[5], h[7], s57, d57, ux + uy, Fx + Fy, k36, a36, c.t_b[1], am36, c.t_bm[1],
+                    c.t_hsp, c.t_hsm);
+  trt_pair<T, FREE>(h[6], h[8], s68, d68, uy - ux, Fy - Fx, k36, a36, c.t_b[1], am36, c.t_bm[1],
+                    c.t_hsp, c.t_hsm);
 }
 
 // MRT (Eq. equa_lbl_mrt with Lu forcing, Eq. Guo2), on the moments of h, for

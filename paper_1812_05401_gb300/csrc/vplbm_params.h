@@ -71,12 +71,10 @@ struct Consts {
   T gx, gy;                               // body force per unit mass
   T heq_in[9];                            // inlet ghost f_eq(1, u_in) - w
   T h_ref[9];                             // 16-bit stores: elements hold h - h_ref
-  // The fused step's two-rate collision works on the stored elements
-  // e = h - h_ref directly; h_ref enters through these sums (zero when
-  // h_ref = 0), with pairs (1,3), (2,4), (5,7), (6,8):
-  T r_sum, r_x;                           // sum of h_ref, sum of xi_x h_ref
-  T r_p[4], r_m[4];                       // -s+/2 (r_a + r_b), -s-/2 (r_a - r_b)
-  T r_0;                                  // -s+ h_ref[0]
+  // h_ref[a] + h_ref[b] and h_ref[a] - h_ref[b] for the opposite pairs (1,3),
+  // (2,4), (5,7), (6,8): the fused step's two-rate collision decodes pair
+  // sums and differences of stored elements with them
+  T r_s[4], r_d[4];
   T u_conv, conv_inv;                     // convective outlet: U_c and 1/(1 + U_c)
   T body[kMaxBodies][5];                  // cx, cy, vx, vy, omega of each body
 };
