@@ -60,13 +60,13 @@ enum { VPLBM_SRT = 0, /* BGK, Eq. LatticeBoltz with Guo forcing, Eq. Guo1 */
  * (the same bytes, a finer rounding step); the *_OFFSET forms store, in 16
  * bits, f_alpha - r_alpha, rounded as vplbm_config.rounding says
  * (stochastically by default). The reference r is w (the rest state), and for
- * a flow with an inlet (bc_x INLET_*) the midpoint between w and the inlet's
- * equilibrium f_eq(1, u_in), taking the part of f_eq(1, u_in) - w that is
- * even in xi_y (all of it for an inlet along x; a population and its mirror
- * image at a free-slip wall then share one reference): a channel's
- * populations lie between the stagnant wake and the free stream, within
- * about half the stream's offsets of r everywhere, which halves the largest
- * elements and their rounding steps. */
+ * a flow with an inlet (bc_x INLET_*) r = w + (3/2) w xi_x u_in,x, half of the
+ * inlet equilibrium's momentum term along x, rounded to multiples of 2^-28:
+ * a channel's populations lie between the stagnant wake and the free stream,
+ * within about half the stream's offsets of r everywhere, which halves the
+ * largest elements and their rounding steps. r is odd in xi (it adds nothing
+ * to density or to sums of opposite populations) and even in xi_y (a
+ * population and its mirror image at a free-slip wall share it). */
 enum { VPLBM_F64 = 0, VPLBM_F32 = 1, VPLBM_F16_OFFSET = 2, VPLBM_BF16_OFFSET = 3 };
 
 /* Rounding of the 16-bit stores. NEAREST: round to nearest even.
@@ -357,9 +357,9 @@ vplbm_status vplbm_fused_timing(vplbm_solver* s, double* total_ms, int64_t* laun
  *
  * Scratch: the per-tile and per-group reduction sums live in a fixed 1 MiB
  * device array inside the library, which every GPU that loads the library
- * holds until the process exits. It holds at most 43,491 tiles of the fused
- * step: with tiles of 128 x 32 nodes (FP32 and 16-bit storage) about 178.1M
- * nodes, with tiles of 64 x 32 (FP64) about 89.1M. Larger grids are rejected
+ * holds until the process exits. It holds at most 43,294 tiles of the fused
+ * step: with tiles of 128 x 32 nodes (FP32 and 16-bit storage) about 177.3M
+ * nodes, with tiles of 64 x 32 (FP64) about 88.7M. Larger grids are rejected
  * with VPLBM_ERR_INVALID and a message; use vplbm_create/vplbm_step for them.
  * The first call on a device looks up the array's device address (done once
  * per device, with that device current) and keeps it for the rest of the

@@ -447,15 +447,12 @@ void heq_host(double rho, double ux, double uy, double out[9]) {
   }
 }
 
-// Pair sums and differences of a store's reference (zero without one), from
-// the reference as the kernels hold it.
+// Pair differences of a store's reference (zero without one), from the
+// reference as the kernels hold it (odd in xi, so its pair sums are zero).
 template <class T>
 void ref_sums(Consts<T>& c) {
   static const int pa[4] = {1, 2, 5, 6}, pb[4] = {3, 4, 7, 8};
-  for (int k = 0; k < 4; ++k) {
-    c.r_s[k] = T(double(c.h_ref[pa[k]]) + double(c.h_ref[pb[k]]));
-    c.r_d[k] = T(double(c.h_ref[pa[k]]) - double(c.h_ref[pb[k]]));
-  }
+  for (int k = 0; k < 4; ++k) c.r_d[k] = T(double(c.h_ref[pa[k]]) - double(c.h_ref[pb[k]]));
 }
 
 // Float copies of the FP64 constants.
@@ -543,23 +540,25 @@ void physics_consts(const vplbm_config* cfg, StepParams* p) {
   p->force_free = cfg->body_force[0] == 0.0 && cfg->body_force[1] == 0.0 ? 1 : 0;
   p->round_key = 0x9e3779b9u ^ (cfg->rounding_seed * 0x85ebca6bu);
   heq_host(1.0, cfg->u_in[0], cfg->u_in[1], cd.heq_in);
-  // 16-bit stores of a channel keep offsets from the midpoint between the rest
-  // state and the inlet's equilibrium: the populations of the stagnant wake
-  // and of the free stream then both lie within about half the stream's
-  // offsets of it, which halves the largest elements and their rounding
-  // steps (offsets from the inlet's equilibrium itself would make the wake's
-  // elements the largest); other flows and storages keep offsets from w.
-  // The reference takes the part of f_eq(1, u_in) - w that is even in xi_y
-  // (all of it for an inlet along x), so that a population and its mirror
-  // image at a free-slip wall share one reference.
-  static const int my[9] = {0, 1, 4, 3, 2, 8, 7, 6, 5};
+  // 16-bit stores of a channel keep offsets from a reference halfway towards
+  // the inlet's equilibrium: r = w + (3/2) w xi_x u_in,x, half of the part of
+  // f_eq(1, u_in) - w that is odd in xi and even in xi_y (its momentum term
+  // along x). The populations of the stagnant wake and of the free stream
+  // then both lie within about half the stream's offsets of r, which halves
+  // the largest elements and their rounding steps (offsets from the inlet's
+  // equilibrium itself would make the wake's elements the largest). Being odd
+  // in xi, r adds nothing to the density or to the pair sums of opposite
+  // populations; being even in xi_y, a population and its mirror image at a
+  // free-slip wall share it. Other flows and storages keep offsets from w.
+  static const double ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  static const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                              1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
   const bool sixteen = cfg->storage == VPLBM_F16_OFFSET || cfg->storage == VPLBM_BF16_OFFSET;
   const bool inlet = cfg->bc_x == VPLBM_BC_INLET_OUTLET || cfg->bc_x == VPLBM_BC_INLET_CONVECTIVE;
-  for (int a = 0; a < 9; ++a)
-    cd.h_ref[a] = sixteen && inlet ? 0.25 * (cd.heq_in[a] + cd.heq_in[my[a]]) : 0.0;
+  for (int a = 0; a < 9; ++a) cd.h_ref[a] = sixteen && inlet ? 1.5 * w[a] * ex[a] * cfg->u_in[0] : 0.0;
   // The reference is rounded to multiples of 2^-28 (of 2^-21 of its largest
-  // magnitude, for references above 2^-7), so that it, its pair sums and
-  // differences, and element + reference for every FP16 element (a multiple
+  // magnitude, for references above 2^-7), so that it, its pair differences,
+  // and element + reference for every FP16 element (a multiple
   // of 2^-24) whose sum stays below 2^-4 are exact in FP32: the kernels decode
   // stored elements without rounding, and no rounding error of a constant
   // repeats at every node and step (stochastic rounding carries such a
@@ -567,9 +566,9 @@ void physics_consts(const vplbm_config* cfg, StepParams* p) {
   double rmax = 0.0;
   for (int a = 0; a < 9; ++a) rmax = std::max(rmax, std::fabs(cd.h_ref[a]));
   if (rmax > 0.0) {
-    int ex;
-    std::frexp(rmax, &ex);  // rmax < 2^ex
-    const double grid = std::ldexp(1.0, std::max(-28, ex - 21));
+    int e2;
+    std::frexp(rmax, &e2);  // rmax < 2^e2
+    const double grid = std::ldexp(1.0, std::max(-28, e2 - 21));
     for (int a = 0; a < 9; ++a) cd.h_ref[a] = std::nearbyint(cd.h_ref[a] / grid) * grid;
   }
   ref_sums(cd);
@@ -725,7 +724,7 @@ int tile_rows_of(const vplbm_config* c) {
   const long long tx = (c->nx + tile_x(c->storage) - 1) / tile_x(c->storage);
   const long long want = 4 * kSmCount * min_blocks_per_sm(c->storage);
   int rows = kTileRowsMax;
-  while (rows > kWarps && tx * ((c->ny + rows - 1) / rows) < want) rows /= 2;
+  while (rows > kTileRowsMin && tx * ((c->ny + rows - 1) / rows) < want) rows /= 2;
   return rows;
 }
 
@@ -907,7 +906,7 @@ vplbm_status vplbm_create(const vplbm_config* cfg, vplbm_solver** out) {
   p.tiles_x = s->tiles_x;
   p.n_tiles = s->n_tiles;
   p.tile_y = tile_rows_of(cfg);
-  p.rows_per_warp = p.tile_y / kWarps;
+  p.rows_per_warp = p.tile_y / warps_per_block(cfg->storage);
   p.mode = s->aa ? kModeAAPush : kModeAB;
   p.z = s->z;
   p.lost = s->lost;
@@ -1600,8 +1599,8 @@ void vplbm_destroy(vplbm_solver* s) {
 
 namespace {
 
-// 1 MiB: 24 bytes per tile, 24 per group of 256 tiles, 4 per group counter
-// (+1), 16-byte alignment and the 4-byte flag hold at most 43,491 tiles.
+// 1 MiB: 24 bytes per tile, 24 per group of 128 tiles, 4 per group counter
+// (+1), 16-byte alignment and the 4-byte flag hold at most 43,294 tiles.
 constexpr size_t kNoAllocScratchBytes = size_t(1) << 20;
 
 // Shared by every call on a device; the last call's contents stay in it.
@@ -1734,7 +1733,7 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_config* cfg, const vplbm_
   p.tiles_x = tx;
   p.n_tiles = nt;
   p.tile_y = tile_rows_of(cfg);
-  p.rows_per_warp = p.tile_y / kWarps;
+  p.rows_per_warp = p.tile_y / warps_per_block(cfg->storage);
   physics_consts(cfg, &p);
   p.n_bodies = n_bodies;
   for (int b = 0; b < n_bodies; ++b) {

@@ -429,14 +429,12 @@ __device__ __forceinline__ void solid_velocity(const StepParams& p, uint8_t m, i
 
 // Sum and difference of the offsets of the opposite pair k ((1,3), (2,4),
 // (5,7), (6,8)) whose values the kernel holds in ha, hb: offsets themselves,
-// or (REF) the elements e = h - h_ref of a 16-bit store, decoded here with
-// the pair's reference sum and difference (exact in FP32).
-template <class T, bool REF>
-__device__ __forceinline__ T pair_s(const Consts<T>& c, T ha, T hb, int k) {
-  if constexpr (REF)
-    return (ha + hb) + c.r_s[k];
-  else
-    return ha + hb;
+// or (REF) the elements e = h - h_ref of a 16-bit store. h_ref is odd in xi,
+// so the pair sum of the elements is that of the offsets, and the difference
+// is decoded with the pair's reference difference (exact in FP32).
+template <class T>
+__device__ __forceinline__ T pair_s(T ha, T hb) {
+  return ha + hb;
 }
 template <class T, bool REF>
 __device__ __forceinline__ T pair_d(const Consts<T>& c, T ha, T hb, int k) {
@@ -457,12 +455,11 @@ __device__ __forceinline__ Macro<T> macros(const StepParams& p, const T h[9], ui
   const Consts<T>& c = consts<T>(p);
   // sums and differences of opposite populations (the two-rate collision
   // reuses them)
-  const T h0 = REF ? h[0] + c.h_ref[0] : h[0];
-  const T s13 = pair_s<T, REF>(c, h[1], h[3], 0), s24 = pair_s<T, REF>(c, h[2], h[4], 1);
-  const T s57 = pair_s<T, REF>(c, h[5], h[7], 2), s68 = pair_s<T, REF>(c, h[6], h[8], 3);
+  const T s13 = pair_s<T>(h[1], h[3]), s24 = pair_s<T>(h[2], h[4]);
+  const T s57 = pair_s<T>(h[5], h[7]), s68 = pair_s<T>(h[6], h[8]);
   const T d13 = pair_d<T, REF>(c, h[1], h[3], 0), d24 = pair_d<T, REF>(c, h[2], h[4], 1);
   const T d57 = pair_d<T, REF>(c, h[5], h[7], 2), d68 = pair_d<T, REF>(c, h[6], h[8], 3);
-  r.drho = h0 + ((s13 + s24) + (s57 + s68));
+  r.drho = h[0] + ((s13 + s24) + (s57 + s68));
   r.rho = T(1) + r.drho;
   const T jx = d13 + (d57 - d68);
   const T jy = d24 + (d57 + d68);
@@ -509,8 +506,8 @@ __device__ __forceinline__ Macro<T> macros(const StepParams& p, const T h[9], ui
 // same with s+ = s- = 1/tau. This is the moment-space operator rearranged,
 // not an approximation of it.
 // On the elements e = h - r of a 16-bit store (REF) the update is the same,
-// e*_a = e_a + P + Q, with s and d decoded from the elements (pair_s, pair_d),
-// and e*_0 = (1 - s+) (e_0 + r_0) + w_0 K - r_0.
+// e*_a = e_a + P + Q, with d decoded from the elements (pair_d); r is odd in
+// xi, so s, e_0 = h_0 and the rest population's update need no decoding.
 // ---------------------------------------------------------------------------
 template <class T, bool FREE>
 __device__ __forceinline__ void trt_pair(T& ha, T& hb, T s, T d, T xu, T xF, T kw, T aw, T bw,
@@ -535,14 +532,11 @@ __device__ __forceinline__ void collide_trt(const StepParams& p, T h[9], const M
   const T a9 = c.t_a[0] * rho, a36 = c.t_a[1] * rho;
   const T am9 = c.t_am[0] * rho, am36 = c.t_am[1] * rho;
   // the pair sums and differences as macros() formed them
-  const T s13 = pair_s<T, REF>(c, h[1], h[3], 0), s24 = pair_s<T, REF>(c, h[2], h[4], 1);
-  const T s57 = pair_s<T, REF>(c, h[5], h[7], 2), s68 = pair_s<T, REF>(c, h[6], h[8], 3);
+  const T s13 = pair_s<T>(h[1], h[3]), s24 = pair_s<T>(h[2], h[4]);
+  const T s57 = pair_s<T>(h[5], h[7]), s68 = pair_s<T>(h[6], h[8]);
   const T d13 = pair_d<T, REF>(c, h[1], h[3], 0), d24 = pair_d<T, REF>(c, h[2], h[4], 1);
   const T d57 = pair_d<T, REF>(c, h[5], h[7], 2), d68 = pair_d<T, REF>(c, h[6], h[8], 3);
-  if constexpr (REF)
-    h[0] = c.t_1msp * (h[0] + c.h_ref[0]) + (T(4.0 / 9.0) * K - c.h_ref[0]);
-  else
-    h[0] = c.t_1msp * h[0] + T(4.0 / 9.0) * K;
+  h[0] = c.t_1msp * h[0] + T(4.0 / 9.0) * K;
   trt_pair<T, FREE>(h[1], h[3], s13, d13, ux, Fx, k9, a9, c.t_b[0], am9, c.t_bm[0], c.t_hsp,
                     c.t_hsm);
   trt_pair<T, FREE>(h[2], h[4], s24, d24, uy, Fy, k9, a9, c.t_b[0], am9, c.t_bm[0], c.t_hsp,
@@ -629,10 +623,11 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// Sum of v[0..2] over the block (kThreads threads), fixed order; result valid
-// in thread 0.
+// Sum of v[0..2] over the block (at most kThreads threads), fixed order;
+// result valid in thread 0.
 __device__ __forceinline__ void block_sum3(double v[3], double (*sm)[3]) {
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int n_warps = int(blockDim.x * blockDim.y) >> 5;
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int k = 0; k < 3; ++k) v[k] = warp_sum(v[k]);
@@ -645,7 +640,7 @@ __device__ __forceinline__ void block_sum3(double v[3], double (*sm)[3]) {
   if (tid == 0) {
     for (int k = 0; k < 3; ++k) {
       double s = 0.0;
-      for (int w = 0; w < kThreads / 32; ++w) s += sm[w][k];
+      for (int w = 0; w < n_warps; ++w) s += sm[w][k];
       v[k] = s;
     }
   }
@@ -712,7 +707,8 @@ __device__ __forceinline__ void finish_reduction(const StepParams& p, int tile, 
   if (!s_last) return;
   __threadfence();
   double v[3] = {0.0, 0.0, 0.0};
-  for (int g = tid; g < n_groups; g += kThreads) {
+  const int n_threads = int(blockDim.x * blockDim.y);
+  for (int g = tid; g < n_groups; g += n_threads) {
     // each thread adds its strided share in increasing group order
     v[0] += __ldcg(p.group_partials + 3ll * g + 0);
     v[1] += __ldcg(p.group_partials + 3ll * g + 1);
@@ -730,8 +726,8 @@ __device__ __forceinline__ void finish_reduction(const StepParams& p, int tile, 
 
 // ---------------------------------------------------------------------------
 // The fused time step of one tile: (32 N) x tile_y nodes, N = npt(STORE). Lane
-// l of warp w takes nodes x0 + N l .. x0 + N l + N - 1 of rows y0 + w + 8 r,
-// r = 0..rows_per_warp-1.
+// l of warp w takes nodes x0 + N l .. x0 + N l + N - 1 of rows y0 + w + W r,
+// r = 0..rows_per_warp-1, W = warps_per_block(STORE).
 //
 // Every direction is pulled with one N-element vector load per lane: a
 // direction with xi_x = +1 takes its first node's value from the lane to the
@@ -1035,8 +1031,9 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
   using E = typename S::E;
   constexpr int N = npt(STORE);
   constexpr int TX = kLanes * N;
-  __shared__ double sm[kThreads / 32][3];
-  __shared__ T smass[kThreads / 32];
+  constexpr int W = warps_per_block(STORE);
+  __shared__ double sm[W][3];
+  __shared__ T smass[W];
 
   const int lane = threadIdx.x, warp = threadIdx.y;
   const int tx = tile % p.tiles_x;
@@ -1204,11 +1201,11 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
 
   if (interior) {
 #pragma unroll 1
-    for (int r = 0; r < p.rows_per_warp; ++r) do_row(y0 + warp + r * kWarps, std::false_type());
+    for (int r = 0; r < p.rows_per_warp; ++r) do_row(y0 + warp + r * W, std::false_type());
   } else {
 #pragma unroll 1
     for (int r = 0; r < p.rows_per_warp; ++r) {
-      const int y = y0 + warp + r * kWarps;
+      const int y = y0 + warp + r * W;
       if (y >= p.ny) break;  // warp-uniform: a warp is one row
       do_row(y, std::true_type());
     }
@@ -1241,10 +1238,10 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
   if (tid == 0) {
     T msum = T(0);
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) msum += smass[w];
+    for (int w = 0; w < W; ++w) msum += smass[w];
     if (block_solid) {
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) {
+      for (int w = 0; w < W; ++w) {
         ts[0] += sm[w][0];
         ts[1] += sm[w][1];
       }
@@ -1260,7 +1257,8 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
 }
 
 template <int STORE, int COLL, int MODE = kModeAB>
-__global__ void __launch_bounds__(kThreads, min_blocks_per_sm(STORE)) fused_step_kernel(const __grid_constant__ StepParams p) {
+__global__ void __launch_bounds__(threads_per_block(STORE), min_blocks_per_sm(STORE))
+    fused_step_kernel(const __grid_constant__ StepParams p) {
   step_tile<STORE, COLL, MODE>(p, blockIdx.x, p.t);
 }
 
@@ -1273,7 +1271,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks_per_sm(STORE)) fused_step
 // covers SRT and MRT solvers of one storage type. MODE: the streaming step of
 // every solver in the launch (in-place solvers are grouped by phase).
 template <int STORE, int MODE = kModeAB>
-__global__ void __launch_bounds__(kThreads, min_blocks_per_sm(STORE))
+__global__ void __launch_bounds__(threads_per_block(STORE), min_blocks_per_sm(STORE))
     fused_group_kernel(const StepParams* __restrict__ params, const GroupTile* __restrict__ table,
                        long long k) {
   __shared__ StepParams sp;
@@ -1284,7 +1282,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks_per_sm(STORE))
     const int* from = reinterpret_cast<const int*>(g);
     int* to = reinterpret_cast<int*>(&sp);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    for (int w = tid; w < int(sizeof(StepParams) / sizeof(int)); w += kThreads) to[w] = __ldg(from + w);
+    for (int w = tid; w < int(sizeof(StepParams) / sizeof(int)); w += threads_per_block(STORE))
+      to[w] = __ldg(from + w);
   }
   __syncthreads();
   if (sp.collision == kTrt)

@@ -16,11 +16,11 @@ static dim3 node_grid(const StepParams& p) {
 template <int COLL>
 static cudaError_t launch_fused_coll(const StepParams& p, cudaStream_t st) {
   if (p.mode == kModeAAPush) {
-    fused_step_kernel<VPLBM_STORE, COLL, kModeAAPush><<<p.n_tiles, dim3(kLanes, kWarps), 0, st>>>(p);
+    fused_step_kernel<VPLBM_STORE, COLL, kModeAAPush><<<p.n_tiles, dim3(kLanes, warps_per_block(VPLBM_STORE)), 0, st>>>(p);
   } else if (p.mode == kModeAALocal) {
-    fused_step_kernel<VPLBM_STORE, COLL, kModeAALocal><<<p.n_tiles, dim3(kLanes, kWarps), 0, st>>>(p);
+    fused_step_kernel<VPLBM_STORE, COLL, kModeAALocal><<<p.n_tiles, dim3(kLanes, warps_per_block(VPLBM_STORE)), 0, st>>>(p);
   } else {
-    fused_step_kernel<VPLBM_STORE, COLL, kModeAB><<<p.n_tiles, dim3(kLanes, kWarps), 0, st>>>(p);
+    fused_step_kernel<VPLBM_STORE, COLL, kModeAB><<<p.n_tiles, dim3(kLanes, warps_per_block(VPLBM_STORE)), 0, st>>>(p);
   }
   return cudaGetLastError();
 }
@@ -32,7 +32,7 @@ cudaError_t VPLBM_FN(launch_fused_)(int coll, const StepParams& p, cudaStream_t 
 cudaError_t VPLBM_FN(launch_group_)(const StepParams* d_params, const GroupTile* d_table,
                                     int n_blocks, long long k, int mode, cudaStream_t st) {
   if (n_blocks <= 0) return cudaSuccess;
-  const dim3 blk(kLanes, kWarps);
+  const dim3 blk(kLanes, warps_per_block(VPLBM_STORE));
   if (mode == kModeAAPush)
     fused_group_kernel<VPLBM_STORE, kModeAAPush><<<n_blocks, blk, 0, st>>>(d_params, d_table, k);
   else if (mode == kModeAALocal)

@@ -20,25 +20,39 @@ enum { kBcPeriodic = 0, kBcInletOutlet = 1, kBcFreeSlip = 2, kBcInletConvective 
 enum { kModeAB = 0, kModeAAPush = 1, kModeAALocal = 2 };
 
 constexpr int kMaxBodies = 8;
-// Fused-step tiles: a block is 8 warps; each warp covers one row segment of
-// 32 lanes x npt(storage) consecutive nodes and rows_per_warp rows (8 apart),
-// so a tile is (32 npt) x (8 rows_per_warp) nodes. npt makes each lane's
+// Fused-step tiles: a block is warps_per_block(storage) warps; each warp
+// covers one row segment of 32 lanes x npt(storage) consecutive nodes and
+// rows_per_warp rows (warps_per_block apart), so a tile is (32 npt) x tile_y
+// nodes, tile_y = warps_per_block x rows_per_warp. npt makes each lane's
 // access 16 bytes for FP32/FP64 storage (8 bytes for the 16-bit forms). The
 // tile height (8, 16 or 32 rows) is chosen per solver: 32 for grids with
 // enough tiles to fill the GPU several times over, shorter ones for grids
 // that would leave most of the last wave of blocks idle.
 constexpr int kLanes = 32;
-constexpr int kWarps = 8;
-constexpr int kThreads = kLanes * kWarps;
+constexpr int kWarpsMax = 8;
+constexpr int kThreads = kLanes * kWarpsMax;  // also the block of the generic reduction kernels
+constexpr int kTileRowsMin = 8;
 constexpr int kTileRowsMax = 32;
+// Warps per fused-step block: 8 for the 8- and 4-byte stores, 4 for the
+// 16-bit stores. The 16-bit kernels are bound by instruction issue; with
+// half-size blocks a warp does twice the rows per tile and fewer warps wait
+// at the per-tile reduction barrier (16384 x 4096 FP16 step 0.4461 vs
+// 0.4408 ms; the FP32 step loses 1% with 4 warps and keeps 8).
+__host__ __device__ constexpr int warps_per_block(int storage) {
+  return storage == kF16 || storage == kBF16 ? 4 : 8;
+}
+__host__ __device__ constexpr int threads_per_block(int storage) {
+  return kLanes * warps_per_block(storage);
+}
 // Resident blocks per SM the fused kernel is compiled for: 3 for the 8- and
-// 4-byte stores (80 registers per thread, 24 warps per SM, no spills), 4 for
-// the 16-bit stores, whose kernels are instruction-issue-bound and gain more
-// from 32 warps than they lose to a few spilled registers (measured on the
-// 16384 x 4096 MRT step: FP32 0.784 vs 0.805 ms at 3 vs 4; FP16 0.735 vs
+// 4-byte stores (80 registers per thread, 24 warps per SM, no spills), 8
+// blocks of 4 warps for the 16-bit stores (64 registers, 32 warps), whose
+// kernels are instruction-issue-bound and gain more from warps than they lose
+// to a few spilled registers (measured on the 16384 x 4096 MRT step with
+// 8-warp blocks: FP32 0.784 vs 0.805 ms at 3 vs 4 blocks; FP16 0.735 vs
 // 0.699 ms).
 __host__ __device__ constexpr int min_blocks_per_sm(int storage) {
-  return storage == kF16 || storage == kBF16 ? 4 : 3;
+  return storage == kF16 || storage == kBF16 ? 8 : 3;
 }
 __host__ __device__ constexpr int npt(int storage) { return storage == kF64 ? 2 : 4; }
 __host__ __device__ constexpr int tile_x(int storage) { return kLanes * npt(storage); }
@@ -46,7 +60,7 @@ __host__ __device__ constexpr int tile_x(int storage) { return kLanes * npt(stor
 // Block shape of the per-node kernels (initialisation, moments, import/export).
 constexpr int kBlockX = 64;
 constexpr int kBlockY = 4;
-constexpr int kGroup = 256;             // tiles per first-level reduction group
+constexpr int kGroup = 128;             // tiles per first-level reduction group (<= a block's threads)
 constexpr int kMeBlocks = 304;          // fixed grid of the momentum-exchange reduction (2 per SM)
 constexpr uint8_t kStaticSolid = 255;   // mask value of a node solid through the static mask
 
@@ -71,10 +85,10 @@ struct Consts {
   T gx, gy;                               // body force per unit mass
   T heq_in[9];                            // inlet ghost f_eq(1, u_in) - w
   T h_ref[9];                             // 16-bit stores: elements hold h - h_ref
-  // h_ref[a] + h_ref[b] and h_ref[a] - h_ref[b] for the opposite pairs (1,3),
-  // (2,4), (5,7), (6,8): the fused step's two-rate collision decodes pair
-  // sums and differences of stored elements with them
-  T r_s[4], r_d[4];
+  // h_ref[a] - h_ref[b] for the opposite pairs (1,3), (2,4), (5,7), (6,8):
+  // the fused step's two-rate collision decodes pair differences of stored
+  // elements with them (h_ref is odd in xi: pair sums need no decoding)
+  T r_d[4];
   T u_conv, conv_inv;                     // convective outlet: U_c and 1/(1 + U_c)
   T body[kMaxBodies][5];                  // cx, cy, vx, vy, omega of each body
 };
@@ -95,7 +109,7 @@ struct StepParams {
   int nx, ny, pitch;
   int bc_x, bc_y;
   int tiles_x, n_tiles;
-  int tile_y, rows_per_warp;  // tile height (8, 16 or 32) and tile_y / kWarps
+  int tile_y, rows_per_warp;  // tile height (8, 16 or 32) and tile_y / warps_per_block
   int n_bodies;
   long long plane;          // pitch * ny
   Consts<double> cd;        // constants for the FP64 kernels

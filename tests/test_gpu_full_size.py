@@ -48,13 +48,12 @@ def _oracle_config(w, cfg):
 
 def _element_offset(f, u_in, axis):
     """|f - r| of each population: the magnitude a 16-bit element of a
-    channel holds (r = w + (f_eq(1, u_in) - w) / 2, the reference of the
-    16-bit stores when the flow has an inlet); its binade sets the rounding
-    step."""
+    channel holds (r = w + (3/2) w xi_x u_in,x, the reference of the 16-bit
+    stores when the flow has an inlet, before its rounding to a 2^-28 grid);
+    its binade sets the rounding step."""
     xi = O.velocity_set().astype(float)
     w = O.weights()
-    xu = xi @ np.array(u_in, dtype=float)
-    r = w + 0.5 * w * (3.0 * xu + 4.5 * xu * xu - 1.5 * float(np.dot(u_in, u_in)))
+    r = w + 1.5 * w * xi[:, 0] * float(u_in[0])
     shape = [1, 1, 1]
     shape[axis] = 9
     return np.abs(f - r.reshape(shape[:f.ndim]))

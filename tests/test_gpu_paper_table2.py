@@ -25,11 +25,14 @@ runs, one change at a time (same steps and window), bound the cause:
   eta = 1e-5                       C_Dave  0.0%, C_Lrms  0.0%, St  0.0%
   window 400k-800k                 C_Dave +0.15%, C_Lrms -0.3%, St +0.3%
   FP64 vs FP32 over 100k steps     C_Dave 2.6e-4, C_Lrms 2e-4, St 1.3e-4
+  inlet ghost at the first
+    column's density (not rho = 1) C_Dave +0.29%, C_Lrms +0.14%, St +0.21%
+  symmetry planes on the node rows C_Dave +0.01%, C_Lrms +0.03%, St  0.0%
 None moves the statistics by more than 1%, so neither blockage, resolution,
-the collision operator, the mask position, eta, the window nor precision
-explains the 7-11% gap; the paper's own numbers come from the same 30D x 10D
-domain. Untested candidates: the inlet (an equilibrium ghost at rho = 1 here)
-and the symmetry plane (half-way here). The gap is stated as open.
+the collision operator, the mask position, eta, the window, precision, the
+inlet's density nor the position of the symmetry planes explains the 7-11%
+gap; the paper's own numbers come from the same 30D x 10D domain. The gap is
+stated as open.
 Bounds: the reproduced values within 1% (C_Dave, St) and 3% (C_Lrms), which
 covers the seed-to-seed spread; both force measures; 1% between the two
 measures' C_Dave and St.

@@ -29,8 +29,8 @@ the rounding step of an element (~0.01) at 11 significant bits is about ten
 times the viscous change of a population per step, and a deterministic
 rounding acts as a small systematic forcing. Those tests document the effect
 with the FP64 GPU run as the reference and bounds that are the measured
-errors with margin (FP16: C_Dave +0.9%, St +0.6%; BF16: C_Dave 0.0%, St
--5.8%, and the RMS lift halved).
+errors with margin (FP16: C_Dave +0.3%, St +0.1%; BF16: C_Dave +1.6%, St
+-7.0%, and the RMS lift halved).
 """
 import json
 import os
