@@ -357,9 +357,9 @@ vplbm_status vplbm_fused_timing(vplbm_solver* s, double* total_ms, int64_t* laun
  *
  * Scratch: the per-tile and per-group reduction sums live in a fixed 1 MiB
  * device array inside the library, which every GPU that loads the library
- * holds until the process exits. It holds at most 43,294 tiles of the fused
- * step: with tiles of 128 x 32 nodes (FP32 and 16-bit storage) about 177.3M
- * nodes, with tiles of 64 x 32 (FP64) about 88.7M. Larger grids are rejected
+ * holds until the process exits. It holds at most 43,491 tiles of the fused
+ * step: with tiles of 128 x 32 nodes (FP32 and 16-bit storage) about 178.1M
+ * nodes, with tiles of 64 x 32 (FP64) about 89.1M. Larger grids are rejected
  * with VPLBM_ERR_INVALID and a message; use vplbm_create/vplbm_step for them.
  * The first call on a device looks up the array's device address (done once
  * per device, with that device current) and keeps it for the rest of the

@@ -1599,8 +1599,8 @@ void vplbm_destroy(vplbm_solver* s) {
 
 namespace {
 
-// 1 MiB: 24 bytes per tile, 24 per group of 128 tiles, 4 per group counter
-// (+1), 16-byte alignment and the 4-byte flag hold at most 43,294 tiles.
+// 1 MiB: 24 bytes per tile, 24 per group of 256 tiles, 4 per group counter
+// (+1), 16-byte alignment and the 4-byte flag hold at most 43,491 tiles.
 constexpr size_t kNoAllocScratchBytes = size_t(1) << 20;
 
 // Shared by every call on a device; the last call's contents stay in it.

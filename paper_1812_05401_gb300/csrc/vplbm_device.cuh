@@ -623,11 +623,12 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// Sum of v[0..2] over the block (at most kThreads threads), fixed order;
-// result valid in thread 0.
+// Sum of v[0..2] over the block of NT threads, fixed order; result valid in
+// thread 0.
+template <int NT = kThreads>
 __device__ __forceinline__ void block_sum3(double v[3], double (*sm)[3]) {
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-  const int n_warps = int(blockDim.x * blockDim.y) >> 5;
+  constexpr int n_warps = NT / 32;
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int k = 0; k < 3; ++k) v[k] = warp_sum(v[k]);
@@ -653,10 +654,12 @@ __device__ __forceinline__ void block_sum3(double v[3], double (*sm)[3]) {
 // step's record (a grid of a single group writes its group sum directly).
 // Both levels are fixed-order, so the result does not depend on which blocks
 // ran when.
+template <int NT>
 __device__ __forceinline__ void finish_reduction(const StepParams& p, int tile, long long t,
                                                  const double tile_sum[3], double (*sm)[3]) {
   __shared__ int s_last;
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  constexpr int n_threads = NT;
   const int group = tile / kGroup;
   const int n_groups = (p.n_tiles + kGroup - 1) / kGroup;
   if (tid == 0) {
@@ -676,13 +679,15 @@ __device__ __forceinline__ void finish_reduction(const StepParams& p, int tile, 
     double v[3] = {0.0, 0.0, 0.0};
     const int t0 = group * kGroup;
     const int gsize = min(kGroup, p.n_tiles - t0);
-    if (tid < gsize) {
-      const double* src = p.partials + 3ll * (t0 + tid);
-      v[0] = __ldcg(src + 0);
-      v[1] = __ldcg(src + 1);
-      v[2] = __ldcg(src + 2);
+    // each thread adds its strided share of the group's tiles in increasing
+    // order (one tile per thread for 8-warp blocks, two for 4-warp blocks)
+    for (int i = tid; i < gsize; i += n_threads) {
+      const double* src = p.partials + 3ll * (t0 + i);
+      v[0] += __ldcg(src + 0);
+      v[1] += __ldcg(src + 1);
+      v[2] += __ldcg(src + 2);
     }
-    block_sum3(v, sm);
+    block_sum3<NT>(v, sm);
     if (tid == 0) {
       p.counters[group] = 0u;  // ready for the next step
       if (n_groups == 1) {
@@ -707,14 +712,13 @@ __device__ __forceinline__ void finish_reduction(const StepParams& p, int tile, 
   if (!s_last) return;
   __threadfence();
   double v[3] = {0.0, 0.0, 0.0};
-  const int n_threads = int(blockDim.x * blockDim.y);
   for (int g = tid; g < n_groups; g += n_threads) {
     // each thread adds its strided share in increasing group order
     v[0] += __ldcg(p.group_partials + 3ll * g + 0);
     v[1] += __ldcg(p.group_partials + 3ll * g + 1);
     v[2] += __ldcg(p.group_partials + 3ll * g + 2);
   }
-  block_sum3(v, sm);
+  block_sum3<NT>(v, sm);
   if (tid == 0) {
     double* r = p.ring + 3ll * (t % p.ring_len);
     r[0] = v[0];
@@ -1253,7 +1257,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int tile, long lo
     }
   }
   __syncthreads();
-  finish_reduction(p, tile, t, ts, sm);
+  finish_reduction<threads_per_block(STORE)>(p, tile, t, ts, sm);
 }
 
 template <int STORE, int COLL, int MODE = kModeAB>

@@ -60,7 +60,7 @@ __host__ __device__ constexpr int tile_x(int storage) { return kLanes * npt(stor
 // Block shape of the per-node kernels (initialisation, moments, import/export).
 constexpr int kBlockX = 64;
 constexpr int kBlockY = 4;
-constexpr int kGroup = 128;             // tiles per first-level reduction group (<= a block's threads)
+constexpr int kGroup = 256;             // tiles per first-level reduction group
 constexpr int kMeBlocks = 304;          // fixed grid of the momentum-exchange reduction (2 per SM)
 constexpr uint8_t kStaticSolid = 255;   // mask value of a node solid through the static mask
 
