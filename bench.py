@@ -500,9 +500,11 @@ def precision_record():
     Re = 100 cylinder channel, 1024 x 256, MRT; the oracle's values are the
     stored ones its own run wrote, tests/golden/c2_wake_statistics.json). The
     FP64 path develops the wake over the oracle's development steps; FP32 and
-    the 16-bit offsets (stochastic rounding) then record the oracle's window
-    from that state. Relative errors of C_Dave and St; the benchmark spec's bar for
-    the reduced-precision stores is 1e-3."""
+    the 16-bit offsets (stochastic rounding, four realizations: rounding seeds
+    0..3) then record the oracle's window from that state. For each storage:
+    the largest relative error of C_Dave, St and C_Lrms over its realizations,
+    the relative error of the realizations' mean statistics, and whether every
+    realization is within the 1e-3 bar on C_Dave and St."""
     import torch
 
     from paper_1812_05401_gb300 import diag
@@ -510,6 +512,7 @@ def precision_record():
     from paper_1812_05401_gb300 import vplbm as V
     g = json.load(open(os.path.join(ROOT, "tests", "golden", "c2_wake_statistics.json")))
     dev, meas = g["develop_steps"], g["measure_steps"]
+    keys = ("C_D_ave", "C_L_rms", "St")
     stream = torch.cuda.Stream()
     t0 = time.perf_counter()
     w = I.c2_cylinder_re100()
@@ -522,18 +525,24 @@ def precision_record():
            "reference": "FP64 oracle statistics (stored)"}
     for st in ("f32", "f16", "bf16"):
         w.storage = st
-        with V.Solver.from_workload(w, stream=stream, ring_len=meas, reduce_mass=False,
-                                    with_initial_velocity=False) as s:
-            s.set_populations(f0)
-            s.step(meas)
-            s.synchronize()
-            fx, fy, _ = s.forces()
-        r = diag.wake_statistics(fx, fy, w.u_ref, w.l_ref, discard=0.0)
-        e = {k: abs(r[k] - g[k]) / abs(g[k]) for k in ("C_D_ave", "C_L_rms", "St")}
-        out[st] = {"C_D_ave_rel_err": float(f"{e['C_D_ave']:.3g}"),
-                   "St_rel_err": float(f"{e['St']:.3g}"),
-                   "C_L_rms_rel_err": float(f"{e['C_L_rms']:.3g}"),
-                   "within_bar": bool(e["C_D_ave"] < 1e-3 and e["St"] < 1e-3)}
+        runs = []
+        for seed in ((0,) if st == "f32" else (0, 1, 2, 3)):
+            with V.Solver.from_workload(w, stream=stream, ring_len=meas, reduce_mass=False,
+                                        with_initial_velocity=False, rounding_seed=seed) as s:
+                s.set_populations(f0)
+                s.step(meas)
+                s.synchronize()
+                fx, fy, _ = s.forces()
+            runs.append(diag.wake_statistics(fx, fy, w.u_ref, w.l_ref, discard=0.0))
+        worst = {k: max(abs(r[k] - g[k]) / abs(g[k]) for r in runs) for k in keys}
+        mean = {k: (sum(r[k] for r in runs) / len(runs) - g[k]) / abs(g[k]) for k in keys}
+        out[st] = {"realizations": len(runs),
+                   "C_D_ave_rel_err": float(f"{worst['C_D_ave']:.3g}"),
+                   "St_rel_err": float(f"{worst['St']:.3g}"),
+                   "C_L_rms_rel_err": float(f"{worst['C_L_rms']:.3g}"),
+                   "mean_C_D_ave_rel_err": float(f"{mean['C_D_ave']:.3g}"),
+                   "mean_St_rel_err": float(f"{mean['St']:.3g}"),
+                   "within_bar": bool(worst["C_D_ave"] < 1e-3 and worst["St"] < 1e-3)}
     out["seconds"] = round(time.perf_counter() - t0, 1)
     return out
 
